@@ -1,0 +1,386 @@
+"""Benchmark: MaxCut QAOA on one GB300 (replicas on N GPUs).
+
+One step is one pass of the whole hot path on a seeded synthetic instance:
+cost vector C(z), p layers with fused <C>, sampling, and the adjoint gradient
+(p forward layers + p uncompute layers).  value = QAOA layers applied per second
+(3p per step), whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--n 30] [--dtype c128] [--p 6] [--shots 1000000] [--family reg3]
+
+Under torchrun every rank runs an independent replica (the simulation does not
+shard); timing is the max over ranks.  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as ct
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "QAOA layer sweeps/s & HBM GB/s at n=28-32; grad evals/s; batched vs plain"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=30)
+    ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
+    ap.add_argument("--p", type=int, default=6)
+    ap.add_argument("--shots", type=int, default=1_000_000)
+    ap.add_argument("--family", default="reg3", choices=["reg3", "gnp"])
+    ap.add_argument("--weights", default=None, help="u01 | int (default: u01 for c128, int for c64)")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    a = ap.parse_args()
+    if a.warmup < 3:
+        a.warmup = 3
+    if a.weights is None:
+        a.weights = "u01" if a.dtype == "c128" else "int"
+    return a
+
+
+def workload_name(a):
+    fam = "random 3-regular" if a.family == "reg3" else "G(n,0.1)"
+    w = "U(0,1) fp64 weights" if a.weights == "u01" else "integer weights {1..10}"
+    return (f"MaxCut QAOA n={a.n} {fam}, {w}, p={a.p}, {a.dtype} statevector: cost vector + "
+            f"{a.p} layers with <C> + {a.shots} samples + adjoint gradient (2p layers)")
+
+
+def make_instance(a):
+    import synth
+    e, w, integer = synth.graph(a.family, a.n, a.seed, weights=a.weights, prob=0.1)
+    gam, bet = synth.angles(a.p, a.seed)
+    return e, w, integer, gam, bet
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    p = ROOT / "MEASURED_PEAKS.json"
+    try:
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_record(kernel_hash: str):
+    """Per-launch DRAM bytes of the sweep kernel from the committed ncu summary, if current."""
+    p = ROOT / "profiles" / "sweep_traffic.json"
+    try:
+        d = json.loads(p.read_text())
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_hash:
+        return None
+    return d
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+
+def oracle_layer_sample(a, e, w, integer, gam, bet):
+    """Time the oracle on a bounded slice of the workload: one layer (phase + RX on the
+    slice's low qubits) over the first 2^k amplitudes of the n-qubit state.  Returns
+    (seconds for the slice, k, the scale factor to one full layer)."""
+    from oracle import qaoa
+    k = min(a.n, 22)
+    zs = np.arange(1 << k, dtype=np.int64)
+    C = np.zeros(1 << k, dtype=np.int64 if integer else np.float64)
+    for (u, v), we in zip(e, w):  # the slice of C(z) (bits >= k are 0)
+        cut = ((zs >> u) ^ (zs >> v)) & 1
+        C = C + (int(we) * cut if integer else we * cut.astype(np.float64))
+    psi = np.full(1 << k, 2.0 ** (-a.n / 2), dtype=np.complex128)
+    t0 = time.perf_counter()
+    psi = qaoa.apply_cost_unitary(psi, C, gam[0])
+    psi = qaoa.apply_rx_all(psi, k, bet[0])
+    dt = time.perf_counter() - t0
+    scale = (2.0 ** (a.n - k)) * (a.n / k)
+    return dt, k, scale
+
+
+def cpu_baseline(a, e, w, integer, gam, bet):
+    reps, total, k, scale = 0, 0.0, 0, 1.0
+    t_end = time.perf_counter() + 12.0
+    while time.perf_counter() < t_end or reps == 0:
+        dt, k, scale = oracle_layer_sample(a, e, w, integer, gam, bet)
+        total += dt
+        reps += 1
+    per_layer = total / reps * scale
+    return {"value": 1.0 / per_layer, "unit": "layers/s", "cores": 1, "kind": "oracle",
+            "sample": (f"numpy oracle, one layer (phase + RX on {k} qubits) over a 2^{k}-amplitude slice of the "
+                       f"n={a.n} state, {reps} repetitions, scaled x{scale:.1f} to one full n={a.n} layer")}
+
+
+def run_reference(a):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    e, w, integer, gam, bet = make_instance(a)
+    times = []
+    for i in range(a.warmup + a.steps):
+        dt, k, scale = oracle_layer_sample(a, e, w, integer, gam, bet)
+        if i >= a.warmup:
+            times.append(dt * scale * 3 * a.p)  # one step = 3p layer applications
+    step = statistics.mean(times)
+    value = 3 * a.p / step
+    line = {"metric": METRIC, "impl": "reference", "value": value, "unit": "layers/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "n": a.n, "p": a.p, "state_dtype": a.dtype},
+            "cpu_baseline": {"value": value, "unit": "layers/s", "cores": 1, "kind": "oracle",
+                             "sample": f"numpy oracle layer over a 2^{k}-amplitude slice of the n={a.n} state, "
+                                       f"scaled x{scale:.1f} per layer, 3p layers per step"},
+            "e2e": {"value": value, "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2407_13012_gb300 as q
+    from paper_2407_13012_gb300 import _build
+
+    e, w, integer, gam, bet = make_instance(a)
+    graph = q.Graph(a.n, e, w, integer)
+    cdt = "i32" if integer else "f64"
+    dev = torch.device("cuda", local)
+    C = torch.empty(1 << a.n, dtype=torch.int32 if integer else torch.float64, device=dev)
+    psi = q.new_state(a.n, a.dtype, dev)
+    lam = q.new_state(a.n, a.dtype, dev)
+    shots = a.shots
+    z = torch.empty(shots, dtype=torch.int64, device=dev)
+    cz = torch.empty(shots, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    dt_code = q.C128 if a.dtype == "c128" else q.C64
+    lo, hi = graph.check()
+    span = hi - lo + 1 if integer else 0
+    ws_bytes = max(q.workspace_size(a.n, dt_code, q.OP_LAYERS, a.p, 0, span),
+                   q.workspace_size(a.n, dt_code, q.OP_SAMPLE, 0, shots),
+                   q.workspace_size(a.n, dt_code, q.OP_GRADIENT, a.p, 0, span),
+                   q.workspace_size(a.n, dt_code, q.OP_EXPECTATION))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    eout = torch.empty(2, dtype=torch.float64, device=dev)
+    gout = torch.empty(2 * a.p + 2, dtype=torch.float64, device=dev)
+    gp = gam.ctypes.data_as(ct.POINTER(ct.c_double))
+    bp = bet.ctypes.data_as(ct.POINTER(ct.c_double))
+    sp = ct.c_void_p(stream.cuda_stream)
+    L = q.lib
+
+    def chk(rc, what):
+        if rc != 0:
+            raise q.QaoaError(rc, what)
+
+    def step_device():
+        desc = q.CostT()
+        gs = graph.as_struct()
+        chk(L.qaoa_cost_vector(ct.byref(gs), ct.c_void_p(C.data_ptr()), q.COST_I32 if integer else q.COST_F64,
+                               ct.byref(desc), sp), "cost")
+        chk(L.qaoa_apply_layers(a.n, dt_code, ct.c_void_p(psi.data_ptr()), ct.byref(desc), gp, bp, a.p, 1,
+                                ct.c_void_p(eout.data_ptr()), ct.c_void_p(ws.data_ptr()), ws_bytes, sp), "layers")
+        chk(L.qaoa_sample(a.n, dt_code, ct.c_void_p(psi.data_ptr()), ct.byref(desc), shots, 7,
+                          ct.c_void_p(z.data_ptr()), ct.c_void_p(cz.data_ptr()), ct.c_void_p(ws.data_ptr()),
+                          ws_bytes, sp), "sample")
+        chk(L.qaoa_gradient(a.n, dt_code, ct.c_void_p(psi.data_ptr()), ct.c_void_p(lam.data_ptr()), ct.byref(desc),
+                            gp, bp, a.p, ct.c_void_p(gout.data_ptr()), ct.c_void_p(ws.data_ptr()), ws_bytes, sp),
+            "gradient")
+
+    # host buffers for the end-to-end variant (pinned)
+    z_host = torch.empty(shots, dtype=torch.int64, pin_memory=True)
+    c_host = torch.empty(shots, dtype=torch.float64, pin_memory=True)
+    g_host = np.zeros(2 * a.p + 2)
+    e_host = np.zeros(2)
+
+    def step_e2e():
+        desc = q.CostT()
+        gs = graph.as_struct()
+        chk(L.qaoa_cost_vector(ct.byref(gs), ct.c_void_p(C.data_ptr()), q.COST_I32 if integer else q.COST_F64,
+                               ct.byref(desc), sp), "cost")
+        chk(L.qaoa_apply_layers(a.n, dt_code, ct.c_void_p(psi.data_ptr()), ct.byref(desc), gp, bp, a.p, 1, None,
+                                ct.c_void_p(ws.data_ptr()), ws_bytes, sp), "layers")
+        chk(L.qaoa_expectation_host(a.n, dt_code, ct.c_void_p(psi.data_ptr()), ct.byref(desc),
+                                    e_host.ctypes.data_as(ct.POINTER(ct.c_double)), ct.c_void_p(ws.data_ptr()),
+                                    ws_bytes, sp), "expectation_host")
+        chk(L.qaoa_sample_host(a.n, dt_code, ct.c_void_p(psi.data_ptr()), ct.byref(desc), shots, 7,
+                               ct.c_void_p(z.data_ptr()), ct.c_void_p(cz.data_ptr()), ct.c_void_p(z_host.data_ptr()),
+                               ct.c_void_p(c_host.data_ptr()), ct.c_void_p(ws.data_ptr()), ws_bytes, sp),
+            "sample_host")
+        chk(L.qaoa_gradient_host(a.n, dt_code, ct.c_void_p(psi.data_ptr()), ct.c_void_p(lam.data_ptr()),
+                                 ct.byref(desc), gp, bp, a.p, ct.c_void_p(gout.data_ptr()),
+                                 g_host.ctypes.data_as(ct.POINTER(ct.c_double)), ct.c_void_p(ws.data_ptr()),
+                                 ws_bytes, sp), "gradient_host")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(a.warmup):
+        step_device()
+    torch.cuda.synchronize()
+
+    # ---- timed device region
+    clocks = Clocks(local)
+    q.timing_read()
+    q.timing_enable(True)
+    q.launch_count_reset()
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(a.steps):
+        step_device()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    launches = q.launch_count()
+    q.timing_enable(False)
+    kms, kla, kby, dropped = q.timing_read()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    step_ms = ms / a.steps
+    layers_per_step = 3 * a.p
+    value = world * layers_per_step * a.steps / (ms / 1e3)
+
+    # ---- end-to-end region (host buffers through the C ABI)
+    for _ in range(1):
+        step_e2e()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * layers_per_step * a.steps / e2e_s
+    h2d = e.nbytes + (w.nbytes if w is not None else 0) + gam.nbytes + bet.nbytes
+    d2h = 16 + shots * 16 + (2 * a.p + 2) * 8
+
+    # ---- roofline of the dominant kernel (layer sweeps), measured live
+    peak, peak_kind = measured_peak_hbm()
+    sweep_ms, sweep_n, sweep_bytes = kms[0], kla[0], kby[0]
+    achieved = (sweep_bytes / (sweep_ms / 1e3)) / 1e9 if sweep_ms > 0 else 0.0
+    tr = traffic_record(_build.source_hash())
+    traffic = None
+    if tr is not None:
+        traffic = tr.get("bytes_per_launch")
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "layers/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if a.dtype == "c128" else "f32", "data": "synthetic",
+            "config": {"workload": workload_name(a), "n": a.n, "p": a.p, "state_dtype": a.dtype,
+                       "family": a.family, "weights": a.weights, "shots": shots,
+                       "layers_per_step": layers_per_step, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (state %.1f GB)" % ((16 if a.dtype == 'c128' else 8) * 2 ** a.n / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "layer sweep", "launches": sweep_n,
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "kernels_ms": {"sweep": kms[0], "cost": kms[1], "sample": kms[2], "other": kms[3]},
+            "kernels_launches": {"sweep": kla[0], "cost": kla[1], "sample": kla[2], "other": kla[3]},
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_value, "unit": "layers/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "clocks": clk,
+        }
+        if not a.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(a, e, w, integer, gam, bet)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,240 @@
+/*
+ * qaoa_gb300.h — C ABI of the GB300 MaxCut-QAOA statevector simulator.
+ *
+ * The method is the QAOA of arXiv 2407.13012 (CUAOA), Eq. 1:
+ *   |psi> = U_M(beta_p) U_C(gamma_p) ... U_M(beta_1) U_C(gamma_1) |+>^n,
+ *   U_C(gamma) = exp(-i gamma H_C), H_C = diag(C(z)) (Sec. II-A),
+ *   U_M(beta)  = exp(-i beta sum_j X_j) = prod_j RX_j(2 beta).
+ * The paper's mixer Hamiltonian H_M = -sum_j X_j (Sec. II-A) gives
+ * R_x(-2 beta) (Sec. IV-B); this library uses RX(+2 beta), i.e. the paper's
+ * angles with beta -> -beta.  Pass mixer angles negated to get the paper's
+ * convention.
+ *
+ * Conventions shared by every call:
+ *  - Amplitude index z in [0, 2^n); qubit j is bit j of z (the one-hot
+ *    encoding of Eq. 3, variable i <-> 2^i).
+ *  - C(z) = sum over edges (u,v) of w_uv * [bit u of z != bit v of z]
+ *    (MaxCut, Sec. V).
+ *  - State buffers are interleaved (re, im): QAOA_C128 = 2 x float64 per
+ *    amplitude (16 B), QAOA_C64 = 2 x float32 (8 B).  Layout is index order.
+ *  - Every pointer named *_dev is device memory owned by the caller; the
+ *    library never allocates or frees device memory.  Host pointers are read
+ *    during the call only.
+ *  - All device work is enqueued on `stream` (a cudaStream_t passed as
+ *    void*; NULL = legacy default stream) and is asynchronous unless the name
+ *    ends in _host, in which case the call synchronises `stream` and writes
+ *    host outputs before returning.
+ *  - `ws_dev`/`ws_bytes`: caller-owned device scratch of at least
+ *    qaoa_workspace_size() bytes, 256-byte aligned.  Its content on entry is
+ *    ignored; calls that share one workspace must be ordered on a stream.
+ *  - Return value: QAOA_OK or an error code.  Argument errors are detected
+ *    on the host before anything is enqueued.  QAOA_ERR_CUDA reports a
+ *    launch or runtime error (cudaGetLastError after each launch).
+ *
+ * Limits: 1 <= n <= 32; p <= QAOA_MAX_P.
+ */
+#ifndef QAOA_GB300_H
+#define QAOA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QAOA_MAX_N 32
+#define QAOA_MAX_P 64
+
+enum qaoa_status {
+  QAOA_OK = 0,
+  QAOA_ERR_INVALID_ARG = 1, /* bad pointer, size, graph or angle */
+  QAOA_ERR_UNSUPPORTED = 2, /* valid but outside this build's limits */
+  QAOA_ERR_CUDA = 3,        /* CUDA launch / runtime error */
+  QAOA_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+  QAOA_ERR_WORKSPACE = 5    /* ws_bytes smaller than qaoa_workspace_size() */
+};
+
+enum qaoa_dtype { QAOA_C128 = 0, QAOA_C64 = 1 };
+enum qaoa_cost_dtype { QAOA_COST_I32 = 0, QAOA_COST_F64 = 1 };
+enum qaoa_weight_kind { QAOA_WEIGHT_INT = 0, QAOA_WEIGHT_F64 = 1 };
+enum qaoa_op {
+  QAOA_OP_COST = 0,
+  QAOA_OP_LAYERS = 1,
+  QAOA_OP_EXPECTATION = 2,
+  QAOA_OP_SAMPLE = 3,
+  QAOA_OP_GRADIENT = 4
+};
+
+/*
+ * Weighted graph on host memory (MaxCut instance, Sec. V).
+ *  n            number of vertices = qubits, 1..32.
+ *  m            number of edges, >= 0.
+ *  uv           2*m int32: edge e joins uv[2e] and uv[2e+1].
+ *  w            m float64 weights, or NULL for all weights 1.
+ *  weight_kind  QAOA_WEIGHT_INT: every weight must be integral with
+ *               sum |w| < 2^31; QAOA_WEIGHT_F64: any finite weights.
+ * Rejected (QAOA_ERR_INVALID_ARG): u == v, a vertex outside [0, n), a
+ * repeated edge (in either orientation), a non-finite weight, a non-integral
+ * weight under QAOA_WEIGHT_INT.
+ */
+typedef struct qaoa_graph {
+  int32_t n;
+  int64_t m;
+  const int32_t* uv;
+  const double* w;
+  int32_t weight_kind;
+} qaoa_graph_t;
+
+/*
+ * Cost vector descriptor.  C_dev holds 2^n entries of `dtype` (device
+ * memory, caller-owned).  For QAOA_COST_I32, [cmin, cmax] are bounds the
+ * caller promises for every entry; the phase kernels then look
+ * exp(-i gamma c) up in a table of cmax - cmin + 1 entries (when that span is
+ * at most QAOA_MAX_TABLE_SPAN).  An entry outside the bounds is still handled
+ * correctly (computed directly), so wrong bounds cost speed, never
+ * correctness.  cmax < cmin means "unknown" (no table).  qaoa_cost_vector()
+ * fills a descriptor with exact bounds.
+ */
+#define QAOA_MAX_TABLE_SPAN 16384
+typedef struct qaoa_cost {
+  const void* C_dev;
+  int32_t dtype;
+  int64_t cmin;
+  int64_t cmax;
+} qaoa_cost_t;
+
+/* Library version as 10000*major + 100*minor + patch. */
+int qaoa_version(void);
+
+/* Static description of a status code (never NULL). */
+const char* qaoa_strerror(int status);
+
+/*
+ * Validate a graph on the host without touching the GPU.  Returns QAOA_OK or
+ * QAOA_ERR_INVALID_ARG; on success, if non-NULL, *cmin/*cmax receive integer
+ * bounds on C(z) (sum of negative / positive weights) for integer graphs.
+ */
+int qaoa_graph_check(const qaoa_graph_t* g, int64_t* cmin, int64_t* cmax);
+
+/*
+ * Bytes of device scratch the call `op` (enum qaoa_op) needs for n qubits,
+ * state dtype `dtype`, depth p (QAOA_OP_LAYERS / QAOA_OP_GRADIENT; ignored
+ * otherwise), `shots` (QAOA_OP_SAMPLE; ignored otherwise) and cost range
+ * `cost_span` = cmax - cmin + 1 of the integer cost vector's descriptor (0
+ * when there is no table: float costs or unknown bounds).  Host-only;
+ * writes *bytes.
+ */
+int qaoa_workspace_size(int n, int dtype, int op, int p, int64_t shots, int64_t cost_span,
+                        size_t* bytes);
+
+/*
+ * S1 — cost vector (Sec. IV-A, Eq. 3; "the precomputation of the cost
+ * Hamiltonian", Sec. I): fill C_dev[z] = C(z) for all z in [0, 2^n).
+ *  cost_dtype QAOA_COST_I32: int32 values, exact; needs an integer graph.
+ *  cost_dtype QAOA_COST_F64: float64 values.  Integer graphs: exact.  Float
+ *    weights: the sum of the edge weights quantised to a common binary
+ *    fixed point with 2^-(62 - ceil(log2(sum|w| + 1))) resolution, summed
+ *    exactly, rounded once to float64 (|error| <= (m+1) 2^-52 max(1, sum|w|)).
+ * C_dev holds 2^n elements of the chosen type.  No workspace.  If desc is
+ * non-NULL it is filled with {C_dev, cost_dtype, cmin, cmax}: the sums of the
+ * negative and of the positive weights for integer graphs, cmax < cmin for
+ * float weights.
+ */
+int qaoa_cost_vector(const qaoa_graph_t* g, void* C_dev, int cost_dtype, qaoa_cost_t* desc,
+                     void* stream);
+
+/*
+ * S2+S3 — apply p QAOA layers in place (Eq. 1; Sec. IV-B):
+ * for l = 0..p-1: psi_z *= exp(-i gamma[l] C(z)), then RX(2 beta[l]) on every
+ * qubit.  init = 1 starts from |+>^n (psi_dev is write-only then); init = 0
+ * continues from the state in psi_dev.  gamma/beta are host arrays of p
+ * doubles.  p = 0 with init = 1 just writes |+>^n.
+ *  expect_dev: optional (may be NULL) device double[2] receiving
+ *    [<C>, <psi|psi>] of the final state, fused into the last sweep.
+ */
+int qaoa_apply_layers(int n, int dtype, void* psi_dev, const qaoa_cost_t* cost,
+                      const double* gamma, const double* beta, int p, int init,
+                      double* expect_dev, void* ws_dev, size_t ws_bytes, void* stream);
+
+/*
+ * S4 — expectation value (Sec. IV-D): out_dev[0] = sum_z C(z) |psi_z|^2,
+ * out_dev[1] = sum_z |psi_z|^2 (device doubles; deterministic reduction
+ * order, float64 accumulation).
+ */
+int qaoa_expectation(int n, int dtype, const void* psi_dev, const qaoa_cost_t* cost,
+                     double* out_dev, void* ws_dev, size_t ws_bytes, void* stream);
+
+/* As qaoa_expectation, then synchronise and copy the two doubles to out_host. */
+int qaoa_expectation_host(int n, int dtype, const void* psi_dev, const qaoa_cost_t* cost,
+                          double* out_host, void* ws_dev, size_t ws_bytes, void* stream);
+
+/*
+ * S5+S6 — draw `shots` bitstrings from |psi_z|^2 on the device (Sec. IV-D)
+ * and return each with its objective value.  Uniforms: u_i (i = 0..shots-1)
+ * is the i-th 53-bit uniform of the SplitMix64 counter stream keyed by
+ * (seed, "sample"): base = mix64(mix64(seed) ^ 0x5f5f656c706d6173),
+ * x_i = mix64(base + (i+1) * 0x9E3779B97F4A7C15), u_i = (x_i >> 11) * 2^-53.
+ * Rule: z_i = min{z : P(z) > u_i * P_total} with P the inclusive prefix sum
+ * of |psi|^2 in index order; a target at or past the end yields the last z
+ * of nonzero probability.  Outputs: z_dev[i] (uint64), cost_dev[i] =
+ * C(z_i) as float64 (exact copy of the cost vector entry).  Shot order is
+ * draw order.  shots may be 0.
+ */
+int qaoa_sample(int n, int dtype, const void* psi_dev, const qaoa_cost_t* cost, int64_t shots,
+                uint64_t seed, uint64_t* z_dev, double* cost_dev, void* ws_dev, size_t ws_bytes,
+                void* stream);
+
+/* As qaoa_sample, then synchronise and copy z and cost to the host arrays. */
+int qaoa_sample_host(int n, int dtype, const void* psi_dev, const qaoa_cost_t* cost,
+                     int64_t shots, uint64_t seed, uint64_t* z_dev, double* cost_dev,
+                     uint64_t* z_host, double* cost_host, void* ws_dev, size_t ws_bytes,
+                     void* stream);
+
+/*
+ * S7 — adjoint gradient of E = <C> (Sec. II-B; QAOA form Sec. IV-C).
+ * Runs the forward pass from |+>^n into psi_dev, sets lambda = C psi, then
+ * walks the layers backwards uncomputing both states, with
+ *   dE/dbeta_l  = 2 Im <lambda| sum_j X_j |psi>  (before U_M(beta_l)^dagger)
+ *   dE/dgamma_l = 2 Im <lambda| C |psi>          (before U_C(gamma_l)^dagger).
+ * out_dev (device, 2p+2 doubles): [E, <psi|psi>, dE/dgamma_1..p,
+ * dE/dbeta_1..p].  psi_dev and lambda_dev are 2^n-amplitude buffers of
+ * `dtype`; on return psi_dev holds the uncomputed state (|+>^n up to
+ * rounding) and lambda_dev is unspecified.
+ */
+int qaoa_gradient(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,
+                  const double* gamma, const double* beta, int p, double* out_dev, void* ws_dev,
+                  size_t ws_bytes, void* stream);
+
+/* As qaoa_gradient, then synchronise and copy the 2p+2 doubles to out_host. */
+int qaoa_gradient_host(int n, int dtype, void* psi_dev, void* lambda_dev,
+                       const qaoa_cost_t* cost, const double* gamma, const double* beta, int p,
+                       double* out_dev, double* out_host, void* ws_dev, size_t ws_bytes,
+                       void* stream);
+
+/*
+ * Launch accounting (for benchmarks): number of kernels this library has
+ * launched in this process since the last reset.  Host-only.
+ */
+int64_t qaoa_launch_count(void);
+void qaoa_launch_count_reset(void);
+
+/*
+ * Per-kernel timing (for benchmarks).  While enabled, the library records a
+ * CUDA event pair around every launch on the launching stream, by kernel
+ * class: 0 = layer sweep, 1 = cost vector, 2 = sampling sweeps, 3 = small
+ * reductions / tables / scans.  qaoa_timing_read() synchronises the recorded
+ * events and writes, per class (arrays of 4, any may be NULL), the summed
+ * milliseconds, the launch count and the algorithmic HBM bytes of those
+ * launches (each state, lambda and cost-vector element read or written once
+ * per launch), then clears them.  At most 65536 launches are recorded between
+ * reads; later ones are counted in *dropped but not timed.
+ */
+int qaoa_timing_enable(int on);
+int qaoa_timing_read(double* ms, int64_t* launches, double* bytes, int64_t* dropped);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QAOA_GB300_H */

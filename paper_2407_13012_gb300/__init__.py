@@ -1,0 +1,318 @@
+"""GB300-native MaxCut-QAOA statevector simulator (arXiv 2407.13012, CUAOA) — Python binding.
+
+A thin ctypes layer over ``libqaoa_gb300.so`` (declared in
+``include/qaoa_gb300.h``).  It only marshals arguments: torch supplies device
+memory and the current CUDA stream; every step of the computation runs in the
+library's CUDA kernels.  There is no CPU fallback: if the library cannot be
+loaded, importing this package raises.
+
+Conventions (see the header): qubit j is bit j of the amplitude index;
+C(z) = sum over edges of w_uv [z_u != z_v]; a layer is
+psi *= exp(-i gamma C) followed by RX(2 beta) on every qubit.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import math
+from dataclasses import dataclass
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+_LIB_PATH = _PKG / "libqaoa_gb300.so"
+
+QAOA_OK, QAOA_ERR_INVALID_ARG, QAOA_ERR_UNSUPPORTED, QAOA_ERR_CUDA, QAOA_ERR_TIMEOUT, QAOA_ERR_WORKSPACE = range(6)
+C128, C64 = 0, 1
+COST_I32, COST_F64 = 0, 1
+WEIGHT_INT, WEIGHT_F64 = 0, 1
+OP_COST, OP_LAYERS, OP_EXPECTATION, OP_SAMPLE, OP_GRADIENT = range(5)
+MAX_N, MAX_P, MAX_TABLE_SPAN = 32, 64, 16384
+
+EXPORTS = [
+    "qaoa_version", "qaoa_strerror", "qaoa_graph_check", "qaoa_workspace_size", "qaoa_cost_vector",
+    "qaoa_apply_layers", "qaoa_expectation", "qaoa_expectation_host", "qaoa_sample", "qaoa_sample_host",
+    "qaoa_gradient", "qaoa_gradient_host", "qaoa_launch_count", "qaoa_launch_count_reset",
+    "qaoa_timing_enable", "qaoa_timing_read",
+]
+
+
+class QaoaError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {_lib.qaoa_strerror(status).decode()} (status {status})")
+        self.status = status
+
+
+class GraphT(ct.Structure):
+    _fields_ = [("n", ct.c_int32), ("m", ct.c_int64), ("uv", ct.POINTER(ct.c_int32)),
+                ("w", ct.POINTER(ct.c_double)), ("weight_kind", ct.c_int32)]
+
+
+class CostT(ct.Structure):
+    _fields_ = [("C_dev", ct.c_void_p), ("dtype", ct.c_int32), ("cmin", ct.c_int64), ("cmax", ct.c_int64)]
+
+
+def _load() -> ct.CDLL:
+    if not _LIB_PATH.exists():
+        from . import _build
+        _build.build()
+    lib = ct.CDLL(str(_LIB_PATH))
+    vp, i32, i64, u64, dp, szp = ct.c_void_p, ct.c_int, ct.c_int64, ct.c_uint64, ct.POINTER(ct.c_double), ct.POINTER(ct.c_size_t)
+    sig = {
+        "qaoa_version": ([], i32),
+        "qaoa_strerror": ([i32], ct.c_char_p),
+        "qaoa_graph_check": ([ct.POINTER(GraphT), ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64)], i32),
+        "qaoa_workspace_size": ([i32, i32, i32, i32, i64, i64, szp], i32),
+        "qaoa_cost_vector": ([ct.POINTER(GraphT), vp, i32, ct.POINTER(CostT), vp], i32),
+        "qaoa_apply_layers": ([i32, i32, vp, ct.POINTER(CostT), dp, dp, i32, i32, vp, vp, ct.c_size_t, vp], i32),
+        "qaoa_expectation": ([i32, i32, vp, ct.POINTER(CostT), vp, vp, ct.c_size_t, vp], i32),
+        "qaoa_expectation_host": ([i32, i32, vp, ct.POINTER(CostT), dp, vp, ct.c_size_t, vp], i32),
+        "qaoa_sample": ([i32, i32, vp, ct.POINTER(CostT), i64, u64, vp, vp, vp, ct.c_size_t, vp], i32),
+        "qaoa_sample_host": ([i32, i32, vp, ct.POINTER(CostT), i64, u64, vp, vp, vp, vp, vp, ct.c_size_t, vp], i32),
+        "qaoa_gradient": ([i32, i32, vp, vp, ct.POINTER(CostT), dp, dp, i32, vp, vp, ct.c_size_t, vp], i32),
+        "qaoa_gradient_host": ([i32, i32, vp, vp, ct.POINTER(CostT), dp, dp, i32, vp, dp, vp, ct.c_size_t, vp], i32),
+        "qaoa_launch_count": ([], i64),
+        "qaoa_launch_count_reset": ([], None),
+        "qaoa_timing_enable": ([i32], i32),
+        "qaoa_timing_read": ([dp, ct.POINTER(ct.c_int64), dp, ct.POINTER(ct.c_int64)], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes, f.restype = args, res
+    return lib
+
+
+_lib = _load()
+lib = _lib
+
+
+def _check(status: int, where: str) -> None:
+    if status != QAOA_OK:
+        raise QaoaError(status, where)
+
+
+def version() -> int:
+    return _lib.qaoa_version()
+
+
+# ---------------------------------------------------------------- graphs
+
+
+@dataclass
+class Graph:
+    """MaxCut instance: n vertices, int32 edges (m, 2), float64 weights, integer flag."""
+    n: int
+    edges: np.ndarray
+    weights: np.ndarray | None = None
+    integer: bool = True
+
+    def __post_init__(self):
+        self.edges = np.ascontiguousarray(np.asarray(self.edges, dtype=np.int32).reshape(-1, 2))
+        if self.weights is not None:
+            self.weights = np.ascontiguousarray(np.asarray(self.weights, dtype=np.float64))
+
+    @property
+    def m(self) -> int:
+        return len(self.edges)
+
+    def as_struct(self) -> GraphT:
+        uv = self.edges.ctypes.data_as(ct.POINTER(ct.c_int32))
+        w = self.weights.ctypes.data_as(ct.POINTER(ct.c_double)) if self.weights is not None else None
+        return GraphT(self.n, self.m, uv, w, WEIGHT_INT if self.integer else WEIGHT_F64)
+
+    def check(self) -> tuple[int, int]:
+        """Host-side validation; returns integer bounds (cmin, cmax) on C(z)."""
+        lo, hi = ct.c_int64(), ct.c_int64()
+        g = self.as_struct()
+        _check(_lib.qaoa_graph_check(ct.byref(g), ct.byref(lo), ct.byref(hi)), "graph_check")
+        return lo.value, hi.value
+
+
+def workspace_size(n: int, dtype: int, op: int, p: int = 0, shots: int = 0, cost_span: int = 0) -> int:
+    out = ct.c_size_t()
+    _check(_lib.qaoa_workspace_size(n, dtype, op, p, shots, cost_span, ct.byref(out)), "workspace_size")
+    return out.value
+
+
+# ------------------------------------------------------------------ torch side
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(device=None) -> int:
+    torch = _torch()
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+_ws_cache: dict = {}
+
+
+def _workspace(nbytes: int, device):
+    """A cached device scratch buffer of at least nbytes (torch-allocated)."""
+    torch = _torch()
+    key = torch.device(device).index if torch.device(device).index is not None else torch.cuda.current_device()
+    buf = _ws_cache.get(key)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+        _ws_cache[key] = buf
+    return buf
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.complex128:
+        return C128
+    if t.dtype == torch.complex64:
+        return C64
+    raise TypeError(f"state must be complex128 or complex64, got {t.dtype}")
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("tensors must be contiguous CUDA tensors")
+
+
+@dataclass
+class CostVector:
+    """A device cost vector C(z) with its descriptor (dtype, integer bounds)."""
+    C: object          # torch tensor int32 or float64, 2^n entries
+    n: int
+    cmin: int = 1
+    cmax: int = 0
+
+    @property
+    def code(self) -> int:
+        torch = _torch()
+        return COST_I32 if self.C.dtype == torch.int32 else COST_F64
+
+    @property
+    def span(self) -> int:
+        return self.cmax - self.cmin + 1 if self.cmax >= self.cmin else 0
+
+    def struct(self) -> CostT:
+        return CostT(self.C.data_ptr(), self.code, self.cmin, self.cmax)
+
+
+def cost_vector(graph: Graph, dtype: str = "i32", device="cuda", out=None) -> CostVector:
+    """S1: C(z) for all z on the device (int32 exact, or float64)."""
+    torch = _torch()
+    tdt = torch.int32 if dtype == "i32" else torch.float64
+    C = out if out is not None else torch.empty(1 << graph.n, dtype=tdt, device=device)
+    _require_cuda(C)
+    desc = CostT()
+    g = graph.as_struct()
+    code = COST_I32 if tdt == torch.int32 else COST_F64
+    _check(_lib.qaoa_cost_vector(ct.byref(g), ct.c_void_p(C.data_ptr()), code, ct.byref(desc),
+                                 ct.c_void_p(_stream(C.device))), "cost_vector")
+    return CostVector(C, graph.n, desc.cmin, desc.cmax)
+
+
+def _angles(gammas, betas):
+    g = np.ascontiguousarray(np.asarray(gammas, dtype=np.float64).reshape(-1))
+    b = np.ascontiguousarray(np.asarray(betas, dtype=np.float64).reshape(-1))
+    if len(g) != len(b):
+        raise ValueError("gammas and betas must have the same length")
+    return g, b, g.ctypes.data_as(ct.POINTER(ct.c_double)), b.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+def new_state(n: int, dtype: str = "c128", device="cuda"):
+    torch = _torch()
+    return torch.empty(1 << n, dtype=torch.complex128 if dtype == "c128" else torch.complex64, device=device)
+
+
+def apply_layers(psi, cost: CostVector, gammas, betas, init: bool = True, expect: bool = False):
+    """S2+S3 in place; returns the device tensor [<C>, norm] when expect=True."""
+    torch = _torch()
+    _require_cuda(psi)
+    n = int(round(math.log2(psi.numel())))
+    g, b, gp, bp = _angles(gammas, betas)
+    dt = _dtype_code(psi)
+    ws_n = workspace_size(n, dt, OP_LAYERS, len(g), 0, cost.span)
+    ws = _workspace(ws_n, psi.device)
+    out = torch.empty(2, dtype=torch.float64, device=psi.device) if expect else None
+    cs = cost.struct()
+    _check(_lib.qaoa_apply_layers(n, dt, ct.c_void_p(psi.data_ptr()), ct.byref(cs), gp, bp, len(g), int(init),
+                                  ct.c_void_p(out.data_ptr() if out is not None else 0),
+                                  ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(_stream(psi.device))),
+           "apply_layers")
+    return out
+
+
+def expectation(psi, cost: CostVector):
+    """S4: device tensor [<C>, <psi|psi>]."""
+    torch = _torch()
+    _require_cuda(psi)
+    n = int(round(math.log2(psi.numel())))
+    dt = _dtype_code(psi)
+    ws = _workspace(workspace_size(n, dt, OP_EXPECTATION), psi.device)
+    out = torch.empty(2, dtype=torch.float64, device=psi.device)
+    cs = cost.struct()
+    _check(_lib.qaoa_expectation(n, dt, ct.c_void_p(psi.data_ptr()), ct.byref(cs), ct.c_void_p(out.data_ptr()),
+                                 ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(_stream(psi.device))),
+           "expectation")
+    return out
+
+
+def sample(psi, cost: CostVector, shots: int, seed: int):
+    """S5+S6: (z uint64 as int64 tensor, cost float64 tensor) on the device, in draw order."""
+    torch = _torch()
+    _require_cuda(psi)
+    n = int(round(math.log2(psi.numel())))
+    dt = _dtype_code(psi)
+    ws = _workspace(workspace_size(n, dt, OP_SAMPLE, 0, shots), psi.device)
+    z = torch.empty(max(shots, 1), dtype=torch.int64, device=psi.device)
+    cz = torch.empty(max(shots, 1), dtype=torch.float64, device=psi.device)
+    cs = cost.struct()
+    _check(_lib.qaoa_sample(n, dt, ct.c_void_p(psi.data_ptr()), ct.byref(cs), shots, ct.c_uint64(seed & (2**64 - 1)),
+                            ct.c_void_p(z.data_ptr()), ct.c_void_p(cz.data_ptr()), ct.c_void_p(ws.data_ptr()),
+                            ws.numel(), ct.c_void_p(_stream(psi.device))), "sample")
+    return z[:shots], cz[:shots]
+
+
+def gradient(psi, lam, cost: CostVector, gammas, betas):
+    """S7: device tensor [E, norm, dE/dgamma_1..p, dE/dbeta_1..p] (psi ends uncomputed)."""
+    torch = _torch()
+    _require_cuda(psi, lam)
+    n = int(round(math.log2(psi.numel())))
+    g, b, gp, bp = _angles(gammas, betas)
+    dt = _dtype_code(psi)
+    if lam.dtype != psi.dtype or lam.numel() != psi.numel():
+        raise ValueError("lambda buffer must match psi")
+    ws = _workspace(workspace_size(n, dt, OP_GRADIENT, len(g), 0, cost.span), psi.device)
+    out = torch.empty(2 * len(g) + 2, dtype=torch.float64, device=psi.device)
+    cs = cost.struct()
+    _check(_lib.qaoa_gradient(n, dt, ct.c_void_p(psi.data_ptr()), ct.c_void_p(lam.data_ptr()), ct.byref(cs), gp, bp,
+                              len(g), ct.c_void_p(out.data_ptr()), ct.c_void_p(ws.data_ptr()), ws.numel(),
+                              ct.c_void_p(_stream(psi.device))), "gradient")
+    return out
+
+
+def launch_count() -> int:
+    return _lib.qaoa_launch_count()
+
+
+def launch_count_reset() -> None:
+    _lib.qaoa_launch_count_reset()
+
+
+def timing_enable(on: bool) -> None:
+    _check(_lib.qaoa_timing_enable(int(on)), "timing_enable")
+
+
+def timing_read():
+    """Per kernel class [sweep, cost, sample, other]: (ms, launches, algorithmic bytes), dropped."""
+    ms = (ct.c_double * 4)()
+    la = (ct.c_int64 * 4)()
+    by = (ct.c_double * 4)()
+    dr = ct.c_int64()
+    _check(_lib.qaoa_timing_read(ms, la, by, ct.byref(dr)), "timing_read")
+    return list(ms), list(la), list(by), dr.value
+
+
+def linear_ramp(p: int):
+    """Constant-speed schedule (Sec. II-A): gamma_i = i/p, beta_i = 1 - i/p for i = 1..p."""
+    i = np.arange(1, p + 1, dtype=np.float64)
+    return i / p, 1.0 - i / p

@@ -1,0 +1,564 @@
+// C ABI entry points: argument checks, sweep planning, workspace carving, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+namespace qaoa {
+
+// ------------------------------------------------------------ launch accounting
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+std::mutex g_timing_mu;
+bool g_timing_on = false;
+constexpr int kMaxTimed = 65536;
+struct TimedLaunch {
+  cudaEvent_t e0, e1;
+  int kind;
+  double bytes;
+};
+std::vector<TimedLaunch> g_timed;
+std::vector<cudaEvent_t> g_event_pool;
+int64_t g_dropped = 0;
+cudaEvent_t g_pending_begin = nullptr;
+
+cudaEvent_t pool_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+void note_launch(int kind, cudaStream_t s, bool begin, double bytes) {
+  if (begin) g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (!g_timing_on) return;
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  if (begin) {
+    if ((int)g_timed.size() >= kMaxTimed) {
+      ++g_dropped;
+      g_pending_begin = nullptr;
+      return;
+    }
+    g_pending_begin = pool_event();
+    cudaEventRecord(g_pending_begin, s);
+  } else if (g_pending_begin != nullptr) {
+    cudaEvent_t e1 = pool_event();
+    cudaEventRecord(e1, s);
+    g_timed.push_back({g_pending_begin, e1, kind, bytes});
+    g_pending_begin = nullptr;
+  }
+}
+
+// ------------------------------------------------------------ planning
+
+struct Group {
+  int j0, t, c;
+};
+
+// Cover the qubits with groups: the first holds bits [0, min(n, B)); the rest carry
+// c low bits for coalescing and as many group qubits as the tile allows, using the
+// fewest groups and then the most carried bits.
+static std::vector<Group> plan_groups(int n, int B) {
+  std::vector<Group> gs;
+  const int t0 = std::min(n, B);
+  gs.push_back({0, t0, 0});
+  int rem = n - t0;
+  if (rem <= 0) return gs;
+  int best_c = 0, best_k = 1 << 30;
+  for (int c = 0; c <= 3; ++c) {
+    const int per = B - c;
+    const int k = (rem + per - 1) / per;
+    if (k < best_k || (k == best_k && c > best_c)) {
+      best_k = k;
+      best_c = c;
+    }
+  }
+  int j = t0;
+  for (int i = 0; i < best_k; ++i) {
+    const int left = best_k - i;
+    const int t = (n - j + left - 1) / left;  // balanced split
+    gs.push_back({j, t, best_c});
+    j += t;
+  }
+  return gs;
+}
+
+struct Sweep {
+  int group;
+  bool init = false, load_psi = true, store_psi = true, load_lam = false, store_lam = false, two = false;
+  std::vector<uint32_t> ops;
+  std::vector<int> red_slot;  // per accumulator
+};
+
+static int64_t tiles_of(const Group& g, int n) { return 1ll << (n - g.t - g.c); }
+
+constexpr int kGridCap = 2048;
+
+static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+static size_t partial_bytes(int nout) { return round256((size_t)nout * kMaxContrib * kGridCap * sizeof(double)); }
+static size_t table_bytes(int dtype, int p, int64_t span) {
+  if (span <= 0 || span > QAOA_MAX_TABLE_SPAN || p <= 0) return 0;
+  return round256((size_t)p * span * (dtype == QAOA_C128 ? 16 : 8));
+}
+
+struct Ctx {
+  int n, dtype;
+  const qaoa_cost_t* cost;
+  cudaStream_t s;
+  char* ws;
+  size_t ws_bytes;
+};
+
+static int cuda_status(cudaError_t e) { return e == cudaSuccess ? QAOA_OK : QAOA_ERR_CUDA; }
+
+// Run a list of sweeps with one shared grid, then reduce the partials into out[0..nout).
+static int run_sweeps(const Ctx& c, std::vector<Sweep>& sw, const std::vector<Group>& gs, void* psi,
+                      void* lam, const double* gamma, const double* beta, int p, int nout,
+                      const std::vector<int>& ncontrib, double* out) {
+  int64_t max_tiles = 1;
+  for (const Sweep& s : sw) max_tiles = std::max(max_tiles, tiles_of(gs[s.group], c.n));
+  int grid = sweep_grid(c.dtype, max_tiles);
+  grid = std::min(grid, kGridCap);
+  char* p_ws = c.ws;
+  double* partials = nullptr;
+  if (nout > 0) {
+    partials = (double*)p_ws;
+    p_ws += partial_bytes(nout);
+  }
+  const void* table = nullptr;
+  int64_t cmin = 0, span = 0;
+  const bool int_cost = c.cost->dtype == QAOA_COST_I32;
+  if (int_cost && c.cost->cmax >= c.cost->cmin && p > 0) {
+    const int64_t sp = c.cost->cmax - c.cost->cmin + 1;
+    if (sp <= QAOA_MAX_TABLE_SPAN) {
+      span = sp;
+      cmin = c.cost->cmin;
+      table = p_ws;
+      int rc = cuda_status(launch_phase_table(c.dtype, gamma, p, cmin, span, (void*)table, c.s));
+      if (rc) return rc;
+      p_ws += table_bytes(c.dtype, p, span);
+    }
+  }
+  for (const Sweep& s : sw) {
+    SweepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = psi;
+    a.lam = s.two ? lam : nullptr;
+    a.C = c.cost->C_dev;
+    a.cost_dtype = c.cost->dtype;
+    const Group& g = gs[s.group];
+    a.g = {c.n, g.j0, g.t, g.c, tiles_of(g, c.n)};
+    a.init_plus = s.init;
+    a.load_psi = s.load_psi;
+    a.store_psi = s.store_psi;
+    a.load_lam = s.load_lam;
+    a.store_lam = s.store_lam;
+    if ((int)s.ops.size() > kMaxOps) return QAOA_ERR_UNSUPPORTED;
+    a.nops = (int)s.ops.size();
+    for (size_t k = 0; k < s.ops.size(); ++k) a.ops[k] = s.ops[k];
+    for (int l = 0; l < p; ++l) {
+      a.gamma[l] = gamma[l];
+      a.cosb[l] = std::cos(beta[l]);
+      a.sinb[l] = std::sin(beta[l]);
+    }
+    a.phase_table = table;
+    a.cmin = cmin;
+    a.span = span;
+    a.nred = (int)s.red_slot.size();
+    if (a.nred > kMaxAcc) return QAOA_ERR_UNSUPPORTED;
+    for (int r = 0; r < a.nred; ++r) a.red_slot[r] = s.red_slot[r];
+    a.partials = partials;
+    a.grid = grid;
+    {
+      const double S = c.dtype == QAOA_C128 ? 16.0 : 8.0;
+      const double cb = c.cost->dtype == QAOA_COST_I32 ? 4.0 : 8.0;
+      bool reads_c = false;
+      for (uint32_t op : s.ops) {
+        const uint32_t k = op & 0xff;
+        reads_c |= (k == OP_PHASE || k == OP_LAMBDA || k == OP_RED_EXPECT || k == OP_RED_CTERM);
+      }
+      const double per = S * ((s.load_psi && !s.init ? 1 : 0) + (s.store_psi ? 1 : 0) +
+                              (s.two && s.load_lam ? 1 : 0) + (s.two && s.store_lam ? 1 : 0)) +
+                         (reads_c ? cb : 0.0);
+      a.algo_bytes = per * (double)(1ull << c.n);
+    }
+    int rc = cuda_status(launch_sweep(c.dtype, a, c.s));
+    if (rc) return rc;
+  }
+  if (nout > 0) {
+    ReducePlan r;
+    std::memset(&r, 0, sizeof(r));
+    r.nout = nout;
+    r.grid = grid;
+    for (int o = 0; o < nout; ++o) r.ncontrib[o] = ncontrib[o];
+    int rc = cuda_status(launch_reduce(r, partials, out, c.s));
+    if (rc) return rc;
+  }
+  return QAOA_OK;
+}
+
+// Sweep schedule of p forward layers.  Layer l visits the groups in increasing
+// order for even l and decreasing order for odd l, so the last group of one layer
+// is the first of the next and the two share a sweep (phase applied in between).
+static void plan_forward(int k, int p, bool init, std::vector<Sweep>& sw) {
+  for (int l = 0; l < p; ++l) {
+    for (int idx = 0; idx < k; ++idx) {
+      const int gi = (l % 2 == 0) ? idx : k - 1 - idx;
+      if (idx == 0 && l > 0) {
+        sw.back().ops.push_back(make_op(OP_PHASE, F_PSI, l));
+        sw.back().ops.push_back(make_op(OP_MIX, F_PSI, l));
+        continue;
+      }
+      Sweep s;
+      s.group = gi;
+      if (l == 0 && idx == 0) {
+        s.init = init;
+        s.load_psi = !init;
+        s.ops.push_back(make_op(OP_PHASE, F_PSI, 0));
+      }
+      s.ops.push_back(make_op(OP_MIX, F_PSI, l));
+      sw.push_back(s);
+    }
+  }
+}
+
+static bool valid_dtype(int d) { return d == QAOA_C128 || d == QAOA_C64; }
+static bool valid_cost(const qaoa_cost_t* c) {
+  return c != nullptr && c->C_dev != nullptr && (c->dtype == QAOA_COST_I32 || c->dtype == QAOA_COST_F64);
+}
+static bool angles_ok(const double* g, const double* b, int p) {
+  if (p < 0 || p > QAOA_MAX_P) return false;
+  if (p > 0 && (g == nullptr || b == nullptr)) return false;
+  for (int l = 0; l < p; ++l)
+    if (!std::isfinite(g[l]) || !std::isfinite(b[l])) return false;
+  return true;
+}
+
+}  // namespace qaoa
+
+using namespace qaoa;
+
+extern "C" {
+
+int qaoa_version(void) { return 100; }
+
+const char* qaoa_strerror(int status) {
+  switch (status) {
+    case QAOA_OK: return "ok";
+    case QAOA_ERR_INVALID_ARG: return "invalid argument";
+    case QAOA_ERR_UNSUPPORTED: return "unsupported size or option";
+    case QAOA_ERR_CUDA: return "CUDA error";
+    case QAOA_ERR_TIMEOUT: return "device-side wait timed out";
+    case QAOA_ERR_WORKSPACE: return "workspace too small";
+    default: return "unknown status";
+  }
+}
+
+int qaoa_graph_check(const qaoa_graph_t* g, int64_t* cmin, int64_t* cmax) {
+  if (g == nullptr || g->n < 1 || g->n > QAOA_MAX_N || g->m < 0) return QAOA_ERR_INVALID_ARG;
+  if (g->m > 0 && g->uv == nullptr) return QAOA_ERR_INVALID_ARG;
+  if (g->weight_kind != QAOA_WEIGHT_INT && g->weight_kind != QAOA_WEIGHT_F64) return QAOA_ERR_INVALID_ARG;
+  if (g->m > (int64_t)g->n * (g->n - 1) / 2) return QAOA_ERR_INVALID_ARG;
+  std::set<std::pair<int, int>> seen;
+  double sum_abs = 0.0;
+  int64_t neg = 0, pos = 0;
+  for (int64_t e = 0; e < g->m; ++e) {
+    const int u = g->uv[2 * e], v = g->uv[2 * e + 1];
+    if (u < 0 || v < 0 || u >= g->n || v >= g->n || u == v) return QAOA_ERR_INVALID_ARG;
+    if (!seen.insert({std::min(u, v), std::max(u, v)}).second) return QAOA_ERR_INVALID_ARG;
+    const double w = g->w ? g->w[e] : 1.0;
+    if (!std::isfinite(w)) return QAOA_ERR_INVALID_ARG;
+    sum_abs += std::fabs(w);
+    if (g->weight_kind == QAOA_WEIGHT_INT) {
+      if (w != std::floor(w) || std::fabs(w) >= 2147483648.0) return QAOA_ERR_INVALID_ARG;
+      if (w < 0) neg += (int64_t)w; else pos += (int64_t)w;
+    }
+  }
+  if (g->weight_kind == QAOA_WEIGHT_INT && sum_abs >= 2147483648.0) return QAOA_ERR_INVALID_ARG;
+  if (g->weight_kind == QAOA_WEIGHT_F64 && !(sum_abs < 1e300)) return QAOA_ERR_INVALID_ARG;
+  if (cmin) *cmin = g->weight_kind == QAOA_WEIGHT_INT ? neg : 1;
+  if (cmax) *cmax = g->weight_kind == QAOA_WEIGHT_INT ? pos : 0;
+  return QAOA_OK;
+}
+
+int qaoa_workspace_size(int n, int dtype, int op, int p, int64_t shots, int64_t cost_span, size_t* bytes) {
+  if (bytes == nullptr || n < 1 || n > QAOA_MAX_N || !valid_dtype(dtype)) return QAOA_ERR_INVALID_ARG;
+  if (p < 0 || p > QAOA_MAX_P || shots < 0 || cost_span < 0) return QAOA_ERR_INVALID_ARG;
+  size_t b = 0;
+  switch (op) {
+    case QAOA_OP_COST: b = 0; break;
+    case QAOA_OP_LAYERS: b = partial_bytes(2) + table_bytes(dtype, p, cost_span); break;
+    case QAOA_OP_EXPECTATION: b = partial_bytes(2) + 256; break;
+    case QAOA_OP_SAMPLE: b = round256(sample_ws_bytes(n, dtype)); break;
+    case QAOA_OP_GRADIENT: b = partial_bytes(2 * p + 2) + table_bytes(dtype, p, cost_span); break;
+    default: return QAOA_ERR_INVALID_ARG;
+  }
+  *bytes = b;
+  return QAOA_OK;
+}
+
+int qaoa_cost_vector(const qaoa_graph_t* g, void* C_dev, int cost_dtype, qaoa_cost_t* desc, void* stream) {
+  int64_t cmin = 0, cmax = 0;
+  int rc = qaoa_graph_check(g, &cmin, &cmax);
+  if (rc) return rc;
+  if (C_dev == nullptr || (cost_dtype != QAOA_COST_I32 && cost_dtype != QAOA_COST_F64)) return QAOA_ERR_INVALID_ARG;
+  if (cost_dtype == QAOA_COST_I32 && g->weight_kind != QAOA_WEIGHT_INT) return QAOA_ERR_INVALID_ARG;
+  CostArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = g->n;
+  a.lo_bits = std::min(g->n, 10);
+  a.cost_dtype = cost_dtype;
+  a.integer = g->weight_kind == QAOA_WEIGHT_INT;
+  a.C = C_dev;
+  double sum_abs = 0.0;
+  for (int64_t e = 0; e < g->m; ++e) sum_abs += std::fabs(g->w ? g->w[e] : 1.0);
+  if (!a.integer) {
+    // fixed point: every partial sum is bounded by sum|w|, keep it below 2^62
+    int e2 = 0;
+    std::frexp(sum_abs + 1.0, &e2);  // sum_abs + 1 < 2^e2
+    a.fixed_shift = 62 - e2;
+  }
+  for (int64_t e = 0; e < g->m; ++e) {
+    const int u = g->uv[2 * e], v = g->uv[2 * e + 1];
+    const double w = g->w ? g->w[e] : 1.0;
+    const int64_t q = a.integer ? (int64_t)w : (int64_t)std::llrint(std::ldexp(w, a.fixed_shift));
+    a.wi[u][v] = q;
+    a.wi[v][u] = q;
+  }
+  rc = cuda_status(launch_cost(a, (cudaStream_t)stream));
+  if (rc) return rc;
+  if (desc) {
+    desc->C_dev = C_dev;
+    desc->dtype = cost_dtype;
+    desc->cmin = a.integer ? cmin : 1;
+    desc->cmax = a.integer ? cmax : 0;
+  }
+  return QAOA_OK;
+}
+
+int qaoa_apply_layers(int n, int dtype, void* psi_dev, const qaoa_cost_t* cost, const double* gamma,
+                      const double* beta, int p, int init, double* expect_dev, void* ws_dev, size_t ws_bytes,
+                      void* stream) {
+  if (n < 1 || n > QAOA_MAX_N || !valid_dtype(dtype) || psi_dev == nullptr) return QAOA_ERR_INVALID_ARG;
+  if (!angles_ok(gamma, beta, p) || (init != 0 && init != 1)) return QAOA_ERR_INVALID_ARG;
+  if ((p > 0 || expect_dev) && !valid_cost(cost)) return QAOA_ERR_INVALID_ARG;
+  const int64_t span = (cost && cost->dtype == QAOA_COST_I32 && cost->cmax >= cost->cmin)
+                           ? cost->cmax - cost->cmin + 1 : 0;
+  size_t need = 0;
+  qaoa_workspace_size(n, dtype, QAOA_OP_LAYERS, p, 0, span, &need);
+  if (need > 0 && (ws_dev == nullptr || ws_bytes < need)) return QAOA_ERR_WORKSPACE;
+  const std::vector<Group> gs = plan_groups(n, sweep_tile_bits(dtype));
+  std::vector<Sweep> sw;
+  plan_forward((int)gs.size(), p, init != 0, sw);
+  if (p == 0) {
+    if (!init && !expect_dev) return QAOA_OK;
+    Sweep s;
+    s.group = 0;
+    s.init = init != 0;
+    s.load_psi = !init;
+    s.store_psi = init != 0;
+    sw.push_back(s);
+  }
+  int nout = 0;
+  std::vector<int> ncontrib;
+  if (expect_dev) {
+    sw.back().ops.push_back(make_op(OP_RED_EXPECT, F_PSI, (uint32_t)sw.back().red_slot.size()));
+    sw.back().red_slot.push_back(0 * kMaxContrib + 0);
+    sw.back().red_slot.push_back(1 * kMaxContrib + 0);
+    nout = 2;
+    ncontrib = {1, 1};
+  }
+  qaoa_cost_t dummy{nullptr, QAOA_COST_F64, 1, 0};
+  Ctx c{n, dtype, cost ? cost : &dummy, (cudaStream_t)stream, (char*)ws_dev, ws_bytes};
+  return run_sweeps(c, sw, gs, psi_dev, nullptr, gamma, beta, p, nout, ncontrib, expect_dev);
+}
+
+int qaoa_expectation(int n, int dtype, const void* psi_dev, const qaoa_cost_t* cost, double* out_dev,
+                     void* ws_dev, size_t ws_bytes, void* stream) {
+  if (n < 1 || n > QAOA_MAX_N || !valid_dtype(dtype) || psi_dev == nullptr || out_dev == nullptr ||
+      !valid_cost(cost))
+    return QAOA_ERR_INVALID_ARG;
+  // the last 256 bytes of the reported size are for qaoa_expectation_host's result
+  if (ws_dev == nullptr || ws_bytes < partial_bytes(2)) return QAOA_ERR_WORKSPACE;
+  const std::vector<Group> gs = plan_groups(n, sweep_tile_bits(dtype));
+  std::vector<Sweep> sw(1);
+  sw[0].group = 0;
+  sw[0].store_psi = false;
+  sw[0].ops.push_back(make_op(OP_RED_EXPECT, F_PSI, 0));
+  sw[0].red_slot = {0 * kMaxContrib, 1 * kMaxContrib};
+  Ctx c{n, dtype, cost, (cudaStream_t)stream, (char*)ws_dev, ws_bytes};
+  return run_sweeps(c, sw, gs, (void*)psi_dev, nullptr, nullptr, nullptr, 0, 2, {1, 1}, out_dev);
+}
+
+int qaoa_expectation_host(int n, int dtype, const void* psi_dev, const qaoa_cost_t* cost, double* out_host,
+                          void* ws_dev, size_t ws_bytes, void* stream) {
+  if (out_host == nullptr) return QAOA_ERR_INVALID_ARG;
+  size_t need = 0;
+  if (qaoa_workspace_size(n, dtype, QAOA_OP_EXPECTATION, 0, 0, 0, &need)) return QAOA_ERR_INVALID_ARG;
+  if (ws_dev == nullptr || ws_bytes < need) return QAOA_ERR_WORKSPACE;
+  double* out_dev = (double*)((char*)ws_dev + partial_bytes(2));
+  int rc = qaoa_expectation(n, dtype, psi_dev, cost, out_dev, ws_dev, partial_bytes(2), stream);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(out_host, out_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return QAOA_ERR_CUDA;
+  return cuda_status(cudaStreamSynchronize(s));
+}
+
+int qaoa_sample(int n, int dtype, const void* psi_dev, const qaoa_cost_t* cost, int64_t shots, uint64_t seed,
+                uint64_t* z_dev, double* cost_dev, void* ws_dev, size_t ws_bytes, void* stream) {
+  if (n < 1 || n > QAOA_MAX_N || !valid_dtype(dtype) || psi_dev == nullptr || !valid_cost(cost) || shots < 0)
+    return QAOA_ERR_INVALID_ARG;
+  if (shots > 0 && (z_dev == nullptr || cost_dev == nullptr)) return QAOA_ERR_INVALID_ARG;
+  size_t need = 0;
+  qaoa_workspace_size(n, dtype, QAOA_OP_SAMPLE, 0, shots, 0, &need);
+  if (ws_dev == nullptr || ws_bytes < need) return QAOA_ERR_WORKSPACE;
+  SampleArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.dtype = dtype;
+  a.psi = psi_dev;
+  a.C = cost->C_dev;
+  a.cost_dtype = cost->dtype;
+  a.shots = shots;
+  a.seed = seed;
+  a.z = z_dev;
+  a.cost = cost_dev;
+  a.leaf = (double*)ws_dev;
+  return cuda_status(launch_sample(a, (cudaStream_t)stream));
+}
+
+int qaoa_sample_host(int n, int dtype, const void* psi_dev, const qaoa_cost_t* cost, int64_t shots, uint64_t seed,
+                     uint64_t* z_dev, double* cost_dev, uint64_t* z_host, double* cost_host, void* ws_dev,
+                     size_t ws_bytes, void* stream) {
+  if (shots > 0 && (z_host == nullptr || cost_host == nullptr)) return QAOA_ERR_INVALID_ARG;
+  int rc = qaoa_sample(n, dtype, psi_dev, cost, shots, seed, z_dev, cost_dev, ws_dev, ws_bytes, stream);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (shots > 0) {
+    if (cudaMemcpyAsync(z_host, z_dev, shots * sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return QAOA_ERR_CUDA;
+    if (cudaMemcpyAsync(cost_host, cost_dev, shots * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return QAOA_ERR_CUDA;
+  }
+  return cuda_status(cudaStreamSynchronize(s));
+}
+
+int qaoa_gradient(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost, const double* gamma,
+                  const double* beta, int p, double* out_dev, void* ws_dev, size_t ws_bytes, void* stream) {
+  if (n < 1 || n > QAOA_MAX_N || !valid_dtype(dtype) || psi_dev == nullptr || lambda_dev == nullptr ||
+      out_dev == nullptr || !valid_cost(cost) || !angles_ok(gamma, beta, p) || p < 1)
+    return QAOA_ERR_INVALID_ARG;
+  if (psi_dev == lambda_dev) return QAOA_ERR_INVALID_ARG;
+  const int64_t span = (cost->dtype == QAOA_COST_I32 && cost->cmax >= cost->cmin) ? cost->cmax - cost->cmin + 1 : 0;
+  size_t need = 0;
+  qaoa_workspace_size(n, dtype, QAOA_OP_GRADIENT, p, 0, span, &need);
+  if (ws_dev == nullptr || ws_bytes < need) return QAOA_ERR_WORKSPACE;
+  const std::vector<Group> gs = plan_groups(n, sweep_tile_bits(dtype));
+  const int k = (int)gs.size();
+  std::vector<Sweep> sw;
+  plan_forward(k, p, true, sw);
+  // outputs: 0 = E, 1 = norm, 2 + l = dE/dgamma_l, 2 + p + l = dE/dbeta_l
+  const int nout = 2 * p + 2;
+  std::vector<int> ncontrib(nout, 0);
+  auto add_red = [&](Sweep& s, uint32_t kind, uint32_t flags, int out0, int outs) {
+    const uint32_t acc = (uint32_t)s.red_slot.size();
+    s.ops.push_back(make_op(kind, flags, acc));
+    for (int i = 0; i < outs; ++i) {
+      s.red_slot.push_back((out0 + i) * kMaxContrib + ncontrib[out0 + i]);
+      ncontrib[out0 + i]++;
+    }
+  };
+  Sweep* cur = &sw.back();
+  cur->two = true;
+  cur->store_lam = true;
+  cur->ops.push_back(make_op(OP_LAMBDA, 0, 0));
+  add_red(*cur, OP_RED_EXPECT, F_PSI, 0, 2);
+  for (int l = p - 1; l >= 0; --l) {
+    const int first = cur->group;
+    for (int idx = 0; idx < k; ++idx) {
+      const int gi = (first == 0) ? idx : k - 1 - idx;
+      if (idx > 0) {
+        Sweep s;
+        s.group = gi;
+        s.two = true;
+        s.load_lam = true;
+        s.store_lam = true;
+        sw.push_back(s);
+        cur = &sw.back();
+      }
+      add_red(*cur, OP_RED_XTERM, F_PSI | F_LAM, 2 + p + l, 1);
+      cur->ops.push_back(make_op(OP_MIX, F_PSI | F_LAM | F_SIGN, l));
+    }
+    add_red(*cur, OP_RED_CTERM, F_PSI | F_LAM, 2 + l, 1);
+    cur->ops.push_back(make_op(OP_PHASE, F_PSI | F_LAM | F_SIGN, l));
+  }
+  cur->store_lam = false;
+  for (int o = 0; o < nout; ++o)
+    if (ncontrib[o] > kMaxContrib) return QAOA_ERR_UNSUPPORTED;
+  Ctx c{n, dtype, cost, (cudaStream_t)stream, (char*)ws_dev, ws_bytes};
+  return run_sweeps(c, sw, gs, psi_dev, lambda_dev, gamma, beta, p, nout, ncontrib, out_dev);
+}
+
+int qaoa_gradient_host(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,
+                       const double* gamma, const double* beta, int p, double* out_dev, double* out_host,
+                       void* ws_dev, size_t ws_bytes, void* stream) {
+  if (out_host == nullptr) return QAOA_ERR_INVALID_ARG;
+  int rc = qaoa_gradient(n, dtype, psi_dev, lambda_dev, cost, gamma, beta, p, out_dev, ws_dev, ws_bytes, stream);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(out_host, out_dev, (2 * p + 2) * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return QAOA_ERR_CUDA;
+  return cuda_status(cudaStreamSynchronize(s));
+}
+
+int64_t qaoa_launch_count(void) { return g_launches.load(); }
+void qaoa_launch_count_reset(void) { g_launches.store(0); }
+
+int qaoa_timing_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  g_timing_on = on != 0;
+  return QAOA_OK;
+}
+
+int qaoa_timing_read(double* ms, int64_t* launches, double* bytes, int64_t* dropped) {
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  for (int k = 0; k < 4; ++k) {
+    if (ms) ms[k] = 0.0;
+    if (launches) launches[k] = 0;
+    if (bytes) bytes[k] = 0.0;
+  }
+  int rc = QAOA_OK;
+  for (TimedLaunch& t : g_timed) {
+    if (cudaEventSynchronize(t.e1) != cudaSuccess) rc = QAOA_ERR_CUDA;
+    float f = 0.f;
+    if (cudaEventElapsedTime(&f, t.e0, t.e1) != cudaSuccess) rc = QAOA_ERR_CUDA;
+    if (t.kind >= 0 && t.kind < 4) {
+      if (ms) ms[t.kind] += f;
+      if (launches) launches[t.kind] += 1;
+      if (bytes) bytes[t.kind] += t.bytes;
+    }
+    g_event_pool.push_back(t.e0);
+    g_event_pool.push_back(t.e1);
+  }
+  g_timed.clear();
+  if (dropped) *dropped = g_dropped;
+  g_dropped = 0;
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// S1 — cost vector C(z) of a weighted MaxCut instance over all 2^n bitstrings
+// ("precomputation of the cost Hamiltonian", Sec. I and Sec. IV-A; bit order of Eq. 3).
+//
+// Split z into its low L bits x and high bits h.  Every edge is low-low, high-high
+// or low-high, and for a low-high edge (u low, v high)
+//   w [x_u != h_v] = w h_v + x_u w (1 - 2 h_v),
+// so C(z) = A[x] + K(h) + sum_{u < L} x_u a_u(h) with
+//   A[x]   = sum over low-low edges of w [x_u != x_v]        (one table per block),
+//   K(h)   = sum over high-high edges of w [h_u != h_v] + sum over low-high edges of w h_v,
+//   a_u(h) = sum over high neighbours v of u of w_uv (1 - 2 h_v).
+// A block builds A once in shared memory, then walks its high parts h; per element
+// the work is one table read plus at most L adds.  Integer weights accumulate
+// exactly in int64 (stored as int32 or float64).  Float weights are quantised once to
+// a common fixed point (int64, value * 2^shift), summed exactly, and rounded once to
+// float64 at the store.
+#include "internal.h"
+
+namespace qaoa {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxLowBits = 12;
+
+__global__ void __launch_bounds__(kThreads) cost_kernel(const __grid_constant__ CostArgs a) {
+  __shared__ long long A[1 << kMaxLowBits];
+  __shared__ long long au[kMaxLowBits];
+  __shared__ long long Kh;
+  const int L = a.lo_bits;
+  const uint32_t X = 1u << L;
+  // low-low table
+  for (uint32_t x = threadIdx.x; x < X; x += kThreads) {
+    long long s = 0;
+    for (int u = 0; u < L; ++u)
+      for (int v = u + 1; v < L; ++v)
+        if (((x >> u) ^ (x >> v)) & 1) s += a.wi[u][v];
+    A[x] = s;
+  }
+  const int64_t H = 1ll << (a.n - L);
+  for (int64_t h = blockIdx.x; h < H; h += gridDim.x) {
+    __syncthreads();
+    if (threadIdx.x < (unsigned)L) {
+      const int u = threadIdx.x;
+      long long s = 0;
+      for (int v = L; v < a.n; ++v) {
+        const long long w = a.wi[u][v];
+        s += ((h >> (v - L)) & 1) ? -w : w;
+      }
+      au[u] = s;
+    } else if (threadIdx.x == (unsigned)L) {
+      long long s = 0;
+      for (int u = L; u < a.n; ++u) {
+        const int hu = (h >> (u - L)) & 1;
+        for (int v = u + 1; v < a.n; ++v)
+          if (hu ^ ((h >> (v - L)) & 1)) s += a.wi[u][v];
+        if (hu)
+          for (int v = 0; v < L; ++v) s += a.wi[v][u];
+      }
+      Kh = s;
+    }
+    __syncthreads();
+    const uint64_t zbase = (uint64_t)h << L;
+    for (uint32_t x = threadIdx.x; x < X; x += kThreads) {
+      long long c = A[x] + Kh;
+      for (int u = 0; u < L; ++u)
+        if ((x >> u) & 1) c += au[u];
+      const uint64_t z = zbase | x;
+      if (a.cost_dtype == QAOA_COST_I32) {
+        ((int*)a.C)[z] = (int)c;
+      } else if (a.integer) {
+        ((double*)a.C)[z] = (double)c;
+      } else {
+        ((double*)a.C)[z] = ldexp((double)c, -a.fixed_shift);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_cost(const CostArgs& a, cudaStream_t s) {
+  const int64_t H = 1ll << (a.n - a.lo_bits);
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t cap = (int64_t)sms * 4;
+  const int grid = (int)(H < cap ? H : cap);
+  note_launch(1, s, true);
+  cost_kernel<<<grid, kThreads, 0, s>>>(a);
+  note_launch(1, s, false, (double)(1ull << a.n) * (a.cost_dtype == QAOA_COST_I32 ? 4.0 : 8.0));
+  return cudaGetLastError();
+}
+
+}  // namespace qaoa

@@ -1,0 +1,106 @@
+"""Host-side checks of the C ABI: the library loads, exports every declared symbol,
+and rejects bad input before any GPU work (no GPU needed)."""
+import ctypes as ct
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+import paper_2407_13012_gb300 as q
+
+HEADERS = sorted((Path(__file__).resolve().parent.parent / "include").glob("*.h"))
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
+        names |= set(re.findall(r"\b(qaoa_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_functions()
+    assert len(names) >= 16
+    lib = ct.CDLL(str(q._LIB_PATH))
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(q.EXPORTS) <= set(names)
+
+
+def test_version_and_strerror():
+    assert q.version() >= 100
+    for s in range(6):
+        assert q.lib.qaoa_strerror(s)
+    assert q.lib.qaoa_strerror(99) == b"unknown status"
+
+
+def check(n, edges, weights=None, integer=True):
+    g = q.Graph(n, np.asarray(edges).reshape(-1, 2), weights, integer)
+    st = g.as_struct()
+    lo, hi = ct.c_int64(), ct.c_int64()
+    return q.lib.qaoa_graph_check(ct.byref(st), ct.byref(lo), ct.byref(hi)), lo.value, hi.value
+
+
+def test_graph_check_accepts_and_bounds():
+    rc, lo, hi = check(4, [[0, 1], [1, 2], [2, 3]], [2.0, -3.0, 5.0])
+    assert rc == 0 and lo == -3 and hi == 7
+    rc, lo, hi = check(4, np.zeros((0, 2)))
+    assert rc == 0 and lo == 0 and hi == 0
+
+
+@pytest.mark.parametrize("n,edges,weights,integer", [
+    (4, [[0, 0]], None, True),             # loop
+    (4, [[0, 4]], None, True),             # vertex out of range
+    (4, [[0, -1]], None, True),            # negative vertex
+    (4, [[0, 1], [1, 0]], None, True),     # repeated edge, other orientation
+    (4, [[0, 1]], [1.5], True),            # non-integral weight under INT
+    (4, [[0, 1]], [float("nan")], False),  # non-finite weight
+    (4, [[0, 1]], [float("inf")], False),
+    (0, np.zeros((0, 2)), None, True),     # n out of range
+    (33, np.zeros((0, 2)), None, True),
+    (3, [[0, 1]], [2.0 ** 31], True),      # integer sum overflows int32
+])
+def test_graph_check_rejects(n, edges, weights, integer):
+    rc, _, _ = check(n, edges, weights, integer)
+    assert rc == q.QAOA_ERR_INVALID_ARG
+
+
+def test_workspace_sizes():
+    assert q.workspace_size(20, q.C128, q.OP_COST) == 0
+    a = q.workspace_size(20, q.C128, q.OP_LAYERS, 4, 0, 0)
+    b = q.workspace_size(20, q.C128, q.OP_LAYERS, 4, 0, 100)
+    assert b > a > 0 and b % 256 == 0
+    assert q.workspace_size(30, q.C64, q.OP_SAMPLE, 0, 10**6) > 8 * (1 << 20)
+    g2 = q.workspace_size(24, q.C128, q.OP_GRADIENT, 10, 0, 0)
+    assert g2 > q.workspace_size(24, q.C128, q.OP_GRADIENT, 1, 0, 0)
+    out = ct.c_size_t()
+    assert q.lib.qaoa_workspace_size(40, 0, 1, 1, 0, 0, ct.byref(out)) == q.QAOA_ERR_INVALID_ARG
+    assert q.lib.qaoa_workspace_size(10, 0, 1, 65, 0, 0, ct.byref(out)) == q.QAOA_ERR_INVALID_ARG
+    assert q.lib.qaoa_workspace_size(10, 7, 1, 1, 0, 0, ct.byref(out)) == q.QAOA_ERR_INVALID_ARG
+
+
+def test_calls_reject_bad_arguments_before_launch():
+    # argument errors are reported on the host; null pointers never reach a kernel
+    dp = ct.POINTER(ct.c_double)
+    g = np.array([0.1]), np.array([0.2])
+    gp, bp = g[0].ctypes.data_as(dp), g[1].ctypes.data_as(dp)
+    cost = q.CostT(0, q.COST_I32, 0, 1)
+    assert q.lib.qaoa_apply_layers(10, q.C128, None, ct.byref(cost), gp, bp, 1, 1, None, None, 0, None) \
+        == q.QAOA_ERR_INVALID_ARG
+    cost = q.CostT(1 << 20, q.COST_I32, 0, 1)  # non-null but never dereferenced on these paths
+    assert q.lib.qaoa_apply_layers(10, 5, ct.c_void_p(1 << 20), ct.byref(cost), gp, bp, 1, 1, None, None, 0,
+                                   None) == q.QAOA_ERR_INVALID_ARG
+    nan = np.array([np.nan])
+    assert q.lib.qaoa_apply_layers(10, q.C128, ct.c_void_p(1 << 20), ct.byref(cost), nan.ctypes.data_as(dp), bp, 1,
+                                   1, None, None, 0, None) == q.QAOA_ERR_INVALID_ARG
+    assert q.lib.qaoa_apply_layers(10, q.C128, ct.c_void_p(1 << 20), ct.byref(cost), gp, bp, 65, 1, None, None, 0,
+                                   None) == q.QAOA_ERR_INVALID_ARG
+    # workspace too small
+    assert q.lib.qaoa_apply_layers(10, q.C128, ct.c_void_p(1 << 20), ct.byref(cost), gp, bp, 1, 1, None,
+                                   ct.c_void_p(1 << 21), 16, None) == q.QAOA_ERR_WORKSPACE
+    assert q.lib.qaoa_gradient(10, q.C128, ct.c_void_p(1 << 20), ct.c_void_p(1 << 20), ct.byref(cost), gp, bp, 1,
+                               ct.c_void_p(1 << 22), ct.c_void_p(1 << 21), 1 << 30, None) == q.QAOA_ERR_INVALID_ARG
+    assert q.lib.qaoa_sample(10, q.C128, ct.c_void_p(1 << 20), ct.byref(cost), -1, 0, None, None, None, 0, None) \
+        == q.QAOA_ERR_INVALID_ARG
