@@ -63,7 +63,8 @@ def workload_name(a):
 
 def make_instance(a):
     import synth
-    e, w, integer = synth.graph(a.family, a.n, a.seed, weights=a.weights, prob=0.1)
+    fam = "gnp" if (a.family == "reg3" and a.n % 2) else a.family  # 3-regular needs even n
+    e, w, integer = synth.graph(fam, a.n, a.seed, weights=a.weights, prob=0.1)
     gam, bet = synth.angles(a.p, a.seed)
     return e, w, integer, gam, bet
 

@@ -53,9 +53,8 @@ class CostT(ct.Structure):
 
 
 def _load() -> ct.CDLL:
-    if not _LIB_PATH.exists():
-        from . import _build
-        _build.build()
+    from . import _build
+    _build.build()  # no-op when the library matches the sources; raises if nvcc is missing
     lib = ct.CDLL(str(_LIB_PATH))
     vp, i32, i64, u64, dp, szp = ct.c_void_p, ct.c_int, ct.c_int64, ct.c_uint64, ct.POINTER(ct.c_double), ct.POINTER(ct.c_size_t)
     sig = {
