@@ -170,6 +170,28 @@ int qaoa_expectation_host(int n, int dtype, const void* psi_dev, const qaoa_cost
                           double* out_host, void* ws_dev, size_t ws_bytes, void* stream);
 
 /*
+ * qaoa_expectation without a workspace argument, for callers that cannot
+ * allocate device memory (they run inside an allocator or pool callback, on
+ * a teardown path, or inside a host that owns all device memory).  The paper
+ * has no counterpart; this is a deployment convenience.
+ *  Scratch: a fixed 256 KiB array in device global memory defined by the
+ *    library (reduction partials for up to 2048 blocks; enough for every n in
+ *    1..32).  Each GPU that loads the library holds it until the process exits.
+ *    The call allocates nothing: no cudaMalloc/cudaFree, no library allocator.
+ *  Set-up: the first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  Sharing: every call uses the same array; each call writes every scratch
+ *    entry it later reads, so no clearing is needed, but calls that overlap on
+ *    the GPU (different streams, or different host threads) race and must be
+ *    serialised by the caller.
+ *  Errors: as qaoa_expectation; QAOA_ERR_UNSUPPORTED if a size would need more
+ *    scratch than the array holds.
+ */
+int qaoa_expectation_noalloc(int n, int dtype, const void* psi_dev, const qaoa_cost_t* cost,
+                             double* out_dev, void* stream);
+
+/*
  * S5+S6 — draw `shots` bitstrings from |psi_z|^2 on the device (Sec. IV-D)
  * and return each with its objective value.  Uniforms: u_i (i = 0..shots-1)
  * is the i-th 53-bit uniform of the SplitMix64 counter stream keyed by

@@ -66,6 +66,7 @@ def _load() -> ct.CDLL:
         "qaoa_apply_layers": ([i32, i32, vp, ct.POINTER(CostT), dp, dp, i32, i32, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_expectation": ([i32, i32, vp, ct.POINTER(CostT), vp, vp, ct.c_size_t, vp], i32),
         "qaoa_expectation_host": ([i32, i32, vp, ct.POINTER(CostT), dp, vp, ct.c_size_t, vp], i32),
+        "qaoa_expectation_noalloc": ([i32, i32, vp, ct.POINTER(CostT), vp, vp], i32),
         "qaoa_sample": ([i32, i32, vp, ct.POINTER(CostT), i64, u64, vp, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_sample_host": ([i32, i32, vp, ct.POINTER(CostT), i64, u64, vp, vp, vp, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_gradient": ([i32, i32, vp, vp, ct.POINTER(CostT), dp, dp, i32, vp, vp, ct.c_size_t, vp], i32),
