@@ -43,14 +43,13 @@ def parse():
     ap.add_argument("--p", type=int, default=6)
     ap.add_argument("--shots", type=int, default=1_000_000)
     ap.add_argument("--family", default="reg3", choices=["reg3", "gnp"])
-    ap.add_argument("--weights", default=None, help="u01 | int (default: u01 for c128, int for c64)")
+    ap.add_argument("--weights", default="int", choices=["int", "u01"],
+                    help="integer weights {1..10} (int32 costs) or U(0,1) float64 weights")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
-    if a.weights is None:
-        a.weights = "u01" if a.dtype == "c128" else "int"
     return a
 
 

@@ -91,7 +91,7 @@ static std::vector<Group> plan_groups(int n, int B) {
   for (int i = 0; i < best_k; ++i) {
     const int left = best_k - i;
     const int t = (n - j + left - 1) / left;  // balanced split
-    gs.push_back({j, t, best_c});
+    gs.push_back({j, t, std::min(j, B - t)});  // carry as many low bits as fill the tile
     j += t;
   }
   return gs;
@@ -99,7 +99,10 @@ static std::vector<Group> plan_groups(int n, int B) {
 
 struct Sweep {
   int group;
-  bool init = false, load_psi = true, store_psi = true, load_lam = false, store_lam = false, two = false;
+  bool two = false;        // lambda buffer present (gradient backward part)
+  bool init = false;       // create |+> instead of loading
+  bool load_user = false;  // load psi in the caller's format
+  bool store_psi = true, store_user = false, load_lam = false, store_lam = false;
   std::vector<uint32_t> ops;
   std::vector<int> red_slot;  // per accumulator
 };
@@ -107,12 +110,22 @@ struct Sweep {
 static int64_t tiles_of(const Group& g, int n) { return 1ll << (n - g.t - g.c); }
 
 constexpr int kGridCap = 2048;
+constexpr size_t kScalarBytes = 256;                     // norm^2 (double), max|C| bits (u64)
+constexpr size_t kNormPartialBytes = 1024 * sizeof(double);
 
 static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 static size_t partial_bytes(int nout) { return round256((size_t)nout * kMaxContrib * kGridCap * sizeof(double)); }
-static size_t table_bytes(int dtype, int p, int64_t span) {
+static size_t phase_table_bytes(int dtype, int p, int64_t span) {
   if (span <= 0 || span > QAOA_MAX_TABLE_SPAN || p <= 0) return 0;
   return round256((size_t)p * span * (dtype == QAOA_C128 ? 16 : 8));
+}
+static size_t fx_table_bytes(int dtype, int p) {
+  if (dtype != QAOA_C128) return 0;
+  return round256((size_t)p * 196 * 16) + round256(3072 * 16);
+}
+static size_t layer_ws_bytes(int dtype, int p, int64_t span, int nout) {
+  return kScalarBytes + kNormPartialBytes + partial_bytes(nout) + phase_table_bytes(dtype, p, span) +
+         fx_table_bytes(dtype, p);
 }
 
 struct Ctx {
@@ -126,33 +139,84 @@ struct Ctx {
 static int cuda_status(cudaError_t e) { return e == cudaSuccess ? QAOA_OK : QAOA_ERR_CUDA; }
 
 // Run a list of sweeps with one shared grid, then reduce the partials into out[0..nout).
-static int run_sweeps(const Ctx& c, std::vector<Sweep>& sw, const std::vector<Group>& gs, void* psi,
+// Fixed-point (complex128) calls also get: the input scale from the norm of a loaded
+// user state, the lambda scale from max |C| (gradient), and the mixer/turn tables.
+static int run_sweeps(const Ctx& c, std::vector<Sweep>& sw, const std::vector<Group>& gs, int tile_bits, void* psi,
                       void* lam, const double* gamma, const double* beta, int p, int nout,
                       const std::vector<int>& ncontrib, double* out) {
+  const bool fx = c.dtype == QAOA_C128;
+  bool any_two = false, any_user_load = false;
   int64_t max_tiles = 1;
-  for (const Sweep& s : sw) max_tiles = std::max(max_tiles, tiles_of(gs[s.group], c.n));
-  int grid = sweep_grid(c.dtype, max_tiles);
+  int tmax = 1;
+  for (const Sweep& s : sw) {
+    max_tiles = std::max(max_tiles, tiles_of(gs[s.group], c.n));
+    any_two |= s.two;
+    any_user_load |= s.load_user;
+  }
+  for (const Group& g : gs) tmax = std::max(tmax, g.t);
+  const int cost_bytes = c.cost->C_dev == nullptr ? 0 : (c.cost->dtype == QAOA_COST_I32 ? 4 : 8);
+  int grid = sweep_grid(c.dtype, false, tile_bits, cost_bytes, max_tiles);
+  if (any_two) grid = std::min(grid, sweep_grid(c.dtype, true, tile_bits, cost_bytes, max_tiles));
   grid = std::min(grid, kGridCap);
+  // workspace carving
   char* p_ws = c.ws;
-  double* partials = nullptr;
-  if (nout > 0) {
-    partials = (double*)p_ws;
-    p_ws += partial_bytes(nout);
-  }
-  const void* table = nullptr;
-  int64_t cmin = 0, span = 0;
+  double* norm2 = (double*)p_ws;
+  unsigned long long* cmax_bits = (unsigned long long*)(p_ws + 8);
+  p_ws += kScalarBytes;
+  double* norm_part = (double*)p_ws;
+  p_ws += kNormPartialBytes;
+  double* partials = (double*)p_ws;
+  p_ws += partial_bytes(nout);
   const bool int_cost = c.cost->dtype == QAOA_COST_I32;
-  if (int_cost && c.cost->cmax >= c.cost->cmin && p > 0) {
-    const int64_t sp = c.cost->cmax - c.cost->cmin + 1;
-    if (sp <= QAOA_MAX_TABLE_SPAN) {
-      span = sp;
-      cmin = c.cost->cmin;
-      table = p_ws;
-      int rc = cuda_status(launch_phase_table(c.dtype, gamma, p, cmin, span, (void*)table, c.s));
-      if (rc) return rc;
-      p_ws += table_bytes(c.dtype, p, span);
-    }
+  int64_t cmin = 0, span = 0;
+  if (int_cost && c.cost->cmax >= c.cost->cmin && p > 0 && c.cost->cmax - c.cost->cmin + 1 <= QAOA_MAX_TABLE_SPAN) {
+    span = c.cost->cmax - c.cost->cmin + 1;
+    cmin = c.cost->cmin;
   }
+  void* phase_table = span > 0 ? p_ws : nullptr;
+  p_ws += phase_table_bytes(c.dtype, p, span);
+  void* d_table = fx ? p_ws : nullptr;
+  void* turn_table = fx ? p_ws + round256((size_t)p * 196 * 16) : nullptr;
+  p_ws += fx_table_bytes(c.dtype, p);
+  if ((size_t)(p_ws - c.ws) > c.ws_bytes) return QAOA_ERR_WORKSPACE;
+
+  if (p > 0 && (span > 0 || fx)) {
+    TableArgs t;
+    std::memset(&t, 0, sizeof(t));
+    t.fx = fx;
+    t.p = p;
+    t.cmin = cmin;
+    t.span = span;
+    for (int l = 0; l < p; ++l) {
+      t.gamma[l] = gamma[l];
+      t.beta[l] = beta[l];
+    }
+    t.phase = phase_table;
+    t.dtab = d_table;
+    t.turn = turn_table;
+    int rc = cuda_status(launch_tables(t, c.s));
+    if (rc) return rc;
+  }
+  if (fx && any_user_load) {  // input scale from |psi|^2 of the caller's state
+    int nb = 0;
+    int rc = cuda_status(launch_norm(psi, c.dtype, c.n, norm_part, &nb, c.s));
+    if (rc) return rc;
+    ReducePlan r;
+    std::memset(&r, 0, sizeof(r));
+    r.nout = 1;
+    r.grid = nb;
+    r.ncontrib[0] = 1;
+    r.scale[0] = 1.0;
+    rc = cuda_status(launch_reduce(r, norm_part, norm2, c.s));
+    if (rc) return rc;
+  }
+  if (fx && any_two) {  // lambda scale from max |C|
+    int rc = cuda_status(launch_cost_bound(c.cost->C_dev, c.cost->dtype == QAOA_COST_F64, c.n, cmax_bits, c.s));
+    if (rc) return rc;
+  }
+
+  const double amp0 = std::pow(2.0, -0.5 * c.n);
+  const int S = fx_shift_for(tmax);
   for (const Sweep& s : sw) {
     SweepArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -162,41 +226,57 @@ static int run_sweeps(const Ctx& c, std::vector<Sweep>& sw, const std::vector<Gr
     a.cost_dtype = c.cost->dtype;
     const Group& g = gs[s.group];
     a.g = {c.n, g.j0, g.t, g.c, tiles_of(g, c.n)};
-    a.init_plus = s.init;
-    a.load_psi = s.load_psi;
-    a.store_psi = s.store_psi;
+    a.tile_bits = tile_bits;
+    a.load_fmt = s.init ? 2 : (s.load_user ? 1 : 0);
+    a.store_fmt = !s.store_psi ? -1 : (s.store_user ? 1 : 0);
     a.load_lam = s.load_lam;
     a.store_lam = s.store_lam;
+    a.fx_shift = S;
+    a.init_fx = (long long)std::llrint(std::ldexp(amp0, S));
+    a.init_f32 = (float)amp0;
+    a.norm2_dev = (fx && any_user_load) ? norm2 : nullptr;
+    a.cmax_dev = (fx && any_two) ? cmax_bits : nullptr;
     if ((int)s.ops.size() > kMaxOps) return QAOA_ERR_UNSUPPORTED;
     a.nops = (int)s.ops.size();
-    for (size_t k = 0; k < s.ops.size(); ++k) a.ops[k] = s.ops[k];
+    bool reads_c = false;
+    for (size_t k = 0; k < s.ops.size(); ++k) {
+      a.ops[k] = s.ops[k];
+      const uint32_t kind = s.ops[k] & 0xff;
+      reads_c |= (kind == OP_PHASE || kind == OP_LAMBDA || kind == OP_RED_EXPECT || kind == OP_RED_CTERM);
+    }
+    a.needs_cost = reads_c;
     for (int l = 0; l < p; ++l) {
-      a.gamma[l] = gamma[l];
+      a.g2pi[l] = gamma[l] / (2.0 * 3.14159265358979323846);
       a.cosb[l] = std::cos(beta[l]);
       a.sinb[l] = std::sin(beta[l]);
     }
-    a.phase_table = table;
+    a.phase_table = phase_table;
     a.cmin = cmin;
     a.span = span;
+    a.smem_table_layer = -1;
+    if (phase_table != nullptr && span <= kSmemTable) {
+      for (uint32_t op : s.ops)
+        if ((op & 0xff) == OP_PHASE) {
+          a.smem_table_layer = (int)((op >> 16) & 0xff);
+          break;
+        }
+    }
+    a.d_table = d_table;
+    a.turn_table = turn_table;
     a.nred = (int)s.red_slot.size();
     if (a.nred > kMaxAcc) return QAOA_ERR_UNSUPPORTED;
     for (int r = 0; r < a.nred; ++r) a.red_slot[r] = s.red_slot[r];
     a.partials = partials;
     a.grid = grid;
     {
-      const double S = c.dtype == QAOA_C128 ? 16.0 : 8.0;
+      const double S_b = c.dtype == QAOA_C128 ? 16.0 : 8.0;
       const double cb = c.cost->dtype == QAOA_COST_I32 ? 4.0 : 8.0;
-      bool reads_c = false;
-      for (uint32_t op : s.ops) {
-        const uint32_t k = op & 0xff;
-        reads_c |= (k == OP_PHASE || k == OP_LAMBDA || k == OP_RED_EXPECT || k == OP_RED_CTERM);
-      }
-      const double per = S * ((s.load_psi && !s.init ? 1 : 0) + (s.store_psi ? 1 : 0) +
-                              (s.two && s.load_lam ? 1 : 0) + (s.two && s.store_lam ? 1 : 0)) +
+      const double per = S_b * ((s.init ? 0 : 1) + (s.store_psi ? 1 : 0) + (s.two && s.load_lam ? 1 : 0) +
+                                (s.two && s.store_lam ? 1 : 0)) +
                          (reads_c ? cb : 0.0);
       a.algo_bytes = per * (double)(1ull << c.n);
     }
-    int rc = cuda_status(launch_sweep(c.dtype, a, c.s));
+    int rc = cuda_status(launch_sweep(c.dtype, s.two, a, c.s));
     if (rc) return rc;
   }
   if (nout > 0) {
@@ -204,7 +284,10 @@ static int run_sweeps(const Ctx& c, std::vector<Sweep>& sw, const std::vector<Gr
     std::memset(&r, 0, sizeof(r));
     r.nout = nout;
     r.grid = grid;
-    for (int o = 0; o < nout; ++o) r.ncontrib[o] = ncontrib[o];
+    for (int o = 0; o < nout; ++o) {
+      r.ncontrib[o] = ncontrib[o];
+      r.scale[o] = 1.0;
+    }
     int rc = cuda_status(launch_reduce(r, partials, out, c.s));
     if (rc) return rc;
   }
@@ -227,7 +310,7 @@ static void plan_forward(int k, int p, bool init, std::vector<Sweep>& sw) {
       s.group = gi;
       if (l == 0 && idx == 0) {
         s.init = init;
-        s.load_psi = !init;
+        s.load_user = !init;
         s.ops.push_back(make_op(OP_PHASE, F_PSI, 0));
       }
       s.ops.push_back(make_op(OP_MIX, F_PSI, l));
@@ -301,10 +384,10 @@ int qaoa_workspace_size(int n, int dtype, int op, int p, int64_t shots, int64_t 
   size_t b = 0;
   switch (op) {
     case QAOA_OP_COST: b = 0; break;
-    case QAOA_OP_LAYERS: b = partial_bytes(2) + table_bytes(dtype, p, cost_span); break;
+    case QAOA_OP_LAYERS: b = layer_ws_bytes(dtype, p, cost_span, 2); break;
     case QAOA_OP_EXPECTATION: b = partial_bytes(2) + 256; break;
     case QAOA_OP_SAMPLE: b = round256(sample_ws_bytes(n, dtype)); break;
-    case QAOA_OP_GRADIENT: b = partial_bytes(2 * p + 2) + table_bytes(dtype, p, cost_span); break;
+    case QAOA_OP_GRADIENT: b = layer_ws_bytes(dtype, p, cost_span, 2 * p + 2); break;
     default: return QAOA_ERR_INVALID_ARG;
   }
   *bytes = b;
@@ -361,7 +444,8 @@ int qaoa_apply_layers(int n, int dtype, void* psi_dev, const qaoa_cost_t* cost, 
   size_t need = 0;
   qaoa_workspace_size(n, dtype, QAOA_OP_LAYERS, p, 0, span, &need);
   if (need > 0 && (ws_dev == nullptr || ws_bytes < need)) return QAOA_ERR_WORKSPACE;
-  const std::vector<Group> gs = plan_groups(n, sweep_tile_bits(dtype));
+  const int B = sweep_tile_bits(dtype, false);
+  const std::vector<Group> gs = plan_groups(n, B);
   std::vector<Sweep> sw;
   plan_forward((int)gs.size(), p, init != 0, sw);
   if (p == 0) {
@@ -369,14 +453,15 @@ int qaoa_apply_layers(int n, int dtype, void* psi_dev, const qaoa_cost_t* cost, 
     Sweep s;
     s.group = 0;
     s.init = init != 0;
-    s.load_psi = !init;
+    s.load_user = !init;
     s.store_psi = init != 0;
     sw.push_back(s);
   }
+  sw.back().store_user = true;
   int nout = 0;
   std::vector<int> ncontrib;
   if (expect_dev) {
-    sw.back().ops.push_back(make_op(OP_RED_EXPECT, F_PSI, (uint32_t)sw.back().red_slot.size()));
+    sw.back().ops.push_back(make_op(OP_RED_EXPECT, F_PSI, 0, (uint32_t)sw.back().red_slot.size()));
     sw.back().red_slot.push_back(0 * kMaxContrib + 0);
     sw.back().red_slot.push_back(1 * kMaxContrib + 0);
     nout = 2;
@@ -384,7 +469,7 @@ int qaoa_apply_layers(int n, int dtype, void* psi_dev, const qaoa_cost_t* cost, 
   }
   qaoa_cost_t dummy{nullptr, QAOA_COST_F64, 1, 0};
   Ctx c{n, dtype, cost ? cost : &dummy, (cudaStream_t)stream, (char*)ws_dev, ws_bytes};
-  return run_sweeps(c, sw, gs, psi_dev, nullptr, gamma, beta, p, nout, ncontrib, expect_dev);
+  return run_sweeps(c, sw, gs, B, psi_dev, nullptr, gamma, beta, p, nout, ncontrib, expect_dev);
 }
 
 int qaoa_expectation(int n, int dtype, const void* psi_dev, const qaoa_cost_t* cost, double* out_dev,
@@ -394,14 +479,25 @@ int qaoa_expectation(int n, int dtype, const void* psi_dev, const qaoa_cost_t* c
     return QAOA_ERR_INVALID_ARG;
   // the last 256 bytes of the reported size are for qaoa_expectation_host's result
   if (ws_dev == nullptr || ws_bytes < partial_bytes(2)) return QAOA_ERR_WORKSPACE;
-  const std::vector<Group> gs = plan_groups(n, sweep_tile_bits(dtype));
-  std::vector<Sweep> sw(1);
-  sw[0].group = 0;
-  sw[0].store_psi = false;
-  sw[0].ops.push_back(make_op(OP_RED_EXPECT, F_PSI, 0));
-  sw[0].red_slot = {0 * kMaxContrib, 1 * kMaxContrib};
-  Ctx c{n, dtype, cost, (cudaStream_t)stream, (char*)ws_dev, ws_bytes};
-  return run_sweeps(c, sw, gs, (void*)psi_dev, nullptr, nullptr, nullptr, 0, 2, {1, 1}, out_dev);
+  int grid = 0;
+  {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t need = ((1ll << n) + 255) / 256;
+    grid = (int)std::min<int64_t>(std::min<int64_t>(need, (int64_t)sms * 8), kGridCap);
+  }
+  double* partials = (double*)ws_dev;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = cuda_status(launch_expect(dtype, psi_dev, cost->C_dev, cost->dtype, n, partials, grid, s));
+  if (rc) return rc;
+  ReducePlan r;
+  std::memset(&r, 0, sizeof(r));
+  r.nout = 2;
+  r.grid = grid;
+  r.ncontrib[0] = r.ncontrib[1] = 1;
+  r.scale[0] = r.scale[1] = 1.0;
+  return cuda_status(launch_reduce(r, partials, out_dev, s));
 }
 
 int qaoa_expectation_host(int n, int dtype, const void* psi_dev, const qaoa_cost_t* cost, double* out_host,
@@ -468,26 +564,27 @@ int qaoa_gradient(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_
   size_t need = 0;
   qaoa_workspace_size(n, dtype, QAOA_OP_GRADIENT, p, 0, span, &need);
   if (ws_dev == nullptr || ws_bytes < need) return QAOA_ERR_WORKSPACE;
-  const std::vector<Group> gs = plan_groups(n, sweep_tile_bits(dtype));
+  const int B = sweep_tile_bits(dtype, true);
+  const std::vector<Group> gs = plan_groups(n, B);
   const int k = (int)gs.size();
   std::vector<Sweep> sw;
   plan_forward(k, p, true, sw);
   // outputs: 0 = E, 1 = norm, 2 + l = dE/dgamma_l, 2 + p + l = dE/dbeta_l
   const int nout = 2 * p + 2;
   std::vector<int> ncontrib(nout, 0);
-  auto add_red = [&](Sweep& s, uint32_t kind, uint32_t flags, int out0, int outs) {
+  auto new_acc = [&](Sweep& s, int out0, int outs) {
     const uint32_t acc = (uint32_t)s.red_slot.size();
-    s.ops.push_back(make_op(kind, flags, acc));
     for (int i = 0; i < outs; ++i) {
       s.red_slot.push_back((out0 + i) * kMaxContrib + ncontrib[out0 + i]);
       ncontrib[out0 + i]++;
     }
+    return acc;
   };
   Sweep* cur = &sw.back();
   cur->two = true;
   cur->store_lam = true;
   cur->ops.push_back(make_op(OP_LAMBDA, 0, 0));
-  add_red(*cur, OP_RED_EXPECT, F_PSI, 0, 2);
+  cur->ops.push_back(make_op(OP_RED_EXPECT, F_PSI, 0, new_acc(*cur, 0, 2)));
   for (int l = p - 1; l >= 0; --l) {
     const int first = cur->group;
     for (int idx = 0; idx < k; ++idx) {
@@ -501,17 +598,19 @@ int qaoa_gradient(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_
         sw.push_back(s);
         cur = &sw.back();
       }
-      add_red(*cur, OP_RED_XTERM, F_PSI | F_LAM, 2 + p + l, 1);
-      cur->ops.push_back(make_op(OP_MIX, F_PSI | F_LAM | F_SIGN, l));
+      cur->ops.push_back(make_op(OP_MIX, F_PSI | F_LAM | F_SIGN | F_XTERM, l, new_acc(*cur, 2 + p + l, 1)));
     }
-    add_red(*cur, OP_RED_CTERM, F_PSI | F_LAM, 2 + l, 1);
+    cur->ops.push_back(make_op(OP_RED_CTERM, F_PSI | F_LAM, l, new_acc(*cur, 2 + l, 1)));
     cur->ops.push_back(make_op(OP_PHASE, F_PSI | F_LAM | F_SIGN, l));
   }
   cur->store_lam = false;
+  cur->store_user = true;
   for (int o = 0; o < nout; ++o)
     if (ncontrib[o] > kMaxContrib) return QAOA_ERR_UNSUPPORTED;
+  for (const Sweep& s : sw)
+    if ((int)s.red_slot.size() > 255) return QAOA_ERR_UNSUPPORTED;
   Ctx c{n, dtype, cost, (cudaStream_t)stream, (char*)ws_dev, ws_bytes};
-  return run_sweeps(c, sw, gs, psi_dev, lambda_dev, gamma, beta, p, nout, ncontrib, out_dev);
+  return run_sweeps(c, sw, gs, B, psi_dev, lambda_dev, gamma, beta, p, nout, ncontrib, out_dev);
 }
 
 int qaoa_gradient_host(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,

@@ -19,27 +19,29 @@ namespace qaoa {
 // at any point of the program; RX mixers act on the group qubits only.
 
 enum OpKind : uint32_t {
-  OP_PHASE = 1,        // psi_z *= exp(-i s gamma_l C(z))           arg = layer, flag SIGN = inverse
-  OP_MIX = 2,          // RX(2 s beta_l) on every group qubit        arg = layer, flag SIGN = inverse
-  OP_LAMBDA = 3,       // lam := C psi
-  OP_RED_EXPECT = 4,   // partial += [sum C|psi|^2, sum |psi|^2]     arg = output index (two outputs)
-  OP_RED_XTERM = 5,    // partial += 2 Im sum_{j in group} <lam|X_j|psi>   arg = output index
-  OP_RED_CTERM = 6,    // partial += 2 Im <lam|C|psi>                arg = output index
+  OP_PHASE = 1,       // psi_z *= exp(-i s gamma_l C(z))                 flag SIGN = inverse
+  OP_MIX = 2,         // RX(2 s beta_l) on every group qubit              flag SIGN = inverse; flag XTERM:
+                      //   also accumulate 2 Im sum_{j in group} <lam|X_j|psi> into accumulator acc
+  OP_LAMBDA = 3,      // lam := C psi
+  OP_RED_EXPECT = 4,  // accumulators acc, acc + 1 += [sum C|psi|^2, sum |psi|^2]
+  OP_RED_CTERM = 6,   // accumulator acc += 2 Im <lam|C|psi>
 };
-enum OpFlags : uint32_t { F_PSI = 1u << 8, F_LAM = 1u << 9, F_SIGN = 1u << 10 };
+enum OpFlags : uint32_t { F_PSI = 1u << 8, F_LAM = 1u << 9, F_SIGN = 1u << 10, F_XTERM = 1u << 11 };
 
-inline uint32_t make_op(uint32_t kind, uint32_t flags, uint32_t arg) {
-  return kind | flags | (arg << 16);
+// op word: kind (bits 0-7) | flags (8-15) | layer (16-23) | accumulator (24-31)
+inline uint32_t make_op(uint32_t kind, uint32_t flags, uint32_t layer, uint32_t acc = 0) {
+  return kind | flags | (layer << 16) | (acc << 24);
 }
 
 constexpr int kMaxOps = 200;
 constexpr int kMaxAcc = 2 * QAOA_MAX_P + 2;  // reduction accumulators per sweep (double each)
 constexpr int kMaxContrib = 8;               // partial slots per output
+constexpr int kSmemTable = 1024;             // phase-table entries a sweep may keep in shared memory
 
 struct SweepGeom {
   int n;      // qubits
   int j0;     // first group qubit
-  int t;      // group qubits in the tile (j0 + t <= n), may be < tile bits for tiny n
+  int t;      // group qubits in the tile (j0 + t <= n)
   int c;      // low index bits carried in the tile (c <= j0), 0 for the first group
   int64_t tiles;  // number of tiles = 2^(n - t - c)
 };
@@ -49,21 +51,33 @@ struct SweepArgs {
   void* lam;
   const void* C;
   int cost_dtype;
+  int needs_cost;  // stage the cost tile in shared memory
   SweepGeom g;
-  int init_plus;   // create |+> instead of loading psi
-  int load_psi, store_psi, load_lam, store_lam;
+  int tile_bits;   // B of the kernel configuration
+  // state formats: load 0 = internal, 1 = user (complex128 / complex64), 2 = create |+>;
+  // store 0 = internal, 1 = user, -1 = none.  complex64 internal == user.
+  int load_fmt, store_fmt;
+  int load_lam, store_lam;
+  long long init_fx;  // |+> amplitude in fixed point
+  float init_f32;     // |+> amplitude in float32
+  int fx_shift;       // fixed-point scale S (value = integer * 2^-S)
+  const double* norm2_dev;             // optional: |psi|^2 of a user state (input scale)
+  const unsigned long long* cmax_dev;  // optional: bits of max |C| (lambda scale)
   int nops;
   uint32_t ops[kMaxOps];
-  // per layer angles, indexed by the op's layer argument
-  double gamma[QAOA_MAX_P];
+  // per layer angles, indexed by the op's layer field
+  double g2pi[QAOA_MAX_P];  // gamma / (2 pi)
   double cosb[QAOA_MAX_P];
   double sinb[QAOA_MAX_P];
-  // integer-cost phase tables: table + l * span holds exp(-i gamma_l c) for c = cmin + k
-  const void* phase_table;  // double2 (C128) or float2 (C64), NULL = compute sincos
+  // tables (workspace): integer-cost phases exp(-i gamma_l c) at [l * span + (c - cmin)];
+  // fixed point also mixer diagonals [(l * 14 + t) * 14 + k] and turn tables [3 * 1024]
+  const void* phase_table;
   int64_t cmin;
   int64_t span;
-  // reductions: accumulator r (the argument of a reduction op; OP_RED_EXPECT uses r and
-  // r + 1) is written to partials[red_slot[r] * grid + block], with
+  int smem_table_layer;  // layer whose table the kernel copies to shared memory (-1: none)
+  const void* d_table;
+  const void* turn_table;
+  // reductions: accumulator r is written to partials[red_slot[r] * grid + block],
   // red_slot = out * kMaxContrib + contrib
   int nred;
   int red_slot[kMaxAcc];
@@ -72,21 +86,38 @@ struct SweepArgs {
   double algo_bytes;  // HBM bytes this sweep must move (for timing reports)
 };
 
-// A reduction plan: out[o] = sum over contributions k < ncontrib[o] and blocks b of
-// partials[(o * kMaxContrib + k) * grid + b].
+// A reduction plan: out[o] = scale[o] * sum over contributions k < ncontrib[o] and
+// blocks b of partials[(o * kMaxContrib + k) * grid + b].
 struct ReducePlan {
   int nout;
   int grid;
   int ncontrib[2 * QAOA_MAX_P + 2];
+  double scale[2 * QAOA_MAX_P + 2];
+};
+
+struct TableArgs {
+  int fx;        // fixed point tables (complex128) or float32 (complex64)
+  int p;
+  int64_t cmin, span;  // integer-cost phase table (span 0 = none)
+  double gamma[QAOA_MAX_P];
+  double beta[QAOA_MAX_P];
+  void* phase;   // p * span entries
+  void* dtab;    // fixed point: p * 14 * 14 entries
+  void* turn;    // fixed point: 3 * 1024 entries
 };
 
 // launchers (return a CUDA error code)
-cudaError_t launch_sweep(int dtype, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep(int dtype, bool two, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_reduce(const ReducePlan& r, const double* partials, double* out, cudaStream_t s);
-cudaError_t launch_phase_table(int dtype, const double* gamma, int p, int64_t cmin, int64_t span,
-                               void* table, cudaStream_t s);
-int sweep_tile_bits(int dtype);   // max t + c per tile
-int sweep_grid(int dtype, int64_t tiles);  // persistent grid size for a sweep
+cudaError_t launch_tables(const TableArgs& t, cudaStream_t s);
+cudaError_t launch_cost_bound(const void* C, int f64, int n, unsigned long long* out, cudaStream_t s);
+cudaError_t launch_norm(const void* psi, int dtype, int n, double* partials, int* nblocks, cudaStream_t s);
+cudaError_t launch_expect(int dtype, const void* psi, const void* C, int cost_dtype, int n, double* partials,
+                          int grid, cudaStream_t s);
+int sweep_tile_bits(int dtype, bool two);     // B of the kernel a sweep uses
+// persistent grid size for a sweep (cost_bytes: 0, 4 or 8 bytes of cost tile per amplitude)
+int sweep_grid(int dtype, bool two, int tile_bits, int cost_bytes, int64_t tiles);
+int fx_shift_for(int tmax);                   // fixed-point scale for groups of <= tmax qubits
 
 // cost vector
 struct CostArgs {

@@ -1,24 +1,77 @@
-// Layer sweeps: phase separator, RX mixer, lambda = C psi and the fused reductions of
-// <C>, the norm and the adjoint-gradient terms (Eq. 1; Sec. II-B, IV-B, IV-C, IV-D).
+// Layer sweeps: phase separator, mixer, lambda = C psi and the fused reductions of <C>,
+// the norm and the adjoint-gradient terms (Eq. 1; Sec. II-B, IV-B, IV-C, IV-D).
 //
-// One kernel runs one sweep: a persistent grid walks the tiles of the state; each
-// tile is staged in shared memory, the sweep's operation program runs on it, and
-// the tile is written back.  Reductions accumulate per thread across tiles and are
-// folded per block into a partials array, so the order of every floating-point sum
-// is fixed for a given grid (deterministic results).
+// A sweep streams every tile of the state once.  A tile holds the 2^t combinations of
+// one group of qubits (local bits [c, c + t)) together with the 2^c lowest index bits
+// (local bits [0, c), kept for coalesced access); the other index bits are fixed per
+// tile.  Each thread holds R = 2^RB amplitudes of the tile in registers.  In "layout" k
+// the register index is the local bit range [lo(k), lo(k) + RB) and the thread index
+// is the rest, so butterflies on the qubits of that range run in registers; moving
+// to the next layout is one swizzled shared-memory exchange.  A sweep runs a short
+// program of operations on each tile (phase, mixer, lambda init, reductions) and
+// writes the tile back.  The grid is persistent over tiles and every reduction has a
+// fixed order, so results are deterministic for a given device.
+//
+// Arithmetic.
+//  * complex64: float32 throughout; the mixer applies RX(2 beta) = cos(b) I - i sin(b) X
+//    as one butterfly per qubit.
+//  * complex128: the state lives in int64 fixed point with scale 2^S inside a call
+//    (GB300 retires ~1.75 float64 FMA per SM clock, 1/73 of its float32 rate, so
+//    float64 butterflies would cost ~20x the sweep's memory time).  The mixer on a
+//    group of t qubits uses RX(2b)^{(x)t} = H^{(x)t} D H^{(x)t} = 2^-t W D W, where W is
+//    the unnormalised Walsh-Hadamard transform on the group (exact integer add/sub
+//    butterflies) and D = diag(exp(-i b (t - 2 popcount(g)))) is one complex multiply
+//    per amplitude, rounded once.  Phase factors are Q62 fixed point.  Reductions
+//    accumulate exact int128 products per thread and per tile and are converted to
+//    float64 once per tile.
 #include "internal.h"
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
+#include "fixedpoint.cuh"
+
 namespace qaoa {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kTileBits = 11;  // 2^11 amplitudes per buffer per tile
+// ------------------------------------------------------------------ tile layouts
 
-template <typename R> struct Cplx;
-template <> struct Cplx<double> { using T = double2; };
-template <> struct Cplx<float> { using T = float2; };
+template <int B_, int RB_, int SW_, int SWW_, int MINB_>
+struct Cfg {
+  static constexpr int MINB = MINB_;        // blocks per SM the register budget is sized for
+  static constexpr int B = B_;              // tile bits
+  static constexpr int RB = RB_;            // register bits per layout
+  static constexpr int R = 1 << RB_;        // amplitudes per thread (per buffer)
+  static constexpr int NT = 1 << (B_ - RB_);  // threads per block
+  static constexpr int NR = (B_ + RB_ - 1) / RB_;  // layouts (rounds)
+  __device__ static __forceinline__ int lo(int k) {
+    const int v = B - RB * (k + 1);
+    return v < 0 ? 0 : v;
+  }
+  // first local bit of round k that no earlier round covers: round k processes
+  // [lo(k), newhi(k)) where newhi(0) = B and newhi(k) = lo(k - 1)
+  __device__ static __forceinline__ int newhi(int k) { return k == 0 ? B : lo(k - 1); }
+  __device__ static __forceinline__ uint32_t idx(int k, uint32_t tid, int r) {
+    const int l = lo(k);
+    return (tid & ((1u << l) - 1)) | ((uint32_t)r << l) | ((tid >> l) << (l + RB));
+  }
+  // shared-memory slot of local index i: XOR-fold higher bits into the bank bits
+  __device__ static __forceinline__ uint32_t phys(uint32_t i) { return i ^ ((i >> SW_) & ((1u << SWW_) - 1)); }
+};
+
+// complex64 single buffer: 8192-amplitude tiles, 32 per thread, 256 threads
+using CfgF1 = Cfg<13, 5, 5, 4, 2>;
+// complex64 two buffers (gradient): 4096-amplitude tiles, 16 per thread per buffer
+using CfgF2 = Cfg<12, 4, 4, 4, 2>;
+// complex128 fixed point single buffer: 4096-amplitude tiles, 16 per thread
+using CfgX1 = Cfg<12, 4, 4, 3, 2>;
+// complex128 fixed point two buffers: 4096-amplitude tiles, 8 per thread per buffer, 512 threads
+using CfgX2 = Cfg<12, 3, 3, 3, 1>;
+
+__device__ __forceinline__ uint32_t phys_cost(uint32_t i, bool f64) {
+  return f64 ? (i ^ ((i >> 4) & 15)) : (i ^ ((i >> 5) & 31));
+}
 
 __device__ __forceinline__ uint64_t tile_base(const SweepGeom& g, int64_t tile) {
   const int lowrest_bits = g.j0 - g.c;
@@ -33,180 +86,533 @@ __device__ __forceinline__ uint64_t local_to_z(const SweepGeom& g, uint64_t base
   return base | l | (q << g.j0);
 }
 
-__device__ __forceinline__ double cost_at(const void* C, int cost_dtype, uint64_t z) {
-  if (cost_dtype == QAOA_COST_I32) return (double)__ldg((const int*)C + z);
-  return __ldg((const double*)C + z);
+// ------------------------------------------------------------------ fixed point helpers
+
+using i128 = __int128;
+using fx::round_shift;
+
+// (x * e) / 2^(62 + extra) for a state value x (|re|, |im| < 2^61) and a Q62 unit complex e
+__device__ __forceinline__ longlong2 cmul_fx(longlong2 x, longlong2 e, int extra) {
+  const fx::C64 o = fx::cmul_q62(x.x, x.y, e.x, e.y, extra);
+  return make_longlong2(o.x, o.y);
+}
+// the same with 128-bit products, for operands up to 2^63 (products of two Q62 factors)
+__device__ __forceinline__ longlong2 cmul_fx_wide(longlong2 x, longlong2 e, int extra) {
+  const fx::C64 o = fx::cmul_q62_exact(x.x, x.y, e.x, e.y, extra);
+  return make_longlong2(o.x, o.y);
+}
+__device__ __forceinline__ double fx_to_double(long long x, int s) { return fx::to_double(x, s); }
+__device__ __forceinline__ double i128_to_double(i128 v, int s) { return fx::i128_to_double(v, s); }
+__device__ __forceinline__ long long double_to_fx(double d, int s) { return fx::from_double(d, s); }
+__device__ __forceinline__ unsigned long long frac_turns(double d) { return fx::frac_turns(d); }
+
+// exp(-2 pi i t / 2^64) in Q62 from three 1024-entry tables and a first-order residual
+__device__ __forceinline__ longlong2 turn_phase(unsigned long long t, const longlong2* __restrict__ tt) {
+  const longlong2 e1 = tt[t >> 54];
+  const longlong2 e2 = tt[1024 + ((t >> 44) & 1023)];
+  const longlong2 e3 = tt[2048 + ((t >> 34) & 1023)];
+  longlong2 e = cmul_fx_wide(e1, e2, 0);
+  e = cmul_fx_wide(e, e3, 0);
+  // residual angle rho = 2 pi r 2^-64 < 2 pi 2^-30; exp(-i rho) = 1 - i rho to 2e-17
+  const unsigned long long r = t & ((1ull << 34) - 1);
+  const long long rho = (long long)(((r >> 2) * 3373259426ull) >> 29);  // rho * 2^62, 3373259426 = round(pi/2 2^31)
+  const long long dre = round_shift((i128)rho * e.y, 62);
+  const long long dim = round_shift((i128)rho * e.x, 62);
+  return make_longlong2(e.x + dre, e.y - dim);
 }
 
-template <typename R>
-__device__ __forceinline__ typename Cplx<R>::T cmul(typename Cplx<R>::T a, typename Cplx<R>::T e) {
-  typename Cplx<R>::T r;
-  r.x = a.x * e.x - a.y * e.y;
-  r.y = a.x * e.y + a.y * e.x;
-  return r;
-}
+// ------------------------------------------------------------------ kernel
 
-// exp(-i s gamma_l C(z)) as (re, im)
-template <typename R>
-__device__ __forceinline__ typename Cplx<R>::T phase_at(const SweepArgs& a, int layer, bool inverse,
-                                                         uint64_t z) {
-  typename Cplx<R>::T e;
-  const int64_t k = a.phase_table != nullptr ? (int64_t)__ldg((const int*)a.C + z) - a.cmin : -1;
-  if (k >= 0 && k < a.span) {  // entries outside the descriptor's bounds take the direct path
-    const typename Cplx<R>::T* tab = (const typename Cplx<R>::T*)a.phase_table;
-    e = tab[(int64_t)layer * a.span + k];
-  } else {
-    const double th = a.gamma[layer] * cost_at(a.C, a.cost_dtype, z);
-    double sn, cs;
-    sincos(th, &sn, &cs);
-    e.x = (R)cs;
-    e.y = (R)(-sn);
+__device__ __forceinline__ double cost_f(const void* Cs, bool f64, uint32_t i) {
+  return f64 ? ((const double*)Cs)[phys_cost(i, true)] : (double)((const int*)Cs)[phys_cost(i, false)];
+}
+__device__ __forceinline__ int cost_i(const void* Cs, uint32_t i) { return ((const int*)Cs)[phys_cost(i, false)]; }
+
+template <class CF, bool FX, bool TWO>
+struct Sweeper {
+  using V = typename std::conditional<FX, longlong2, float2>::type;
+  static constexpr int R = CF::R;
+
+  const SweepArgs& a;
+  V (&v)[R];
+  V (&w)[R];
+  V* X;          // exchange buffer, 2^B slots
+  void* Cs;      // cost tile, 2^B slots
+  const V* Ts;   // shared-memory copy of one layer's phase table (or nullptr)
+  int ts_layer;  // layer whose table Ts holds (-1: none)
+  double* blk;   // block accumulators
+  double* red;   // reduction scratch [2][NT/32]
+  int cur;       // current layout
+  int lam_shift;  // lambda scale exponent (fixed point)
+  int in_shift;   // extra input scale exponent of a user state (fixed point)
+  uint32_t evalid;
+  uint64_t base;
+  const uint32_t tid;
+
+  __device__ Sweeper(const SweepArgs& a_, V (&v_)[R], V (&w_)[R], V* X_, void* Cs_, double* blk_, double* red_)
+      : a(a_), v(v_), w(w_), X(X_), Cs(Cs_), Ts(nullptr), ts_layer(-1), blk(blk_), red(red_), cur(0), lam_shift(0),
+        in_shift(0), evalid(0), base(0), tid(threadIdx.x) {}
+
+  __device__ __forceinline__ uint32_t idx(int r) const { return CF::idx(cur, tid, r); }
+
+  __device__ void exchange_one(V (&u)[R], int to) {
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) X[CF::phys(CF::idx(cur, tid, r))] = u[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) u[r] = X[CF::phys(CF::idx(to, tid, r))];
   }
-  if (inverse) e.y = -e.y;
-  return e;
-}
+  // both buffers always share one layout
+  __device__ void go(int to) {
+    if (to == cur) return;
+    exchange_one(v, to);
+    if (TWO) exchange_one(w, to);
+    cur = to;
+  }
 
-template <typename R>
-__global__ void __launch_bounds__(kThreads) sweep_kernel(const __grid_constant__ SweepArgs a) {
-  using T = typename Cplx<R>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const SweepGeom& g = a.g;
-  const int bits = g.t + g.c;
-  const uint32_t E = 1u << bits;
-  T* sp = (T*)smem_raw;
-  T* sl = sp + E;
-  const bool two = (a.lam != nullptr);
-  T* gpsi = (T*)a.psi;
-  T* glam = (T*)a.lam;
-  __shared__ double blk_acc[kMaxAcc];
-  __shared__ double red_tmp[2][kThreads / 32];
-  for (int r = threadIdx.x; r < kMaxAcc; r += kThreads) blk_acc[r] = 0.0;
-  // block-reduce (v0, v1) and add to blk_acc[r] (and blk_acc[r + 1] when two)
-  auto block_add = [&](int r, double v0, double v1, bool two_vals) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // block-reduce and add to blk[r] (and blk[r + 1])
+  __device__ void block_add(int r, double v0, double v1, bool pair) {
+    const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       v0 += __shfl_down_sync(0xffffffffu, v0, o);
       v1 += __shfl_down_sync(0xffffffffu, v1, o);
     }
+    __syncthreads();
     if (lane == 0) {
-      red_tmp[0][warp] = v0;
-      red_tmp[1][warp] = v1;
+      red[warp] = v0;
+      red[CF::NT / 32 + warp] = v1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       double s0 = 0.0, s1 = 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) {
-        s0 += red_tmp[0][w];
-        s1 += red_tmp[1][w];
+      for (int k = 0; k < CF::NT / 32; ++k) {
+        s0 += red[k];
+        s1 += red[CF::NT / 32 + k];
       }
-      blk_acc[r] += s0;
-      if (two_vals) blk_acc[r + 1] += s1;
+      blk[r] += s0;
+      if (pair) blk[r + 1] += s1;
     }
+  }
+
+  // ---------------------------------------------------------------- phase
+  __device__ __forceinline__ V phase_factor(int layer, bool inverse, uint32_t i) const {
+    const bool f64 = a.cost_dtype == QAOA_COST_F64;
+    long long k = -1;
+    if (!f64 && a.phase_table != nullptr) k = (long long)cost_i(Cs, i) - a.cmin;
+    V e;
+    if (k >= 0 && k < a.span) {
+      e = layer == ts_layer ? Ts[k] : __ldg((const V*)a.phase_table + (long long)layer * a.span + k);
+    } else {
+      const double th = a.g2pi[layer] * cost_f(Cs, f64, i);  // turns
+      if constexpr (FX) {
+        e = turn_phase(frac_turns(th), (const longlong2*)a.turn_table);
+      } else {
+        const float f = (float)(th - rint(th));
+        float s, c;
+        sincospif(2.0f * f, &s, &c);
+        e = make_float2(c, -s);
+      }
+    }
+    if (inverse) e.y = -e.y;
+    return e;
+  }
+
+  __device__ void op_phase(int layer, bool inverse, bool on_psi, bool on_lam) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t i = idx(r);
+      const V e = phase_factor(layer, inverse, i);
+      if constexpr (FX) {
+        if (on_psi) v[r] = cmul_fx(v[r], e, 0);
+        if (TWO && on_lam) w[r] = cmul_fx(w[r], e, 0);
+      } else {
+        if (on_psi) v[r] = make_float2(v[r].x * e.x - v[r].y * e.y, v[r].x * e.y + v[r].y * e.x);
+        if (TWO && on_lam) w[r] = make_float2(w[r].x * e.x - w[r].y * e.y, w[r].x * e.y + w[r].y * e.x);
+      }
+    }
+  }
+
+  // ---------------------------------------------------------------- mixer, float32: RX butterflies
+  // RX(2b) = cos(b) (I - i tan(b) X) = -i sin(b) (X + i cot(b) I).  For |tan b| <= 1 a pair
+  // (x, y) goes to (x - i t y, y - i t x) with t = tan b and the factor cos b; otherwise to
+  // (y + i u x, x + i u y) with u = cot b and the factor -i sin b.  Either way a butterfly
+  // is 4 FMAs with |t|, |u| <= 1; the per-qubit factors of a round are applied once at its end.
+  __device__ __forceinline__ void bf_tan(float2& x, float2& y, float t) {
+    const float2 p = x, q = y;
+    x = make_float2(fmaf(t, q.y, p.x), fmaf(-t, q.x, p.y));
+    y = make_float2(fmaf(t, p.y, q.x), fmaf(-t, p.x, q.y));
+  }
+  __device__ __forceinline__ void bf_cot(float2& x, float2& y, float u) {
+    const float2 p = x, q = y;
+    x = make_float2(fmaf(-u, p.y, q.x), fmaf(u, p.x, q.y));
+    y = make_float2(fmaf(-u, q.y, p.x), fmaf(u, q.x, p.y));
+  }
+  __device__ void scale_f32(V (&u)[R], bool tanf, float m, int nb) {
+    // multiply by (m)^nb (tangent form) or (-i m)^nb (cotangent form)
+    float f = 1.f;
+    for (int j = 0; j < nb; ++j) f *= m;
+    const int rot = tanf ? 0 : (nb & 3);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float2 z = u[r];
+      float2 o;
+      if (rot == 0) o = make_float2(z.x, z.y);
+      else if (rot == 1) o = make_float2(z.y, -z.x);
+      else if (rot == 2) o = make_float2(-z.x, -z.y);
+      else o = make_float2(-z.y, z.x);
+      u[r] = make_float2(o.x * f, o.y * f);
+    }
+  }
+
+  __device__ void mix_f32(int layer, bool inverse, bool on_psi, bool on_lam, int xacc) {
+    const double cbd = a.cosb[layer], sbd = inverse ? -a.sinb[layer] : a.sinb[layer];
+    const bool tanf = fabs(cbd) >= fabs(sbd);
+    const float tu = tanf ? (float)(sbd / cbd) : (float)(cbd / sbd);
+    const float m = tanf ? (float)cbd : (float)sbd;
+    const int gl = a.g.c, gh = a.g.c + a.g.t;
+    const bool rev = (cur == CF::NR - 1) && CF::NR > 1;
+    float xs = 0.f;
+    for (int s = 0; s < CF::NR; ++s) {
+      const int k = rev ? CF::NR - 1 - s : s;
+      const int l0 = CF::lo(k), l1 = CF::newhi(k);
+      if (l1 <= gl || l0 >= gh) continue;  // no group qubit in this round
+      go(k);
+      if (TWO && xacc >= 0) {  // sum over this round's qubits of Im(conj(la) pb + conj(lb) pa), state exact here
+#pragma unroll
+        for (int rb = 0; rb < CF::RB; ++rb) {
+          const int b = l0 + rb;
+          if (b < l1 && b >= gl && b < gh) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              if (r & (1 << rb)) continue;
+              const int q = r | (1 << rb);
+              xs += w[r].x * v[q].y - w[r].y * v[q].x + w[q].x * v[r].y - w[q].y * v[r].x;
+            }
+          }
+        }
+      }
+      int nb = 0;
+#pragma unroll
+      for (int rb = 0; rb < CF::RB; ++rb) {
+        const int b = l0 + rb;
+        if (b < l1 && b >= gl && b < gh) {
+          ++nb;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            if (r & (1 << rb)) continue;
+            const int q = r | (1 << rb);
+            if (tanf) {
+              if (on_psi) bf_tan(v[r], v[q], tu);
+              if (TWO && on_lam) bf_tan(w[r], w[q], tu);
+            } else {
+              if (on_psi) bf_cot(v[r], v[q], tu);
+              if (TWO && on_lam) bf_cot(w[r], w[q], tu);
+            }
+          }
+        }
+      }
+      if (on_psi) scale_f32(v, tanf, m, nb);
+      if (TWO && on_lam) scale_f32(w, tanf, m, nb);
+    }
+    if (TWO && xacc >= 0) block_add(xacc, 2.0 * (double)xs, 0.0, false);
+  }
+
+  // ---------------------------------------------------------------- mixer, fixed point: W D W
+  template <int RBc>
+  __device__ __forceinline__ void wht_bit(V (&u)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r & (1 << RBc)) continue;
+      const int q = r | (1 << RBc);
+      const longlong2 x = u[r], y = u[q];
+      u[r] = make_longlong2(x.x + y.x, x.y + y.y);
+      u[q] = make_longlong2(x.x - y.x, x.y - y.y);
+    }
+  }
+  __device__ void wht_round(int k, bool on_psi, bool on_lam) {
+    const int l0 = CF::lo(k), l1 = CF::newhi(k);
+    const int gl = a.g.c, gh = a.g.c + a.g.t;
+#pragma unroll
+    for (int rb = 0; rb < CF::RB; ++rb) {
+      const int b = l0 + rb;
+      if (b < l1 && b >= gl && b < gh) {
+        if (on_psi) {
+          if constexpr (FX) {
+            if (rb == 0) wht_bit<0>(v);
+            if (CF::RB > 1 && rb == 1) wht_bit<(CF::RB > 1 ? 1 : 0)>(v);
+            if (CF::RB > 2 && rb == 2) wht_bit<(CF::RB > 2 ? 2 : 0)>(v);
+            if (CF::RB > 3 && rb == 3) wht_bit<(CF::RB > 3 ? 3 : 0)>(v);
+            if (CF::RB > 4 && rb == 4) wht_bit<(CF::RB > 4 ? 4 : 0)>(v);
+          }
+        }
+        if (TWO && on_lam) {
+          if constexpr (FX) {
+            if (rb == 0) wht_bit<0>(w);
+            if (CF::RB > 1 && rb == 1) wht_bit<(CF::RB > 1 ? 1 : 0)>(w);
+            if (CF::RB > 2 && rb == 2) wht_bit<(CF::RB > 2 ? 2 : 0)>(w);
+            if (CF::RB > 3 && rb == 3) wht_bit<(CF::RB > 3 ? 3 : 0)>(w);
+            if (CF::RB > 4 && rb == 4) wht_bit<(CF::RB > 4 ? 4 : 0)>(w);
+          }
+        }
+      }
+    }
+  }
+
+  __device__ void mix_fx(int layer, bool inverse, bool on_psi, bool on_lam, int xacc) {
+    const int gl = a.g.c, gh = a.g.c + a.g.t, t = a.g.t;
+    // rounds that hold group qubits, walked from the current layout outwards
+    int ks[8], nk = 0;
+    const bool rev = (cur == CF::NR - 1) && CF::NR > 1;
+    for (int s = 0; s < CF::NR; ++s) {
+      const int k = rev ? CF::NR - 1 - s : s;
+      if (CF::newhi(k) <= gl || CF::lo(k) >= gh) continue;
+      ks[nk++] = k;
+    }
+    for (int j = 0; j < nk; ++j) {
+      go(ks[j]);
+      wht_round(ks[j], on_psi, on_lam);
+    }
+    // D = exp(-i s b (t - 2 popcount(g))) / 2^t, with the X-term reduction on the way
+    const longlong2* dt = (const longlong2*)a.d_table + ((long long)layer * 14 + t) * 14;
+    i128 xs = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t i = idx(r);
+      const int pc = __popc((i >> gl) & ((1u << t) - 1));
+      longlong2 e = dt[pc];
+      if (inverse) e.y = -e.y;
+      if (TWO && xacc >= 0) {
+        const i128 pr = (i128)w[r].x * v[r].y - (i128)w[r].y * v[r].x;  // Im(conj(lam~) psi~)
+        xs += (pr >> 32) * (t - 2 * pc);
+      }
+      if (on_psi) v[r] = cmul_fx(v[r], e, t);
+      if (TWO && on_lam) w[r] = cmul_fx(w[r], e, t);
+    }
+    if (TWO && xacc >= 0) {
+      // value = 2 * xs * 2^32 * 2^-t * 2^-2S (lambda also carries the scale 2^klam)
+      block_add(xacc, 2.0 * i128_to_double(xs, 2 * a.fx_shift + t - 32 - lam_shift), 0.0, false);
+    }
+    for (int j = nk - 1; j >= 0; --j) {
+      go(ks[j]);
+      wht_round(ks[j], on_psi, on_lam);
+    }
+  }
+
+  // ---------------------------------------------------------------- elementwise ops
+  // lambda := C psi; fixed point stores lambda / 2^lam_shift (2^lam_shift >= max |C|) so
+  // that lambda keeps the norm bound of the state
+  __device__ void op_lambda() {
+    const bool f64 = a.cost_dtype == QAOA_COST_F64;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t i = idx(r);
+      if constexpr (FX) {
+        if (!f64) {
+          const long long c = cost_i(Cs, i);
+          w[r] = make_longlong2(round_shift((i128)v[r].x * c, lam_shift), round_shift((i128)v[r].y * c, lam_shift));
+        } else {
+          const long long cq = double_to_fx(cost_f(Cs, true, i), 62 - lam_shift);
+          w[r] = make_longlong2(round_shift((i128)v[r].x * cq, 62), round_shift((i128)v[r].y * cq, 62));
+        }
+      } else {
+        const float c = (float)cost_f(Cs, f64, i);
+        w[r] = make_float2(c * v[r].x, c * v[r].y);
+      }
+    }
+  }
+
+  __device__ void op_expect(int acc) {
+    const bool f64 = a.cost_dtype == QAOA_COST_F64;
+    double e0 = 0.0, e1 = 0.0;
+    if constexpr (FX) {
+      i128 sc = 0, sn = 0;
+      double sf = 0.0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t i = idx(r);
+        if (i >= evalid) continue;
+        const i128 p2 = (i128)v[r].x * v[r].x + (i128)v[r].y * v[r].y;
+        sn += p2 >> 16;
+        if (!f64) sc += (p2 >> 32) * cost_i(Cs, i);
+        else sf += cost_f(Cs, true, i) * i128_to_double(p2, 2 * a.fx_shift);
+      }
+      e1 = i128_to_double(sn, 2 * (a.fx_shift - in_shift) - 16);
+      e0 = f64 ? ldexp(sf, 2 * in_shift) : i128_to_double(sc, 2 * (a.fx_shift - in_shift) - 32);
+    } else {
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t i = idx(r);
+        if (i >= evalid) continue;
+        const float p2 = v[r].x * v[r].x + v[r].y * v[r].y;
+        s0 += (float)cost_f(Cs, f64, i) * p2;
+        s1 += p2;
+      }
+      e0 = s0;
+      e1 = s1;
+    }
+    block_add(acc, e0, e1, true);
+  }
+
+  __device__ void op_cterm(int acc) {
+    const bool f64 = a.cost_dtype == QAOA_COST_F64;
+    double e0 = 0.0;
+    if constexpr (FX) {
+      i128 sc = 0;
+      double sf = 0.0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t i = idx(r);
+        if (i >= evalid) continue;
+        const i128 pr = (i128)w[r].x * v[r].y - (i128)w[r].y * v[r].x;
+        if (!f64) sc += (pr >> 32) * cost_i(Cs, i);
+        else sf += cost_f(Cs, true, i) * i128_to_double(pr, 2 * a.fx_shift - lam_shift);
+      }
+      e0 = f64 ? sf : i128_to_double(sc, 2 * a.fx_shift - 32 - lam_shift);
+    } else {
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t i = idx(r);
+        if (i >= evalid) continue;
+        s += (float)cost_f(Cs, f64, i) * (w[r].x * v[r].y - w[r].y * v[r].x);
+      }
+      e0 = s;
+    }
+    block_add(acc, 2.0 * e0, 0.0, false);
+  }
+};
+
+template <class CF, bool FX, bool TWO>
+__global__ void __launch_bounds__(CF::NT, CF::MINB) sweep_kernel(const __grid_constant__ SweepArgs a) {
+  using S = Sweeper<CF, FX, TWO>;
+  using V = typename S::V;
+  constexpr int R = CF::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* X = (V*)smem_raw;
+  void* Cs = smem_raw + (sizeof(V) << CF::B);
+  V* Tsm = (V*)((unsigned char*)Cs + (a.needs_cost ? ((a.cost_dtype == QAOA_COST_F64 ? 8 : 4) << CF::B) : 0));
+  __shared__ double blk[kMaxAcc];
+  __shared__ double red[2 * (CF::NT / 32)];
+  for (int r = threadIdx.x; r < kMaxAcc; r += CF::NT) blk[r] = 0.0;
+
+  V v[R], w[R];
+  S s(a, v, w, X, Cs, blk, red);
+  if (a.smem_table_layer >= 0) {  // one layer's phase table in shared memory
+    const V* src = (const V*)a.phase_table + (long long)a.smem_table_layer * a.span;
+    for (int k = threadIdx.x; k < a.span; k += CF::NT) Tsm[k] = __ldg(src + k);
+    s.Ts = Tsm;
+    s.ts_layer = a.smem_table_layer;
     __syncthreads();
-  };
-  const R amp0 = (R)rsqrt((double)(1ull << g.n));
+  }
+  const SweepGeom& g = a.g;
+  s.evalid = 1u << (g.t + g.c);
+  const bool cf64 = a.cost_dtype == QAOA_COST_F64;
+  if constexpr (FX) {
+    if (a.cmax_dev != nullptr) {  // smallest k >= 0 with 2^k >= max |C|
+      const unsigned long long b = *a.cmax_dev;
+      const int ex = (int)((b >> 52) & 0x7FF);
+      int k = ex == 0 ? 0 : ex - 1023 + ((b & ((1ull << 52) - 1)) != 0 ? 1 : 0);
+      s.lam_shift = k < 0 ? 0 : k;
+    }
+    if (a.norm2_dev != nullptr) {  // 2^k with |psi| / 2^k in [1, 2)
+      const unsigned long long b = (unsigned long long)__double_as_longlong(*a.norm2_dev);
+      const int ex = (int)((b >> 52) & 0x7FF);
+      s.in_shift = ex == 0 ? 0 : ((ex - 1023) >= 0 ? (ex - 1023) / 2 : -((1023 - ex + 1) / 2));
+    }
+  }
+  const uint32_t tid = threadIdx.x;
 
   for (int64_t tile = blockIdx.x; tile < g.tiles; tile += gridDim.x) {
     const uint64_t base = tile_base(g, tile);
-    for (uint32_t i = threadIdx.x; i < E; i += kThreads) {
-      const uint64_t z = local_to_z(g, base, i);
-      if (a.init_plus) {
-        sp[i] = T{amp0, (R)0};
-      } else if (a.load_psi) {
-        sp[i] = gpsi[z];
+    s.base = base;
+    s.cur = 0;
+    // cost tile (linear order, coalesced)
+    if (a.needs_cost) {
+      __syncthreads();
+      for (uint32_t i = tid; i < (1u << CF::B); i += CF::NT) {
+        // slots past the tile's valid range hold cost 0 (phase 1) so their zero
+        // amplitudes stay zero
+        const bool ok = i < s.evalid;
+        const uint64_t z = ok ? local_to_z(g, base, i) : 0;
+        if (cf64) ((double*)Cs)[phys_cost(i, true)] = ok ? __ldg((const double*)a.C + z) : 0.0;
+        else ((int*)Cs)[phys_cost(i, false)] = ok ? __ldg((const int*)a.C + z) : 0;
       }
-      if (two && a.load_lam) sl[i] = glam[z];
+      __syncthreads();
     }
-    __syncthreads();
+    // state (layout 0)
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t i = CF::idx(0, tid, r);
+      const bool ok = i < s.evalid;
+      const uint64_t z = ok ? local_to_z(g, base, i) : 0;
+      if constexpr (FX) {
+        if (!ok) v[r] = make_longlong2(0, 0);
+        else if (a.load_fmt == 2) v[r] = make_longlong2(a.init_fx, 0);
+        else if (a.load_fmt == 1) {
+          const double2 d = __ldg((const double2*)a.psi + z);
+          v[r] = make_longlong2(double_to_fx(d.x, a.fx_shift - s.in_shift), double_to_fx(d.y, a.fx_shift - s.in_shift));
+        } else v[r] = __ldg((const longlong2*)a.psi + z);
+        if (TWO) w[r] = (ok && a.load_lam) ? __ldg((const longlong2*)a.lam + z) : make_longlong2(0, 0);
+      } else {
+        if (!ok) v[r] = make_float2(0.f, 0.f);
+        else if (a.load_fmt == 2) v[r] = make_float2(a.init_f32, 0.f);
+        else v[r] = __ldg((const float2*)a.psi + z);
+        if (TWO) w[r] = (ok && a.load_lam) ? __ldg((const float2*)a.lam + z) : make_float2(0.f, 0.f);
+      }
+    }
 
     for (int k = 0; k < a.nops; ++k) {
       const uint32_t op = a.ops[k];
       const uint32_t kind = op & 0xff;
-      const uint32_t arg = op >> 16;
+      const int layer = (op >> 16) & 0xff;
+      const int acc = (int)((op >> 24) & 0xff);
       const bool on_psi = op & F_PSI, on_lam = op & F_LAM, inv = op & F_SIGN;
+      const bool has_x = op & F_XTERM;
       if (kind == OP_PHASE) {
-        for (uint32_t i = threadIdx.x; i < E; i += kThreads) {
-          const uint64_t z = local_to_z(g, base, i);
-          const T e = phase_at<R>(a, arg, inv, z);
-          if (on_psi) sp[i] = cmul<R>(sp[i], e);
-          if (on_lam) sl[i] = cmul<R>(sl[i], e);
-        }
+        s.op_phase(layer, inv, on_psi, on_lam);
       } else if (kind == OP_MIX) {
-        const R cb = (R)a.cosb[arg];
-        const R sb = (R)(inv ? -a.sinb[arg] : a.sinb[arg]);
-        for (int q = 0; q < g.t; ++q) {
-          const int bit = g.c + q;
-          const uint32_t lowmask = (1u << bit) - 1;
-          for (uint32_t pi = threadIdx.x; pi < (E >> 1); pi += kThreads) {
-            const uint32_t ia = ((pi & ~lowmask) << 1) | (pi & lowmask);
-            const uint32_t ib = ia | (1u << bit);
-            if (on_psi) {
-              const T x = sp[ia], y = sp[ib];
-              sp[ia] = T{cb * x.x + sb * y.y, cb * x.y - sb * y.x};
-              sp[ib] = T{cb * y.x + sb * x.y, cb * y.y - sb * x.x};
-            }
-            if (on_lam) {
-              const T x = sl[ia], y = sl[ib];
-              sl[ia] = T{cb * x.x + sb * y.y, cb * x.y - sb * y.x};
-              sl[ib] = T{cb * y.x + sb * x.y, cb * y.y - sb * x.x};
-            }
-          }
-          __syncthreads();
-        }
+        if constexpr (FX) s.mix_fx(layer, inv, on_psi, on_lam, has_x ? acc : -1);
+        else s.mix_f32(layer, inv, on_psi, on_lam, has_x ? acc : -1);
       } else if (kind == OP_LAMBDA) {
-        for (uint32_t i = threadIdx.x; i < E; i += kThreads) {
-          const uint64_t z = local_to_z(g, base, i);
-          const R cz = (R)cost_at(a.C, a.cost_dtype, z);
-          sl[i] = T{cz * sp[i].x, cz * sp[i].y};
-        }
+        if constexpr (TWO) s.op_lambda();
       } else if (kind == OP_RED_EXPECT) {
-        double e0 = 0.0, e1 = 0.0;
-        for (uint32_t i = threadIdx.x; i < E; i += kThreads) {
-          const uint64_t z = local_to_z(g, base, i);
-          const double pr = (double)sp[i].x * sp[i].x + (double)sp[i].y * sp[i].y;
-          e0 += cost_at(a.C, a.cost_dtype, z) * pr;
-          e1 += pr;
-        }
-        block_add(arg, e0, e1, true);
-      } else if (kind == OP_RED_XTERM) {
-        double e0 = 0.0;
-        for (int q = 0; q < g.t; ++q) {
-          const int bit = g.c + q;
-          const uint32_t lowmask = (1u << bit) - 1;
-          for (uint32_t pi = threadIdx.x; pi < (E >> 1); pi += kThreads) {
-            const uint32_t ia = ((pi & ~lowmask) << 1) | (pi & lowmask);
-            const uint32_t ib = ia | (1u << bit);
-            const T la = sl[ia], lb = sl[ib], pa = sp[ia], pb = sp[ib];
-            // Im(conj(la) pb + conj(lb) pa)
-            e0 += (double)la.x * pb.y - (double)la.y * pb.x + (double)lb.x * pa.y - (double)lb.y * pa.x;
-          }
-        }
-        block_add(arg, 2.0 * e0, 0.0, false);
+        s.op_expect(acc);
       } else if (kind == OP_RED_CTERM) {
-        double e0 = 0.0;
-        for (uint32_t i = threadIdx.x; i < E; i += kThreads) {
-          const uint64_t z = local_to_z(g, base, i);
-          const T l = sl[i], p = sp[i];
-          e0 += cost_at(a.C, a.cost_dtype, z) * ((double)l.x * p.y - (double)l.y * p.x);
-        }
-        block_add(arg, 2.0 * e0, 0.0, false);
+        if constexpr (TWO) s.op_cterm(acc);
       }
-      __syncthreads();
     }
 
-    for (uint32_t i = threadIdx.x; i < E; i += kThreads) {
+    // store (layout 0)
+    s.go(0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t i = CF::idx(0, tid, r);
+      if (i >= s.evalid) continue;
       const uint64_t z = local_to_z(g, base, i);
-      if (a.store_psi) gpsi[z] = sp[i];
-      if (two && a.store_lam) glam[z] = sl[i];
+      if constexpr (FX) {
+        if (a.store_fmt == 1) {
+          ((double2*)a.psi)[z] = make_double2(fx_to_double(v[r].x, a.fx_shift - s.in_shift),
+                                              fx_to_double(v[r].y, a.fx_shift - s.in_shift));
+        } else if (a.store_fmt == 0) {
+          ((longlong2*)a.psi)[z] = v[r];
+        }
+        if (TWO && a.store_lam) ((longlong2*)a.lam)[z] = w[r];
+      } else {
+        if (a.store_fmt >= 0) ((float2*)a.psi)[z] = v[r];
+        if (TWO && a.store_lam) ((float2*)a.lam)[z] = w[r];
+      }
     }
-    __syncthreads();
   }
 
-  // write this block's accumulators
   __syncthreads();
-  for (int r = threadIdx.x; r < a.nred; r += kThreads)
-    a.partials[(int64_t)a.red_slot[r] * a.grid + blockIdx.x] = blk_acc[r];
+  for (int r = threadIdx.x; r < a.nred; r += CF::NT)
+    a.partials[(int64_t)a.red_slot[r] * a.grid + blockIdx.x] = blk[r];
 }
+
+// ------------------------------------------------------------------ small kernels
 
 __global__ void reduce_kernel(const __grid_constant__ ReducePlan r, const double* __restrict__ partials,
                               double* __restrict__ out) {
@@ -222,37 +628,85 @@ __global__ void reduce_kernel(const __grid_constant__ ReducePlan r, const double
     if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[o] = sh[0];
+  if (threadIdx.x == 0) out[o] = sh[0] * r.scale[o];
 }
 
-template <typename T>
-__global__ void phase_table_kernel(const __grid_constant__ SweepArgs a, int p, T* __restrict__ table) {
-  const int64_t total = (int64_t)p * a.span;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int l = (int)(i / a.span);
-    const int64_t c = a.cmin + (i - (int64_t)l * a.span);
-    const double th = a.gamma[l] * (double)c;
-    double sn, cs;
-    sincos(th, &sn, &cs);
-    table[i] = T{(decltype(T::x))cs, (decltype(T::x))(-sn)};
+__device__ __forceinline__ long long q62(double x) { return llrint(ldexp(x, 62)); }
+
+// integer-cost phase tables exp(-i gamma_l c), c = cmin + k; then (fixed point) the
+// mixer diagonals exp(-i beta_l (t - 2k)) for t = 1..13, k = 0..t, and the turn tables
+__global__ void tables_kernel(const __grid_constant__ TableArgs ta) {
+  const int64_t nphase = (int64_t)ta.p * ta.span;
+  const int64_t nd = ta.fx ? (int64_t)ta.p * 14 * 14 : 0;
+  const int64_t nt = ta.fx ? 3 * 1024 : 0;
+  const int64_t total = nphase + nd + nt;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < nphase) {
+      const int l = (int)(i / ta.span);
+      const int64_t c = ta.cmin + (i - (int64_t)l * ta.span);
+      const double th = ta.gamma[l] * (double)c;
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      if (ta.fx) ((longlong2*)ta.phase)[i] = make_longlong2(q62(cs), q62(-sn));
+      else ((float2*)ta.phase)[i] = make_float2((float)cs, (float)(-sn));
+    } else if (i < nphase + nd) {
+      const int64_t j = i - nphase;
+      const int l = (int)(j / 196), t = (int)((j / 14) % 14), k = (int)(j % 14);
+      const double th = ta.beta[l] * (double)(t - 2 * k);
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      ((longlong2*)ta.dtab)[j] = (k <= t) ? make_longlong2(q62(cs), q62(-sn)) : make_longlong2(0, 0);
+    } else {
+      const int64_t j = i - nphase - nd;
+      const int level = (int)(j / 1024), k = (int)(j % 1024);
+      // exp(-2 pi i k / 2^(10 (level + 1)))
+      const double th = -2.0 * 3.141592653589793238 * (double)k * ldexp(1.0, -10 * (level + 1));
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      ((longlong2*)ta.turn)[j] = make_longlong2(q62(cs), q62(sn));
+    }
   }
 }
 
-template <typename R>
-int max_blocks_per_sm() {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const size_t smem = 2 * sizeof(typename Cplx<R>::T) << kTileBits;
-    cudaFuncSetAttribute(sweep_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<R>, kThreads, smem);
-    cached = nb > 0 ? nb : 1;
+// max |C(z)| over the cost vector -> lam_shift = smallest k with 2^k >= max|C| (device scalar)
+__global__ void cost_bound_kernel(const void* __restrict__ C, int f64, int64_t count, unsigned long long* out) {
+  unsigned long long mx = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    double c = f64 ? __ldg((const double*)C + i) : (double)__ldg((const int*)C + i);
+    c = fabs(c);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(c);  // monotone for c >= 0
+    mx = b > mx ? b : mx;
   }
-  return cached;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long y = __shfl_down_sync(0xffffffffu, mx, o);
+    mx = y > mx ? y : mx;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
 }
+
+// state norm^2 of a user (float64 / float32) state, for the fixed-point input scale
+__global__ void norm_kernel(const void* __restrict__ psi, int dtype, int64_t count, double* __restrict__ partials) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    if (dtype == QAOA_C128) {
+      const double2 d = __ldg((const double2*)psi + i);
+      s += d.x * d.x + d.y * d.y;
+    } else {
+      const float2 f = __ldg((const float2*)psi + i);
+      s += (double)f.x * f.x + (double)f.y * f.y;
+    }
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+// ------------------------------------------------------------------ launch plumbing
 
 int num_sms() {
   static int cached = 0;
@@ -265,30 +719,135 @@ int num_sms() {
   return cached;
 }
 
+template <class CF, bool FX, bool TWO>
+size_t smem_bytes(int cost_bytes, int table_entries = 0) {
+  const size_t vb = FX ? sizeof(longlong2) : sizeof(float2);
+  return (vb << CF::B) + ((size_t)cost_bytes << CF::B) + vb * table_entries;
+}
+
+// blocks per SM for a configuration with a cost tile of cost_bytes per amplitude (0, 4, 8)
+template <class CF, bool FX, bool TWO>
+int blocks_per_sm(int cost_bytes) {
+  static int cached[3] = {0, 0, 0};
+  static bool attr = false;
+  const int slot = cost_bytes == 0 ? 0 : (cost_bytes == 4 ? 1 : 2);
+  if (!attr) {
+    cudaFuncSetAttribute(sweep_kernel<CF, FX, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_bytes<CF, FX, TWO>(8, kSmemTable));
+    attr = true;
+  }
+  if (!cached[slot]) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<CF, FX, TWO>, CF::NT,
+                                                  smem_bytes<CF, FX, TWO>(cost_bytes, kSmemTable));
+    cached[slot] = nb > 0 ? nb : 1;
+  }
+  return cached[slot];
+}
+
+template <class CF, bool FX, bool TWO>
+void launch_t(const SweepArgs& a, cudaStream_t s) {
+  blocks_per_sm<CF, FX, TWO>(8);
+  const int cb = a.needs_cost ? (a.cost_dtype == QAOA_COST_F64 ? 8 : 4) : 0;
+  const int te = a.smem_table_layer >= 0 ? (int)a.span : 0;
+  sweep_kernel<CF, FX, TWO><<<a.grid, CF::NT, smem_bytes<CF, FX, TWO>(cb, te), s>>>(a);
+}
+
+// <C> and the norm of a user-format state, one pass (stand-alone expectation)
+template <bool C128>
+__global__ void expect_kernel(const void* __restrict__ psi, const void* __restrict__ C, int cost_f64, int64_t count,
+                              double* __restrict__ partials, int grid) {
+  double e0 = 0.0, e1 = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < count; i0 += 32 * stride) {
+    float f0 = 0.f, f1 = 0.f;
+    for (int k = 0; k < 32; ++k) {
+      const int64_t i = i0 + k * stride;
+      if (i >= count) break;
+      const double c = cost_f64 ? __ldg((const double*)C + i) : (double)__ldg((const int*)C + i);
+      if (C128) {
+        const double2 d = __ldg((const double2*)psi + i);
+        const double pr = d.x * d.x + d.y * d.y;
+        e0 += c * pr;
+        e1 += pr;
+      } else {
+        const float2 f = __ldg((const float2*)psi + i);
+        const float pr = f.x * f.x + f.y * f.y;
+        f0 += (float)c * pr;
+        f1 += pr;
+      }
+    }
+    if (!C128) {
+      e0 += f0;
+      e1 += f1;
+    }
+  }
+  __shared__ double sh[2][256];
+  sh[0][threadIdx.x] = e0;
+  sh[1][threadIdx.x] = e1;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = sh[0][0];
+    partials[(int64_t)kMaxContrib * grid + blockIdx.x] = sh[1][0];
+  }
+}
+
 }  // namespace
 
-int sweep_tile_bits(int /*dtype*/) { return kTileBits; }
+int sweep_tile_bits(int dtype, bool two) {
+  if (dtype == QAOA_C128) return 12;
+  return two ? 12 : 13;
+}
 
-int sweep_grid(int dtype, int64_t tiles) {
-  const int per_sm = dtype == QAOA_C128 ? max_blocks_per_sm<double>() : max_blocks_per_sm<float>();
+// values stay below 2^61 through a group's Walsh-Hadamard transform (growth 2^(t/2)) for
+// states of norm < 2, as the limb multiply requires
+int fx_shift_for(int tmax) { return 62 - (tmax + 1) / 2 - 2; }
+
+int sweep_grid(int dtype, bool two, int tile_bits, int cost_bytes, int64_t tiles) {
+  int per_sm;
+  if (dtype == QAOA_C128) {
+    per_sm = two ? blocks_per_sm<CfgX2, true, true>(cost_bytes) : blocks_per_sm<CfgX1, true, false>(cost_bytes);
+  } else if (two) {
+    per_sm = blocks_per_sm<CfgF2, false, true>(cost_bytes);
+  } else {
+    per_sm = tile_bits == 12 ? blocks_per_sm<CfgF2, false, false>(cost_bytes)
+                             : blocks_per_sm<CfgF1, false, false>(cost_bytes);
+  }
   const int64_t cap = (int64_t)num_sms() * per_sm;
   return (int)(tiles < cap ? tiles : cap);
 }
 
-cudaError_t launch_sweep(int dtype, const SweepArgs& a, cudaStream_t s) {
-  const int bits = a.g.t + a.g.c;
-  const bool two = a.lam != nullptr;
+cudaError_t launch_sweep(int dtype, bool two, const SweepArgs& a, cudaStream_t s) {
   note_launch(0, s, true);
   if (dtype == QAOA_C128) {
-    max_blocks_per_sm<double>();
-    const size_t smem = (two ? 2 : 1) * sizeof(double2) << bits;
-    sweep_kernel<double><<<a.grid, kThreads, smem, s>>>(a);
+    if (two) launch_t<CfgX2, true, true>(a, s);
+    else launch_t<CfgX1, true, false>(a, s);
   } else {
-    max_blocks_per_sm<float>();
-    const size_t smem = (two ? 2 : 1) * sizeof(float2) << bits;
-    sweep_kernel<float><<<a.grid, kThreads, smem, s>>>(a);
+    if (two) launch_t<CfgF2, false, true>(a, s);
+    else if (a.tile_bits == 12) launch_t<CfgF2, false, false>(a, s);
+    else launch_t<CfgF1, false, false>(a, s);
   }
   note_launch(0, s, false, a.algo_bytes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expect(int dtype, const void* psi, const void* C, int cost_dtype, int n, double* partials,
+                          int grid, cudaStream_t s) {
+  const int64_t count = 1ll << n;
+  const double bytes = (double)count * ((dtype == QAOA_C128 ? 16.0 : 8.0) + (cost_dtype == QAOA_COST_F64 ? 8.0 : 4.0));
+  note_launch(0, s, true);
+  if (dtype == QAOA_C128)
+    expect_kernel<true><<<grid, 256, 0, s>>>(psi, C, cost_dtype == QAOA_COST_F64, count, partials, grid);
+  else
+    expect_kernel<false><<<grid, 256, 0, s>>>(psi, C, cost_dtype == QAOA_COST_F64, count, partials, grid);
+  note_launch(0, s, false, bytes);
   return cudaGetLastError();
 }
 
@@ -299,20 +858,35 @@ cudaError_t launch_reduce(const ReducePlan& r, const double* partials, double* o
   return cudaGetLastError();
 }
 
-cudaError_t launch_phase_table(int dtype, const double* gamma, int p, int64_t cmin, int64_t span,
-                               void* table, cudaStream_t s) {
-  SweepArgs a{};
-  for (int l = 0; l < p; ++l) a.gamma[l] = gamma[l];
-  a.cmin = cmin;
-  a.span = span;
-  const int64_t total = (int64_t)p * span;
+cudaError_t launch_tables(const TableArgs& t, cudaStream_t s) {
+  const int64_t total = (int64_t)t.p * t.span + (t.fx ? (int64_t)t.p * 196 + 3072 : 0);
+  if (total <= 0) return cudaSuccess;
   const int blocks = (int)((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024);
   note_launch(3, s, true);
-  if (dtype == QAOA_C128)
-    phase_table_kernel<double2><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(a, p, (double2*)table);
-  else
-    phase_table_kernel<float2><<<blocks > 0 ? blocks : 1, 256, 0, s>>>(a, p, (float2*)table);
+  tables_kernel<<<blocks, 256, 0, s>>>(t);
   note_launch(3, s, false);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cost_bound(const void* C, int f64, int n, unsigned long long* out, cudaStream_t s) {
+  note_launch(3, s, true, (double)(1ull << n) * (f64 ? 8.0 : 4.0));
+  cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  const int64_t count = 1ll << n;
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
+  cost_bound_kernel<<<(int)blocks, 256, 0, s>>>(C, f64, count, out);
+  note_launch(3, s, false, (double)(1ull << n) * (f64 ? 8.0 : 4.0));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm(const void* psi, int dtype, int n, double* partials, int* nblocks, cudaStream_t s) {
+  const int64_t count = 1ll << n;
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  *nblocks = (int)blocks;
+  note_launch(3, s, true);
+  norm_kernel<<<(int)blocks, 256, 0, s>>>(psi, dtype, count, partials);
+  note_launch(3, s, false, (double)count * (dtype == QAOA_C128 ? 16.0 : 8.0));
   return cudaGetLastError();
 }
 

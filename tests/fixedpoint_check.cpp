@@ -1,0 +1,84 @@
+// Host check of the fixed-point helpers in csrc/fixedpoint.cuh against 128-bit exact
+// arithmetic and the C library's correctly rounded conversions.  Exit 0 = all good.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <random>
+
+#include "fixedpoint.cuh"
+
+using namespace qaoa::fx;
+
+static long long q62(double x) { return llrint(ldexp(x, 62)); }
+
+int main() {
+  std::mt19937_64 rng(12345);
+  int fails = 0;
+  long long exact = 0, total = 0;
+  std::uniform_real_distribution<double> ang(0.0, 6.283185307179586);
+  for (int it = 0; it < 2000000; ++it) {
+    const int bits = 1 + (int)(rng() % 61);  // magnitudes from tiny to < 2^61
+    const long long lim = (1ll << bits) - 1;
+    const long long xr = (long long)(rng() % (2 * (unsigned long long)lim + 1)) - lim;
+    const long long xi = (long long)(rng() % (2 * (unsigned long long)lim + 1)) - lim;
+    const double th = ang(rng);
+    long long ur = q62(std::cos(th)), ui = q62(std::sin(th));
+    if (it % 97 == 0) { ur = 1ll << 62; ui = 0; }
+    if (it % 89 == 0) { ur = 0; ui = -(1ll << 62); }
+    const int e = (int)(rng() % 14);
+    const C64 a = cmul_q62(xr, xi, ur, ui, e);
+    const C64 b = cmul_q62_exact(xr, xi, ur, ui, e);
+    const long long dx = a.x - b.x, dy = a.y - b.y;
+    total += 2;
+    exact += (dx == 0) + (dy == 0);
+    if (dx > 1 || dx < -1 || dy > 1 || dy < -1) {
+      if (fails++ < 5) printf("cmul mismatch x=(%lld,%lld) u=(%lld,%lld) e=%d: %lld %lld vs %lld %lld\n", xr, xi, ur, ui,
+                              e, a.x, a.y, b.x, b.y);
+    }
+  }
+  if ((double)exact / (double)total < 0.9999) {
+    printf("cmul exact rate too low: %lld / %lld\n", exact, total);
+    ++fails;
+  }
+  for (int it = 0; it < 1000000; ++it) {
+    const long long x = (long long)(rng() >> (rng() % 63)) * ((rng() & 1) ? 1 : -1);
+    const int s = (int)(rng() % 120);
+    const double ref = ldexp((double)x, -s);  // int64 -> double is correctly rounded
+    const double got = to_double(x, s);
+    if (x != 0 && got != ref) {
+      if (fails++ < 10) printf("to_double(%lld, %d) = %.17g vs %.17g\n", x, s, got, ref);
+    }
+    const __int128 v = ((__int128)(long long)rng() << (rng() % 60)) + (long long)rng();
+    const int s2 = (int)(rng() % 200);
+    const double r2 = ldexp((double)v, -s2);
+    if (v != 0 && i128_to_double(v, s2) != r2) {
+      if (fails++ < 10) printf("i128_to_double mismatch\n");
+    }
+    const double d = ldexp((double)(long long)(rng() >> 11) - 4503599627370496.0, -(int)(rng() % 60));
+    const int s3 = (int)(rng() % 40);
+    if (std::fabs(ldexp(d, s3)) < 4.0e18) {
+      const long long r3 = llround(ldexp(d, s3));
+      if (from_double(d, s3) != r3) {
+        if (fails++ < 10) printf("from_double(%.17g, %d) = %lld vs %lld\n", d, s3, from_double(d, s3), r3);
+      }
+    }
+  }
+  // frac_turns: fixed points and period 1
+  if (frac_turns(0.5) != (1ull << 63) || frac_turns(-0.25) != 3ull << 62 || frac_turns(7.0) != 0ull ||
+      frac_turns(0.125) != (1ull << 61)) {
+    printf("frac_turns special values wrong\n");
+    ++fails;
+  }
+  for (int it = 0; it < 100000; ++it) {
+    const double d = ldexp((double)(rng() >> 11), -53) * 64.0 - 32.0;  // multiples of 2^-47 in [-32, 32)
+    const double k = (double)((long long)(rng() % 64) - 32);
+    const unsigned long long a = frac_turns(d), b = frac_turns(d + k);
+    const double back = ldexp((double)a, -64);
+    const double want = d - std::floor(d);
+    if (a != b || std::fabs(back - want) > 1e-15) {
+      if (fails++ < 10) printf("frac_turns(%.17g) = %llu\n", d, a);
+    }
+  }
+  printf(fails ? "FAIL %d\n" : "OK\n", fails);
+  return fails ? 1 : 0;
+}

@@ -118,6 +118,26 @@ def test_layers_parity(n, p, dtype):
         assert abs(nrm - 1.0) <= 1e-5
 
 
+@pytest.mark.parametrize("n,dtype,kind", [(22, "c128", "int"), (22, "c128", "u01"), (24, "c64", "int")])
+def test_layers_three_groups(n, dtype, kind):
+    """Sizes whose qubits split into three tile groups, compared element by element."""
+    g, e, w, integer = instance("reg3", n, 9, kind)
+    C = qaoa.cut_values(n, e, w, integer=integer)
+    cv = q.cost_vector(g, "i32" if integer else "f64")
+    gam, bet = synth.angles(3, 31)
+    psi = q.new_state(n, dtype)
+    out = to_np(q.apply_layers(psi, cv, gam, bet, expect=True))
+    ref = qaoa.qaoa_state(n, C, gam, bet)
+    Eref = qaoa.expectation(ref, C)
+    got = state_np(psi)
+    if dtype == "c128":
+        assert np.linalg.norm(got - ref) <= 1e-11
+        assert abs(out[0] - Eref) <= 1e-10 * scale_of(w)
+    else:
+        assert np.linalg.norm(got - ref) <= 1e-5
+        assert abs(out[0] - Eref) <= 1e-4 * max(1.0, abs(Eref))
+
+
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("n", [5, 12, 15])
 def test_layers_continue_from_state(n, dtype):
@@ -246,7 +266,7 @@ def test_sample_zero_shots_and_basis_state():
 # ------------------------------------------------------------------ S7 gradient
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-@pytest.mark.parametrize("n,p", [(3, 1), (8, 2), (12, 3), (15, 2), (17, 4)])
+@pytest.mark.parametrize("n,p", [(3, 1), (8, 2), (12, 3), (15, 2), (17, 4), (22, 2)])
 def test_gradient_parity(n, p, dtype):
     kind = "u01" if n % 2 else "int"
     g, e, w, integer = instance("gnp", n, n + p, kind, prob=0.4)
