@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <set>
@@ -137,6 +138,33 @@ struct Ctx {
 };
 
 static int cuda_status(cudaError_t e) { return e == cudaSuccess ? QAOA_OK : QAOA_ERR_CUDA; }
+
+// Whether a sweep matches one of the two lean kernel shapes: full tile with affine
+// layout-0 addresses, internal formats, and the op pattern MIX or MIX PHASE MIX (with
+// lambda: MIX+X, or MIX+X CTERM PHASE MIX+X).
+static int lean_kind(const Sweep& s, const Group& g, int tile_bits, int dtype, bool cost_f64) {
+  // measured on GB300: the lean shapes help the fixed-point (complex128) kernels; the
+  // float32 generic kernel is already faster than its lean form
+  if (dtype != QAOA_C128) return SWEEP_GENERIC;
+  const int rb = dtype == QAOA_C128 ? (s.two ? 3 : 4) : (tile_bits == 13 ? 5 : 4);
+  if (g.t + g.c != tile_bits || g.c > tile_bits - rb) return SWEEP_GENERIC;
+  if (s.init || s.load_user || s.store_user || !s.store_psi) return SWEEP_GENERIC;
+  if (s.two && !(s.load_lam && s.store_lam)) return SWEEP_GENERIC;
+  const uint32_t want_mix = s.two ? (F_PSI | F_LAM | F_XTERM) : F_PSI;
+  auto is = [](uint32_t op, uint32_t kind, uint32_t flags) {
+    return (op & 0xff) == kind && ((op & 0xff00) & ~(uint32_t)F_SIGN) == flags;
+  };
+  const std::vector<uint32_t>& o = s.ops;
+  if (o.size() == 1 && is(o[0], OP_MIX, want_mix)) return SWEEP_LEAN_MIX;
+  const bool chunky = g.j0 == 0 || (1 << g.c) >= (cost_f64 ? 2 : 4);
+  if (!chunky) return SWEEP_GENERIC;
+  if (!s.two && o.size() == 3 && is(o[0], OP_MIX, F_PSI) && is(o[1], OP_PHASE, F_PSI) && is(o[2], OP_MIX, F_PSI))
+    return SWEEP_LEAN_MERGED;
+  if (s.two && o.size() == 4 && is(o[0], OP_MIX, want_mix) && is(o[1], OP_RED_CTERM, F_PSI | F_LAM) &&
+      is(o[2], OP_PHASE, F_PSI | F_LAM) && is(o[3], OP_MIX, want_mix))
+    return SWEEP_LEAN_MERGED;
+  return SWEEP_GENERIC;
+}
 
 // Run a list of sweeps with one shared grid, then reduce the partials into out[0..nout).
 // Fixed-point (complex128) calls also get: the input scale from the norm of a loaded
@@ -276,6 +304,7 @@ static int run_sweeps(const Ctx& c, std::vector<Sweep>& sw, const std::vector<Gr
                          (reads_c ? cb : 0.0);
       a.algo_bytes = per * (double)(1ull << c.n);
     }
+    a.kind = lean_kind(s, g, tile_bits, c.dtype, c.cost->dtype == QAOA_COST_F64);
     int rc = cuda_status(launch_sweep(c.dtype, s.two, a, c.s));
     if (rc) return rc;
   }

@@ -46,7 +46,10 @@ struct SweepGeom {
   int64_t tiles;  // number of tiles = 2^(n - t - c)
 };
 
+enum SweepKind : int { SWEEP_GENERIC = 0, SWEEP_LEAN_MIX = 1, SWEEP_LEAN_MERGED = 2 };
+
 struct SweepArgs {
+  int kind;  // SweepKind: generic op program or one of the lean shapes
   void* psi;
   void* lam;
   const void* C;

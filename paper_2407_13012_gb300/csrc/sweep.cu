@@ -28,6 +28,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "fixedpoint.cuh"
@@ -69,8 +70,18 @@ using CfgX1 = Cfg<12, 4, 4, 3, 2>;
 // complex128 fixed point two buffers: 4096-amplitude tiles, 8 per thread per buffer, 512 threads
 using CfgX2 = Cfg<12, 3, 3, 3, 1>;
 
+// cost-tile slot of local index i; the XOR leaves the bits inside a 16-byte chunk alone so
+// the tile can be fetched with 16-byte asynchronous copies
 __device__ __forceinline__ uint32_t phys_cost(uint32_t i, bool f64) {
-  return f64 ? (i ^ ((i >> 4) & 15)) : (i ^ ((i >> 5) & 31));
+  return f64 ? (i ^ ((i >> 3) & 14)) : (i ^ ((i >> 3) & 28));
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 __device__ __forceinline__ uint64_t tile_base(const SweepGeom& g, int64_t tile) {
@@ -106,6 +117,16 @@ __device__ __forceinline__ double i128_to_double(i128 v, int s) { return fx::i12
 __device__ __forceinline__ long long double_to_fx(double d, int s) { return fx::from_double(d, s); }
 __device__ __forceinline__ unsigned long long frac_turns(double d) { return fx::frac_turns(d); }
 
+// exp(-2 pi i th) in float32 for a turn count th (the rare path of float costs or costs
+// outside the table); kept out of line so it does not raise the register budget of the
+// common path
+__device__ __noinline__ float2 phase_f32_direct(double th) {
+  const float f = (float)(th - rint(th));
+  float s, c;
+  sincospif(2.0f * f, &s, &c);
+  return make_float2(c, -s);
+}
+
 // exp(-2 pi i t / 2^64) in Q62 from three 1024-entry tables and a first-order residual
 __device__ __forceinline__ longlong2 turn_phase(unsigned long long t, const longlong2* __restrict__ tt) {
   const longlong2 e1 = tt[t >> 54];
@@ -134,11 +155,12 @@ struct Sweeper {
   static constexpr int R = CF::R;
 
   const SweepArgs& a;
-  V (&v)[R];
-  V (&w)[R];
+  V v[R];        // register tile of psi (layout cur)
+  V w[R];        // register tile of lambda (two-buffer sweeps)
   V* X;          // exchange buffer, 2^B slots
   void* Cs;      // cost tile, 2^B slots
   const V* Ts;   // shared-memory copy of one layer's phase table (or nullptr)
+  longlong2* Ds; // shared-memory mixer diagonal of the current fixed-point mixer (14 entries)
   int ts_layer;  // layer whose table Ts holds (-1: none)
   double* blk;   // block accumulators
   double* red;   // reduction scratch [2][NT/32]
@@ -149,22 +171,42 @@ struct Sweeper {
   uint64_t base;
   const uint32_t tid;
 
-  __device__ Sweeper(const SweepArgs& a_, V (&v_)[R], V (&w_)[R], V* X_, void* Cs_, double* blk_, double* red_)
-      : a(a_), v(v_), w(w_), X(X_), Cs(Cs_), Ts(nullptr), ts_layer(-1), blk(blk_), red(red_), cur(0), lam_shift(0),
+  __device__ Sweeper(const SweepArgs& a_, V* X_, void* Cs_, double* blk_, double* red_)
+      : a(a_), X(X_), Cs(Cs_), Ts(nullptr), Ds(nullptr), ts_layer(-1), blk(blk_), red(red_), cur(0), lam_shift(0),
         in_shift(0), evalid(0), base(0), tid(threadIdx.x) {}
 
   __device__ __forceinline__ uint32_t idx(int r) const { return CF::idx(cur, tid, r); }
 
-  __device__ void exchange_one(V (&u)[R], int to) {
+  // move u from layout F to layout T through the shared exchange buffer; layouts known at
+  // compile time so each slot address is one base plus an immediate
+  template <int F, int T>
+  __device__ __forceinline__ void ex(V (&u)[R]) {
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < R; ++r) X[CF::phys(CF::idx(cur, tid, r))] = u[r];
+    for (int r = 0; r < R; ++r) X[CF::phys(CF::idx(F, tid, r))] = u[r];
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < R; ++r) u[r] = X[CF::phys(CF::idx(to, tid, r))];
+    for (int r = 0; r < R; ++r) u[r] = X[CF::phys(CF::idx(T, tid, r))];
+  }
+  template <int F>
+  __device__ __forceinline__ void ex_from(V (&u)[R], int to) {
+    switch (to) {
+      case 0: ex<F, 0>(u); break;
+      case 1: if constexpr (CF::NR > 1) ex<F, (CF::NR > 1 ? 1 : 0)>(u); break;
+      case 2: if constexpr (CF::NR > 2) ex<F, (CF::NR > 2 ? 2 : 0)>(u); break;
+      default: if constexpr (CF::NR > 3) ex<F, (CF::NR > 3 ? 3 : 0)>(u); break;
+    }
+  }
+  __device__ __forceinline__ void exchange_one(V (&u)[R], int to) {
+    switch (cur) {
+      case 0: ex_from<0>(u, to); break;
+      case 1: if constexpr (CF::NR > 1) ex_from<(CF::NR > 1 ? 1 : 0)>(u, to); break;
+      case 2: if constexpr (CF::NR > 2) ex_from<(CF::NR > 2 ? 2 : 0)>(u, to); break;
+      default: if constexpr (CF::NR > 3) ex_from<(CF::NR > 3 ? 3 : 0)>(u, to); break;
+    }
   }
   // both buffers always share one layout
-  __device__ void go(int to) {
+  __device__ __forceinline__ void go(int to) {
     if (to == cur) return;
     exchange_one(v, to);
     if (TWO) exchange_one(w, to);
@@ -172,7 +214,7 @@ struct Sweeper {
   }
 
   // block-reduce and add to blk[r] (and blk[r + 1])
-  __device__ void block_add(int r, double v0, double v1, bool pair) {
+  __device__ __forceinline__ void block_add(int r, double v0, double v1, bool pair) {
     const int warp = tid >> 5, lane = tid & 31;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -209,28 +251,34 @@ struct Sweeper {
       if constexpr (FX) {
         e = turn_phase(frac_turns(th), (const longlong2*)a.turn_table);
       } else {
-        const float f = (float)(th - rint(th));
-        float s, c;
-        sincospif(2.0f * f, &s, &c);
-        e = make_float2(c, -s);
+        e = phase_f32_direct(th);
       }
     }
     if (inverse) e.y = -e.y;
     return e;
   }
 
-  __device__ void op_phase(int layer, bool inverse, bool on_psi, bool on_lam) {
+  template <bool INV>
+  __device__ __forceinline__ void phase_apply(V (&u)[R], int layer) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const uint32_t i = idx(r);
-      const V e = phase_factor(layer, inverse, i);
+      V e = phase_factor(layer, false, idx(r));
+      if constexpr (INV) e.y = -e.y;
       if constexpr (FX) {
-        if (on_psi) v[r] = cmul_fx(v[r], e, 0);
-        if (TWO && on_lam) w[r] = cmul_fx(w[r], e, 0);
+        u[r] = cmul_fx(u[r], e, 0);
       } else {
-        if (on_psi) v[r] = make_float2(v[r].x * e.x - v[r].y * e.y, v[r].x * e.y + v[r].y * e.x);
-        if (TWO && on_lam) w[r] = make_float2(w[r].x * e.x - w[r].y * e.y, w[r].x * e.y + w[r].y * e.x);
+        u[r] = make_float2(u[r].x * e.x - u[r].y * e.y, u[r].x * e.y + u[r].y * e.x);
       }
+    }
+  }
+
+  __device__ __forceinline__ void op_phase(int layer, bool inverse, bool on_psi, bool on_lam) {
+    if (inverse) {
+      if (on_psi) phase_apply<true>(v, layer);
+      if (TWO && on_lam) phase_apply<true>(w, layer);
+    } else {
+      if (on_psi) phase_apply<false>(v, layer);
+      if (TWO && on_lam) phase_apply<false>(w, layer);
     }
   }
 
@@ -249,74 +297,99 @@ struct Sweeper {
     x = make_float2(fmaf(-u, p.y, q.x), fmaf(u, p.x, q.y));
     y = make_float2(fmaf(-u, q.y, p.x), fmaf(u, q.x, p.y));
   }
-  __device__ void scale_f32(V (&u)[R], bool tanf, float m, int nb) {
-    // multiply by (m)^nb (tangent form) or (-i m)^nb (cotangent form)
-    float f = 1.f;
-    for (int j = 0; j < nb; ++j) f *= m;
-    const int rot = tanf ? 0 : (nb & 3);
+  // butterflies on the register bits set in todo, branch-free inside the pair loops
+  template <bool TAN>
+  __device__ __forceinline__ void bf_round(V (&u)[R], unsigned todo, float tu) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const float2 z = u[r];
-      float2 o;
-      if (rot == 0) o = make_float2(z.x, z.y);
-      else if (rot == 1) o = make_float2(z.y, -z.x);
-      else if (rot == 2) o = make_float2(-z.x, -z.y);
-      else o = make_float2(-z.y, z.x);
-      u[r] = make_float2(o.x * f, o.y * f);
+    for (int rb = 0; rb < CF::RB; ++rb) {
+      if (!((todo >> rb) & 1u)) continue;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (r & (1 << rb)) continue;
+        const int q = r | (1 << rb);
+        if constexpr (TAN) bf_tan(u[r], u[q], tu);
+        else bf_cot(u[r], u[q], tu);
+      }
     }
   }
 
-  __device__ void mix_f32(int layer, bool inverse, bool on_psi, bool on_lam, int xacc) {
+  // multiply every amplitude of u by the complex factor f
+  __device__ __forceinline__ void scale_f32(V (&u)[R], float2 f) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float2 z = u[r];
+      u[r] = make_float2(z.x * f.x - z.y * f.y, z.x * f.y + z.y * f.x);
+    }
+  }
+  // (m)^nb (tangent form) or (-i m)^nb (cotangent form)
+  __device__ __forceinline__ static float2 round_factor(bool tanf, float m, int nb) {
+    float f = 1.f;
+    for (int j = 0; j < nb; ++j) f *= m;
+    if (tanf) return make_float2(f, 0.f);
+    switch (nb & 3) {
+      case 0: return make_float2(f, 0.f);
+      case 1: return make_float2(0.f, -f);
+      case 2: return make_float2(-f, 0.f);
+      default: return make_float2(0.f, f);
+    }
+  }
+
+  __device__ __forceinline__ void mix_f32(int layer, bool inverse, bool on_psi, bool on_lam, int xacc) {
     const double cbd = a.cosb[layer], sbd = inverse ? -a.sinb[layer] : a.sinb[layer];
     const bool tanf = fabs(cbd) >= fabs(sbd);
     const float tu = tanf ? (float)(sbd / cbd) : (float)(cbd / sbd);
     const float m = tanf ? (float)cbd : (float)sbd;
     const int gl = a.g.c, gh = a.g.c + a.g.t;
     const bool rev = (cur == CF::NR - 1) && CF::NR > 1;
+    const bool xt = TWO && xacc >= 0;
     float xs = 0.f;
+    int pending = 0;  // qubits whose factor is not applied yet
     for (int s = 0; s < CF::NR; ++s) {
       const int k = rev ? CF::NR - 1 - s : s;
       const int l0 = CF::lo(k), l1 = CF::newhi(k);
       if (l1 <= gl || l0 >= gh) continue;  // no group qubit in this round
       go(k);
-      if (TWO && xacc >= 0) {  // sum over this round's qubits of Im(conj(la) pb + conj(lb) pa), state exact here
+      if (xt) {  // sum over this round's qubits of Im(conj(la) pb + conj(lb) pa); state exact here
 #pragma unroll
         for (int rb = 0; rb < CF::RB; ++rb) {
           const int b = l0 + rb;
-          if (b < l1 && b >= gl && b < gh) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-              if (r & (1 << rb)) continue;
-              const int q = r | (1 << rb);
-              xs += w[r].x * v[q].y - w[r].y * v[q].x + w[q].x * v[r].y - w[q].y * v[r].x;
-            }
-          }
-        }
-      }
-      int nb = 0;
-#pragma unroll
-      for (int rb = 0; rb < CF::RB; ++rb) {
-        const int b = l0 + rb;
-        if (b < l1 && b >= gl && b < gh) {
-          ++nb;
+          if (!(b < l1 && b >= gl && b < gh)) continue;
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             if (r & (1 << rb)) continue;
             const int q = r | (1 << rb);
-            if (tanf) {
-              if (on_psi) bf_tan(v[r], v[q], tu);
-              if (TWO && on_lam) bf_tan(w[r], w[q], tu);
-            } else {
-              if (on_psi) bf_cot(v[r], v[q], tu);
-              if (TWO && on_lam) bf_cot(w[r], w[q], tu);
-            }
+            xs += w[r].x * v[q].y - w[r].y * v[q].x + w[q].x * v[r].y - w[q].y * v[r].x;
           }
         }
       }
-      if (on_psi) scale_f32(v, tanf, m, nb);
-      if (TWO && on_lam) scale_f32(w, tanf, m, nb);
+      // which of this round's register bits are group qubits (uniform)
+      unsigned todo = 0;
+#pragma unroll
+      for (int rb = 0; rb < CF::RB; ++rb) {
+        const int b = l0 + rb;
+        if (b < l1 && b >= gl && b < gh) todo |= 1u << rb;
+      }
+      pending += __popc(todo);
+      if (tanf) {
+        if (on_psi) bf_round<true>(v, todo, tu);
+        if (TWO && on_lam) bf_round<true>(w, todo, tu);
+      } else {
+        if (on_psi) bf_round<false>(v, todo, tu);
+        if (TWO && on_lam) bf_round<false>(w, todo, tu);
+      }
+      if (xt && pending) {  // the X-terms of the next round need the exact state
+        const float2 f = round_factor(tanf, m, pending);
+        if (on_psi) scale_f32(v, f);
+        if (on_lam) scale_f32(w, f);
+        pending = 0;
+      }
     }
-    if (TWO && xacc >= 0) block_add(xacc, 2.0 * (double)xs, 0.0, false);
+    if (pending) {
+      const float2 f = round_factor(tanf, m, pending);
+      if (on_psi) scale_f32(v, f);
+      if (TWO && on_lam) scale_f32(w, f);
+    }
+    if (xt) block_add(xacc, 2.0 * (double)xs, 0.0, false);
   }
 
   // ---------------------------------------------------------------- mixer, fixed point: W D W
@@ -331,7 +404,7 @@ struct Sweeper {
       u[q] = make_longlong2(x.x - y.x, x.y - y.y);
     }
   }
-  __device__ void wht_round(int k, bool on_psi, bool on_lam) {
+  __device__ __forceinline__ void wht_round(int k, bool on_psi, bool on_lam) {
     const int l0 = CF::lo(k), l1 = CF::newhi(k);
     const int gl = a.g.c, gh = a.g.c + a.g.t;
 #pragma unroll
@@ -360,7 +433,28 @@ struct Sweeper {
     }
   }
 
-  __device__ void mix_fx(int layer, bool inverse, bool on_psi, bool on_lam, int xacc) {
+  // D multiply on the register tile: u[r] *= Ds[popcount] / 2^t; E = t >= 3 selects the
+  // shift form of the limb multiply at compile time
+  template <bool BIG>
+  __device__ __forceinline__ void d_mul(V (&u)[R], const longlong2* Ds, int gl, int t) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int pc = __popc((idx(r) >> gl) & ((1u << t) - 1));
+      const longlong2 e = Ds[pc];
+      fx::C64 o;
+      if constexpr (BIG) {
+        const fx::Limbs xr = fx::split(u[r].x), xi = fx::split(u[r].y), nxi = fx::split(-u[r].y);
+        const fx::Limbs er = fx::split(e.x), ei = fx::split(e.y);
+        o.x = fx::dot2_q62(xr, er, nxi, ei, t);
+        o.y = fx::dot2_q62(xr, ei, xi, er, t);
+      } else {
+        o = fx::cmul_q62(u[r].x, u[r].y, e.x, e.y, t);
+      }
+      u[r] = make_longlong2(o.x, o.y);
+    }
+  }
+
+  __device__ __forceinline__ void mix_fx(int layer, bool inverse, bool on_psi, bool on_lam, int xacc) {
     const int gl = a.g.c, gh = a.g.c + a.g.t, t = a.g.t;
     // rounds that hold group qubits, walked from the current layout outwards
     int ks[8], nk = 0;
@@ -370,29 +464,35 @@ struct Sweeper {
       if (CF::newhi(k) <= gl || CF::lo(k) >= gh) continue;
       ks[nk++] = k;
     }
+    // this mixer's diagonal exp(-i s b (t - 2k)), k = 0..t, into shared memory (sign applied)
+    __syncthreads();
+    if (tid <= (uint32_t)t) {
+      longlong2 e = __ldg((const longlong2*)a.d_table + ((long long)layer * 14 + t) * 14 + tid);
+      if (inverse) e.y = -e.y;
+      Ds[tid] = e;
+    }
     for (int j = 0; j < nk; ++j) {
       go(ks[j]);
       wht_round(ks[j], on_psi, on_lam);
     }
-    // D = exp(-i s b (t - 2 popcount(g))) / 2^t, with the X-term reduction on the way
-    const longlong2* dt = (const longlong2*)a.d_table + ((long long)layer * 14 + t) * 14;
-    i128 xs = 0;
+    __syncthreads();
+    if (TWO && xacc >= 0) {  // 2 Im <lam|sum_j X_j|psi> = 2 Im sum conj(lam~) (t - 2 popcount) psi~ 2^-t
+      i128 xs = 0;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const uint32_t i = idx(r);
-      const int pc = __popc((i >> gl) & ((1u << t) - 1));
-      longlong2 e = dt[pc];
-      if (inverse) e.y = -e.y;
-      if (TWO && xacc >= 0) {
+      for (int r = 0; r < R; ++r) {
+        const int pc = __popc((idx(r) >> gl) & ((1u << t) - 1));
         const i128 pr = (i128)w[r].x * v[r].y - (i128)w[r].y * v[r].x;  // Im(conj(lam~) psi~)
         xs += (pr >> 32) * (t - 2 * pc);
       }
-      if (on_psi) v[r] = cmul_fx(v[r], e, t);
-      if (TWO && on_lam) w[r] = cmul_fx(w[r], e, t);
-    }
-    if (TWO && xacc >= 0) {
-      // value = 2 * xs * 2^32 * 2^-t * 2^-2S (lambda also carries the scale 2^klam)
+      // value = 2 * xs * 2^32 * 2^-t * 2^-2S (lambda carries the scale 2^lam_shift)
       block_add(xacc, 2.0 * i128_to_double(xs, 2 * a.fx_shift + t - 32 - lam_shift), 0.0, false);
+    }
+    if (t >= 3) {
+      if (on_psi) d_mul<true>(v, Ds, gl, t);
+      if (TWO && on_lam) d_mul<true>(w, Ds, gl, t);
+    } else {
+      if (on_psi) d_mul<false>(v, Ds, gl, t);
+      if (TWO && on_lam) d_mul<false>(w, Ds, gl, t);
     }
     for (int j = nk - 1; j >= 0; --j) {
       go(ks[j]);
@@ -403,7 +503,7 @@ struct Sweeper {
   // ---------------------------------------------------------------- elementwise ops
   // lambda := C psi; fixed point stores lambda / 2^lam_shift (2^lam_shift >= max |C|) so
   // that lambda keeps the norm bound of the state
-  __device__ void op_lambda() {
+  __device__ __forceinline__ void op_lambda() {
     const bool f64 = a.cost_dtype == QAOA_COST_F64;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -423,7 +523,7 @@ struct Sweeper {
     }
   }
 
-  __device__ void op_expect(int acc) {
+  __device__ __forceinline__ void op_expect(int acc) {
     const bool f64 = a.cost_dtype == QAOA_COST_F64;
     double e0 = 0.0, e1 = 0.0;
     if constexpr (FX) {
@@ -456,7 +556,7 @@ struct Sweeper {
     block_add(acc, e0, e1, true);
   }
 
-  __device__ void op_cterm(int acc) {
+  __device__ __forceinline__ void op_cterm(int acc) {
     const bool f64 = a.cost_dtype == QAOA_COST_F64;
     double e0 = 0.0;
     if constexpr (FX) {
@@ -485,6 +585,298 @@ struct Sweeper {
   }
 };
 
+// ------------------------------------------------------------------ lean sweeps
+//
+// Most of the time goes to two sweep shapes: a mixer sweep (one group mixer) and a merged
+// sweep (mixer, phase, mixer; with lambda the adjoint X-terms, the C-term and the inverse
+// phase in between).  They get kernels whose layout sequence is fixed at compile time, so
+// each instance holds only the code it runs.  Tiles are full, the state is in the internal
+// format and layout 0 addresses are affine; the host checks all of that before choosing
+// them.
+
+template <class CF, bool FX, bool TWO>
+struct Lean : Sweeper<CF, FX, TWO> {
+  using B = Sweeper<CF, FX, TWO>;
+  using V = typename B::V;
+  static constexpr int R = CF::R, NR = CF::NR;
+  using B::B;
+
+  // group-qubit register bits of round K (relative to lo(K)), uniform
+  template <int K>
+  __device__ __forceinline__ unsigned gmask() const {
+    const int gl = this->a.g.c, gh = this->a.g.c + this->a.g.t;
+    unsigned m = 0;
+#pragma unroll
+    for (int rb = 0; rb < CF::RB; ++rb) {
+      const int b = CF::lo(K) + rb;
+      if (b < CF::newhi(K) && b >= gl && b < gh) m |= 1u << rb;
+    }
+    return m;
+  }
+  template <int F, int T>
+  __device__ __forceinline__ void exb() {
+    this->template ex<F, T>(this->v);
+    if constexpr (TWO) this->template ex<F, T>(this->w);
+    this->cur = T;
+  }
+  template <int K>
+  __device__ __forceinline__ uint32_t ix(int r) const { return CF::idx(K, this->tid, r); }
+
+  // ---- fixed point: W rounds, D multiply (and X-term) at layout L
+  __device__ __forceinline__ void wht_mask(V (&u)[R], unsigned m) {
+    if constexpr (FX) {
+      if (m & 1u) this->template wht_bit<0>(u);
+      if constexpr (CF::RB > 1) if (m & 2u) this->template wht_bit<(CF::RB > 1 ? 1 : 0)>(u);
+      if constexpr (CF::RB > 2) if (m & 4u) this->template wht_bit<(CF::RB > 2 ? 2 : 0)>(u);
+      if constexpr (CF::RB > 3) if (m & 8u) this->template wht_bit<(CF::RB > 3 ? 3 : 0)>(u);
+      if constexpr (CF::RB > 4) if (m & 16u) this->template wht_bit<(CF::RB > 4 ? 4 : 0)>(u);
+    }
+  }
+  template <int K>
+  __device__ __forceinline__ void wht_k(bool lam) {
+    const unsigned m = gmask<K>();
+    wht_mask(this->v, m);
+    if constexpr (TWO) if (lam) wht_mask(this->w, m);
+  }
+  template <int K, int L>
+  __device__ __forceinline__ void fx_fwd(bool lam) {
+    if constexpr (K > 0) exb<K - 1, K>();
+    wht_k<K>(lam);
+    if constexpr (K < L) fx_fwd<K + 1, L>(lam);
+  }
+  template <int K>
+  __device__ __forceinline__ void fx_back(bool lam) {
+    wht_k<K>(lam);
+    if constexpr (K > 0) {
+      exb<K, K - 1>();
+      fx_back<K - 1>(lam);
+    }
+  }
+  template <int L, bool BIG>
+  __device__ __forceinline__ void dmul_l(V (&u)[R], int gl, int t) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const longlong2 e = this->Ds[__popc((ix<L>(r) >> gl) & ((1u << t) - 1))];
+      fx::C64 o;
+      if constexpr (BIG) {
+        const fx::Limbs xr = fx::split(u[r].x), xi = fx::split(u[r].y), nxi = fx::split(-u[r].y);
+        const fx::Limbs er = fx::split(e.x), ei = fx::split(e.y);
+        o.x = fx::dot2_q62(xr, er, nxi, ei, t);
+        o.y = fx::dot2_q62(xr, ei, xi, er, t);
+      } else {
+        o = fx::cmul_q62(u[r].x, u[r].y, e.x, e.y, t);
+      }
+      u[r] = make_longlong2(o.x, o.y);
+    }
+  }
+  // W D W from layout 0 back to layout 0; D at layout L (the last round with group qubits)
+  template <int L>
+  __device__ __forceinline__ void fx_mixer(int layer, bool inverse, bool lam, int xacc) {
+    const int gl = this->a.g.c, t = this->a.g.t;
+    __syncthreads();
+    if (this->tid <= (uint32_t)t) {
+      longlong2 e = __ldg((const longlong2*)this->a.d_table + ((long long)layer * 14 + t) * 14 + this->tid);
+      if (inverse) e.y = -e.y;
+      this->Ds[this->tid] = e;
+    }
+    fx_fwd<0, L>(lam);
+    __syncthreads();
+    if constexpr (TWO) {
+      if (xacc >= 0) {
+        i128 xs = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int pc = __popc((ix<L>(r) >> gl) & ((1u << t) - 1));
+          const i128 pr = (i128)this->w[r].x * this->v[r].y - (i128)this->w[r].y * this->v[r].x;
+          xs += (pr >> 32) * (t - 2 * pc);
+        }
+        this->block_add(xacc, 2.0 * i128_to_double(xs, 2 * this->a.fx_shift + t - 32 - this->lam_shift), 0.0, false);
+      }
+    }
+    if (t >= 3) {
+      dmul_l<L, true>(this->v, gl, t);
+      if constexpr (TWO) if (lam) dmul_l<L, true>(this->w, gl, t);
+    } else {
+      dmul_l<L, false>(this->v, gl, t);
+      if constexpr (TWO) if (lam) dmul_l<L, false>(this->w, gl, t);
+    }
+    fx_back<L>(lam);
+  }
+
+  // ---- float32: rounds K..L forwards (F32_FWD) or K..0 backwards
+  template <int K>
+  __device__ __forceinline__ void f32_round(bool tanf, float tu, float m, bool lam, bool xt, float& xs, int& pending) {
+    if constexpr (!FX) {
+      const unsigned msk = gmask<K>();
+      if (xt) {
+#pragma unroll
+        for (int rb = 0; rb < CF::RB; ++rb) {
+          if (!((msk >> rb) & 1u)) continue;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            if (r & (1 << rb)) continue;
+            const int q = r | (1 << rb);
+            xs += this->w[r].x * this->v[q].y - this->w[r].y * this->v[q].x + this->w[q].x * this->v[r].y -
+                  this->w[q].y * this->v[r].x;
+          }
+        }
+      }
+      pending += __popc(msk);
+      if (tanf) {
+        this->template bf_round<true>(this->v, msk, tu);
+        if constexpr (TWO) if (lam) this->template bf_round<true>(this->w, msk, tu);
+      } else {
+        this->template bf_round<false>(this->v, msk, tu);
+        if constexpr (TWO) if (lam) this->template bf_round<false>(this->w, msk, tu);
+      }
+      if (xt && pending) {
+        const float2 f = B::round_factor(tanf, m, pending);
+        this->scale_f32(this->v, f);
+        if constexpr (TWO) if (lam) this->scale_f32(this->w, f);
+        pending = 0;
+      }
+    }
+  }
+  template <int K, int L>
+  __device__ __forceinline__ void f32_fwd(bool tanf, float tu, float m, bool lam, bool xt, float& xs, int& pending) {
+    if constexpr (K > 0) exb<K - 1, K>();
+    f32_round<K>(tanf, tu, m, lam, xt, xs, pending);
+    if constexpr (K < L) f32_fwd<K + 1, L>(tanf, tu, m, lam, xt, xs, pending);
+  }
+  template <int K>
+  __device__ __forceinline__ void f32_back(bool tanf, float tu, float m, bool lam, bool xt, float& xs, int& pending) {
+    f32_round<K>(tanf, tu, m, lam, xt, xs, pending);
+    if constexpr (K > 0) {
+      exb<K, K - 1>();
+      f32_back<K - 1>(tanf, tu, m, lam, xt, xs, pending);
+    }
+  }
+  // RX on the group from layout 0 to layout L (BACK = false) or from L to 0 (BACK = true)
+  template <int L, bool BACK>
+  __device__ __forceinline__ void f32_mixer(int layer, bool inverse, bool lam, int xacc) {
+    const double cbd = this->a.cosb[layer], sbd = inverse ? -this->a.sinb[layer] : this->a.sinb[layer];
+    const bool tanf = fabs(cbd) >= fabs(sbd);
+    const float tu = tanf ? (float)(sbd / cbd) : (float)(cbd / sbd);
+    const float m = tanf ? (float)cbd : (float)sbd;
+    const bool xt = TWO && xacc >= 0;
+    float xs = 0.f;
+    int pending = 0;
+    if constexpr (BACK) f32_back<L>(tanf, tu, m, lam, xt, xs, pending);
+    else f32_fwd<0, L>(tanf, tu, m, lam, xt, xs, pending);
+    if (pending) {
+      const float2 f = B::round_factor(tanf, m, pending);
+      this->scale_f32(this->v, f);
+      if constexpr (TWO) if (lam) this->scale_f32(this->w, f);
+    }
+    if (xt) this->block_add(xacc, 2.0 * (double)xs, 0.0, false);
+  }
+
+  // ---- the two sweep shapes; L = last round with group qubits
+  template <int L, bool MERGED>
+  __device__ __forceinline__ void run() {
+    const uint32_t* ops = this->a.ops;
+    const uint32_t o1 = ops[0];
+    const bool lam = TWO;
+    auto acc_of = [](uint32_t op) { return (op & F_XTERM) ? (int)((op >> 24) & 0xff) : -1; };
+    if constexpr (FX) {
+      fx_mixer<L>((o1 >> 16) & 0xff, o1 & F_SIGN, lam, acc_of(o1));
+      if constexpr (MERGED) {
+        const uint32_t oc = TWO ? ops[1] : 0u, op = ops[TWO ? 2 : 1], o2 = ops[TWO ? 3 : 2];
+        if constexpr (TWO) this->op_cterm((oc >> 24) & 0xff);
+        this->op_phase((op >> 16) & 0xff, op & F_SIGN, true, TWO);
+        fx_mixer<L>((o2 >> 16) & 0xff, o2 & F_SIGN, lam, acc_of(o2));
+      }
+    } else {
+      f32_mixer<L, false>((o1 >> 16) & 0xff, o1 & F_SIGN, lam, acc_of(o1));
+      if constexpr (MERGED) {
+        const uint32_t oc = TWO ? ops[1] : 0u, op = ops[TWO ? 2 : 1], o2 = ops[TWO ? 3 : 2];
+        if constexpr (TWO) this->op_cterm((oc >> 24) & 0xff);
+        this->op_phase((op >> 16) & 0xff, op & F_SIGN, true, TWO);
+        f32_mixer<L, true>((o2 >> 16) & 0xff, o2 & F_SIGN, lam, acc_of(o2));
+      } else {
+        if constexpr (L > 0) exb<L, 0>();
+      }
+    }
+  }
+};
+
+template <class CF, bool FX, bool TWO, bool MERGED, int LAST>
+__global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_constant__ SweepArgs a) {
+  using S = Lean<CF, FX, TWO>;
+  using V = typename S::V;
+  constexpr int R = CF::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* X = (V*)smem_raw;
+  void* Cs = smem_raw + (sizeof(V) << CF::B);
+  V* Tsm = (V*)((unsigned char*)Cs + (MERGED ? ((a.cost_dtype == QAOA_COST_F64 ? 8 : 4) << CF::B) : 0));
+  __shared__ double blk[kMaxAcc];
+  __shared__ double red[2 * (CF::NT / 32)];
+  __shared__ longlong2 dsm[16];
+  for (int r = threadIdx.x; r < kMaxAcc; r += CF::NT) blk[r] = 0.0;
+  S s(a, X, Cs, blk, red);
+  V (&v)[R] = s.v;
+  V (&w)[R] = s.w;
+  s.Ds = dsm;
+  if (MERGED && a.smem_table_layer >= 0) {
+    const V* src = (const V*)a.phase_table + (long long)a.smem_table_layer * a.span;
+    for (int k = threadIdx.x; k < a.span; k += CF::NT) Tsm[k] = __ldg(src + k);
+    s.Ts = Tsm;
+    s.ts_layer = a.smem_table_layer;
+  }
+  const SweepGeom& g = a.g;
+  s.evalid = 1u << CF::B;
+  if constexpr (FX && TWO) {
+    if (a.cmax_dev != nullptr) {
+      const unsigned long long b = *a.cmax_dev;
+      const int ex = (int)((b >> 52) & 0x7FF);
+      const int k = ex == 0 ? 0 : ex - 1023 + ((b & ((1ull << 52) - 1)) != 0 ? 1 : 0);
+      s.lam_shift = k < 0 ? 0 : k;
+    }
+  }
+  const uint32_t tid = threadIdx.x;
+  const bool cf64 = a.cost_dtype == QAOA_COST_F64;
+  const uint32_t tb0 = CF::idx(0, tid, 0);
+  const uint64_t zs = 1ull << (CF::lo(0) - g.c + g.j0);
+  __syncthreads();
+  for (int64_t tile = blockIdx.x; tile < g.tiles; tile += gridDim.x) {
+    const uint64_t base = tile_base(g, tile);
+    s.base = base;
+    s.cur = 0;
+    if constexpr (MERGED) {  // cost tile, 16-byte asynchronous copies
+      __syncthreads();
+      const int per = cf64 ? 2 : 4;
+      const uint32_t nch = (1u << CF::B) / per;
+      for (uint32_t ch = tid; ch < nch; ch += CF::NT) {
+        const uint32_t i = ch * per;
+        const uint64_t z = local_to_z(g, base, i);
+        cp_async16((char*)Cs + (size_t)phys_cost(i, cf64) * (cf64 ? 8 : 4), (const char*)a.C + z * (cf64 ? 8 : 4));
+      }
+    }
+    const uint64_t z0 = local_to_z(g, base, tb0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint64_t z = z0 + (uint64_t)r * zs;
+      v[r] = __ldg((const V*)a.psi + z);
+      if constexpr (TWO) w[r] = __ldg((const V*)a.lam + z);
+    }
+    if constexpr (MERGED) {
+      cp_async_wait_all();
+      __syncthreads();
+    }
+    s.template run<LAST, MERGED>();
+    const uint64_t z1 = local_to_z(g, base, tb0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint64_t z = z1 + (uint64_t)r * zs;
+      ((V*)a.psi)[z] = v[r];
+      if constexpr (TWO) ((V*)a.lam)[z] = w[r];
+    }
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < a.nred; r += CF::NT)
+    a.partials[(int64_t)a.red_slot[r] * a.grid + blockIdx.x] = blk[r];
+}
+
 template <class CF, bool FX, bool TWO>
 __global__ void __launch_bounds__(CF::NT, CF::MINB) sweep_kernel(const __grid_constant__ SweepArgs a) {
   using S = Sweeper<CF, FX, TWO>;
@@ -496,10 +888,13 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) sweep_kernel(const __grid_co
   V* Tsm = (V*)((unsigned char*)Cs + (a.needs_cost ? ((a.cost_dtype == QAOA_COST_F64 ? 8 : 4) << CF::B) : 0));
   __shared__ double blk[kMaxAcc];
   __shared__ double red[2 * (CF::NT / 32)];
+  __shared__ longlong2 dsm[16];
   for (int r = threadIdx.x; r < kMaxAcc; r += CF::NT) blk[r] = 0.0;
 
-  V v[R], w[R];
-  S s(a, v, w, X, Cs, blk, red);
+  S s(a, X, Cs, blk, red);
+  V (&v)[R] = s.v;
+  V (&w)[R] = s.w;
+  s.Ds = dsm;
   if (a.smem_table_layer >= 0) {  // one layer's phase table in shared memory
     const V* src = (const V*)a.phase_table + (long long)a.smem_table_layer * a.span;
     for (int k = threadIdx.x; k < a.span; k += CF::NT) Tsm[k] = __ldg(src + k);
@@ -529,25 +924,48 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) sweep_kernel(const __grid_co
     const uint64_t base = tile_base(g, tile);
     s.base = base;
     s.cur = 0;
-    // cost tile (linear order, coalesced)
+    // cost tile: 16-byte asynchronous copies when every chunk is contiguous in memory
+    // (the first group, or at least one chunk of carried low bits), element copies otherwise
     if (a.needs_cost) {
-      __syncthreads();
-      for (uint32_t i = tid; i < (1u << CF::B); i += CF::NT) {
-        // slots past the tile's valid range hold cost 0 (phase 1) so their zero
-        // amplitudes stay zero
-        const bool ok = i < s.evalid;
-        const uint64_t z = ok ? local_to_z(g, base, i) : 0;
-        if (cf64) ((double*)Cs)[phys_cost(i, true)] = ok ? __ldg((const double*)a.C + z) : 0.0;
-        else ((int*)Cs)[phys_cost(i, false)] = ok ? __ldg((const int*)a.C + z) : 0;
+      __syncthreads();  // the previous tile's ops are done with Cs
+      const int per = cf64 ? 2 : 4;  // elements per 16-byte chunk
+      const bool chunky = (g.j0 == 0) || ((1 << g.c) >= per);
+      if (chunky && s.evalid >= (uint32_t)per) {
+        const uint32_t nch = s.evalid / per;
+        for (uint32_t ch = tid; ch < nch; ch += CF::NT) {
+          const uint32_t i = ch * per;
+          const uint64_t z = local_to_z(g, base, i);
+          const char* src = (const char*)a.C + z * (cf64 ? 8 : 4);
+          char* dst = (char*)Cs + (size_t)phys_cost(i, cf64) * (cf64 ? 8 : 4);
+          cp_async16(dst, src);
+        }
+      } else {
+        for (uint32_t i = tid; i < s.evalid; i += CF::NT) {
+          const uint64_t z = local_to_z(g, base, i);
+          if (cf64) ((double*)Cs)[phys_cost(i, true)] = __ldg((const double*)a.C + z);
+          else ((int*)Cs)[phys_cost(i, false)] = __ldg((const int*)a.C + z);
+        }
       }
-      __syncthreads();
+      // slots past the tile's valid range hold cost 0 (phase 1) so their zero amplitudes
+      // stay zero
+      for (uint32_t i = s.evalid + tid; i < (1u << CF::B); i += CF::NT) {
+        if (cf64) ((double*)Cs)[phys_cost(i, true)] = 0.0;
+        else ((int*)Cs)[phys_cost(i, false)] = 0;
+      }
     }
-    // state (layout 0)
+    // state (layout 0): register r holds local index tb0 + (r << lo(0)), i.e. global index
+    // z0 + r * zs, since the register bits of layout 0 are group bits
+    // (when the carried low bits reach into the register bits, the general map is used)
+    {
+    const uint32_t tb0 = CF::idx(0, tid, 0);
+    const uint64_t z0 = local_to_z(g, base, tb0);
+    const bool affine = g.c <= CF::lo(0);
+    const uint64_t zs = affine ? (1ull << (CF::lo(0) - g.c + g.j0)) : 0ull;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const uint32_t i = CF::idx(0, tid, r);
+      const uint32_t i = tb0 + ((uint32_t)r << CF::lo(0));
       const bool ok = i < s.evalid;
-      const uint64_t z = ok ? local_to_z(g, base, i) : 0;
+      const uint64_t z = affine ? z0 + (uint64_t)r * zs : local_to_z(g, base, i);
       if constexpr (FX) {
         if (!ok) v[r] = make_longlong2(0, 0);
         else if (a.load_fmt == 2) v[r] = make_longlong2(a.init_fx, 0);
@@ -563,7 +981,12 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) sweep_kernel(const __grid_co
         if (TWO) w[r] = (ok && a.load_lam) ? __ldg((const float2*)a.lam + z) : make_float2(0.f, 0.f);
       }
     }
+    }
 
+    if (a.needs_cost) {
+      cp_async_wait_all();
+      __syncthreads();
+    }
     for (int k = 0; k < a.nops; ++k) {
       const uint32_t op = a.ops[k];
       const uint32_t kind = op & 0xff;
@@ -585,13 +1008,18 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) sweep_kernel(const __grid_co
       }
     }
 
-    // store (layout 0)
+    // store (layout 0); addresses recomputed rather than kept live through the ops
     s.go(0);
+    {
+    const uint32_t tb0 = CF::idx(0, tid, 0);
+    const uint64_t z0 = local_to_z(g, base, tb0);
+    const bool affine = g.c <= CF::lo(0);
+    const uint64_t zs = affine ? (1ull << (CF::lo(0) - g.c + g.j0)) : 0ull;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const uint32_t i = CF::idx(0, tid, r);
+      const uint32_t i = tb0 + ((uint32_t)r << CF::lo(0));
       if (i >= s.evalid) continue;
-      const uint64_t z = local_to_z(g, base, i);
+      const uint64_t z = affine ? z0 + (uint64_t)r * zs : local_to_z(g, base, i);
       if constexpr (FX) {
         if (a.store_fmt == 1) {
           ((double2*)a.psi)[z] = make_double2(fx_to_double(v[r].x, a.fx_shift - s.in_shift),
@@ -604,6 +1032,7 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) sweep_kernel(const __grid_co
         if (a.store_fmt >= 0) ((float2*)a.psi)[z] = v[r];
         if (TWO && a.store_lam) ((float2*)a.lam)[z] = w[r];
       }
+    }
     }
   }
 
@@ -745,12 +1174,46 @@ int blocks_per_sm(int cost_bytes) {
   return cached[slot];
 }
 
+template <class CF, bool FX, bool TWO, bool MERGED, int LAST>
+void lean_launch_l(const SweepArgs& a, size_t sm, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(lean_kernel<CF, FX, TWO, MERGED, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_bytes<CF, FX, TWO>(8, kSmemTable));
+    attr = true;
+  }
+  lean_kernel<CF, FX, TWO, MERGED, LAST><<<a.grid, CF::NT, sm, s>>>(a);
+}
+template <class CF, bool FX, bool TWO, bool MERGED>
+void lean_launch(const SweepArgs& a, int last, size_t sm, cudaStream_t s) {
+  switch (last) {
+    case 0: lean_launch_l<CF, FX, TWO, MERGED, 0>(a, sm, s); break;
+    case 1: lean_launch_l<CF, FX, TWO, MERGED, 1>(a, sm, s); break;
+    case 2: lean_launch_l<CF, FX, TWO, MERGED, 2>(a, sm, s); break;
+    default: lean_launch_l<CF, FX, TWO, MERGED, (CF::NR > 3 ? 3 : 2)>(a, sm, s); break;
+  }
+}
+
 template <class CF, bool FX, bool TWO>
 void launch_t(const SweepArgs& a, cudaStream_t s) {
   blocks_per_sm<CF, FX, TWO>(8);
   const int cb = a.needs_cost ? (a.cost_dtype == QAOA_COST_F64 ? 8 : 4) : 0;
   const int te = a.smem_table_layer >= 0 ? (int)a.span : 0;
-  sweep_kernel<CF, FX, TWO><<<a.grid, CF::NT, smem_bytes<CF, FX, TWO>(cb, te), s>>>(a);
+  const size_t sm = smem_bytes<CF, FX, TWO>(cb, te);
+  if (FX && (a.kind == SWEEP_LEAN_MIX || a.kind == SWEEP_LEAN_MERGED)) {
+    // last round holding group qubits selects the instance
+    int last = 0;
+    for (int k = 0; k < CF::NR; ++k) {
+      const int lo = std::max(0, CF::B - CF::RB * (k + 1)), hi = k == 0 ? CF::B : std::max(0, CF::B - CF::RB * k);
+      if (hi > a.g.c && lo < a.g.c + a.g.t) last = k;
+    }
+    if constexpr (FX) {
+      if (a.kind == SWEEP_LEAN_MERGED) lean_launch<CF, FX, TWO, true>(a, last, sm, s);
+      else lean_launch<CF, FX, TWO, false>(a, last, sm, s);
+    }
+    return;
+  }
+  sweep_kernel<CF, FX, TWO><<<a.grid, CF::NT, sm, s>>>(a);
 }
 
 // <C> and the norm of a user-format state, one pass (stand-alone expectation)
