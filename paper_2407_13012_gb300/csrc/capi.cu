@@ -146,8 +146,8 @@ static int lean_kind(const Sweep& s, const Group& g, int tile_bits, int dtype, b
   // measured on GB300: the lean shapes help the fixed-point (complex128) kernels; the
   // float32 generic kernel is already faster than its lean form
   if (dtype != QAOA_C128) return SWEEP_GENERIC;
-  const int rb = dtype == QAOA_C128 ? (s.two ? 3 : 4) : (tile_bits == 13 ? 5 : 4);
-  if (g.t + g.c != tile_bits || g.c > tile_bits - rb) return SWEEP_GENERIC;
+  const int rb = dtype == QAOA_C128 ? (s.two ? 3 : 4) : (tile_bits == 13 ? 5 : 4);  // float32 lean: unused
+  if (g.t + g.c != tile_bits || g.c > tile_bits - rb || g.t < 3) return SWEEP_GENERIC;
   if (s.init || s.load_user || s.store_user || !s.store_psi) return SWEEP_GENERIC;
   if (s.two && !(s.load_lam && s.store_lam)) return SWEEP_GENERIC;
   const uint32_t want_mix = s.two ? (F_PSI | F_LAM | F_XTERM) : F_PSI;
@@ -183,8 +183,10 @@ static int run_sweeps(const Ctx& c, std::vector<Sweep>& sw, const std::vector<Gr
   }
   for (const Group& g : gs) tmax = std::max(tmax, g.t);
   const int cost_bytes = c.cost->C_dev == nullptr ? 0 : (c.cost->dtype == QAOA_COST_I32 ? 4 : 8);
+  // one grid (the partials' stride) for all sweeps: sized for the single-buffer kernels;
+  // two-buffer kernels with fewer resident blocks per SM run it in waves
   int grid = sweep_grid(c.dtype, false, tile_bits, cost_bytes, max_tiles);
-  if (any_two) grid = std::min(grid, sweep_grid(c.dtype, true, tile_bits, cost_bytes, max_tiles));
+  if (any_two) grid = std::max(grid, sweep_grid(c.dtype, true, tile_bits, cost_bytes, max_tiles));
   grid = std::min(grid, kGridCap);
   // workspace carving
   char* p_ws = c.ws;

@@ -46,25 +46,28 @@ struct Cfg {
   static constexpr int R = 1 << RB_;        // amplitudes per thread (per buffer)
   static constexpr int NT = 1 << (B_ - RB_);  // threads per block
   static constexpr int NR = (B_ + RB_ - 1) / RB_;  // layouts (rounds)
-  __device__ static __forceinline__ int lo(int k) {
+  __host__ __device__ static constexpr int lo(int k) {
     const int v = B - RB * (k + 1);
     return v < 0 ? 0 : v;
   }
   // first local bit of round k that no earlier round covers: round k processes
   // [lo(k), newhi(k)) where newhi(0) = B and newhi(k) = lo(k - 1)
-  __device__ static __forceinline__ int newhi(int k) { return k == 0 ? B : lo(k - 1); }
-  __device__ static __forceinline__ uint32_t idx(int k, uint32_t tid, int r) {
+  __host__ __device__ static constexpr int newhi(int k) { return k == 0 ? B : lo(k - 1); }
+  __host__ __device__ static constexpr uint32_t idx(int k, uint32_t tid, int r) {
     const int l = lo(k);
     return (tid & ((1u << l) - 1)) | ((uint32_t)r << l) | ((tid >> l) << (l + RB));
   }
   // shared-memory slot of local index i: XOR-fold higher bits into the bank bits
-  __device__ static __forceinline__ uint32_t phys(uint32_t i) { return i ^ ((i >> SW_) & ((1u << SWW_) - 1)); }
+  __host__ __device__ static constexpr uint32_t phys(uint32_t i) { return i ^ ((i >> SW_) & ((1u << SWW_) - 1)); }
 };
 
 // complex64 single buffer: 8192-amplitude tiles, 32 per thread, 256 threads
 using CfgF1 = Cfg<13, 5, 5, 4, 2>;
 // complex64 two buffers (gradient): 4096-amplitude tiles, 16 per thread per buffer
 using CfgF2 = Cfg<12, 4, 4, 4, 2>;
+// complex64 two buffers (gradient) with 8192-amplitude tiles: 32 amplitudes per thread per
+// buffer, one block per SM; at n = 32 this keeps >= 3 carried low bits (64-byte rows)
+using CfgF3 = Cfg<13, 5, 5, 4, 1>;
 // complex128 fixed point single buffer: 4096-amplitude tiles, 16 per thread
 using CfgX1 = Cfg<12, 4, 4, 3, 2>;
 // complex128 fixed point two buffers: 4096-amplitude tiles, 8 per thread per buffer, 512 threads
@@ -127,6 +130,13 @@ __device__ __noinline__ float2 phase_f32_direct(double th) {
   return make_float2(c, -s);
 }
 
+__device__ __forceinline__ longlong2 turn_phase(unsigned long long t, const longlong2* __restrict__ tt);
+
+// exp(-2 pi i th) in Q62 for a turn count th (out of line, like phase_f32_direct)
+__device__ __noinline__ longlong2 phase_fx_direct(double th, const longlong2* __restrict__ tt) {
+  return turn_phase(frac_turns(th), tt);
+}
+
 // exp(-2 pi i t / 2^64) in Q62 from three 1024-entry tables and a first-order residual
 __device__ __forceinline__ longlong2 turn_phase(unsigned long long t, const longlong2* __restrict__ tt) {
   const longlong2 e1 = tt[t >> 54];
@@ -179,14 +189,17 @@ struct Sweeper {
 
   // move u from layout F to layout T through the shared exchange buffer; layouts known at
   // compile time so each slot address is one base plus an immediate
+  // The swizzle is linear over GF(2) and idx(k, tid, r) = idx(k, tid, 0) | (r << lo(k)) with
+  // disjoint bits, so a slot is the thread's base slot XOR a compile-time constant.
   template <int F, int T>
   __device__ __forceinline__ void ex(V (&u)[R]) {
+    const uint32_t pf = CF::phys(CF::idx(F, tid, 0)), pt = CF::phys(CF::idx(T, tid, 0));
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < R; ++r) X[CF::phys(CF::idx(F, tid, r))] = u[r];
+    for (int r = 0; r < R; ++r) X[pf ^ CF::phys((uint32_t)r << CF::lo(F))] = u[r];
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < R; ++r) u[r] = X[CF::phys(CF::idx(T, tid, r))];
+    for (int r = 0; r < R; ++r) u[r] = X[pt ^ CF::phys((uint32_t)r << CF::lo(T))];
   }
   template <int F>
   __device__ __forceinline__ void ex_from(V (&u)[R], int to) {
@@ -258,16 +271,47 @@ struct Sweeper {
     return e;
   }
 
+  __device__ __forceinline__ static V vmul(V x, V e) {
+    if constexpr (FX) {
+      return cmul_fx(x, e, 0);
+    } else {
+      return make_float2(x.x * e.x - x.y * e.y, x.x * e.y + x.y * e.x);
+    }
+  }
+  // phase factor of cost c computed directly (out of line: only costs outside the table and
+  // float costs take it)
+  __device__ __forceinline__ V phase_direct(int layer, double c) const {
+    if constexpr (FX) return phase_fx_direct(a.g2pi[layer] * c, (const longlong2*)a.turn_table);
+    else return phase_f32_direct(a.g2pi[layer] * c);
+  }
+  // psi (or lambda) *= exp(-i s gamma_l C): table lookups first, the rest out of line
   template <bool INV>
   __device__ __forceinline__ void phase_apply(V (&u)[R], int layer) {
+    const bool f64 = a.cost_dtype == QAOA_COST_F64;
+    unsigned miss = 0;
+    if (!f64 && a.phase_table != nullptr) {
+      const V* tab = layer == ts_layer ? Ts : (const V*)a.phase_table + (long long)layer * a.span;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      V e = phase_factor(layer, false, idx(r));
-      if constexpr (INV) e.y = -e.y;
-      if constexpr (FX) {
-        u[r] = cmul_fx(u[r], e, 0);
-      } else {
-        u[r] = make_float2(u[r].x * e.x - u[r].y * e.y, u[r].x * e.y + u[r].y * e.x);
+      for (int r = 0; r < R; ++r) {
+        const long long k = (long long)cost_i(Cs, idx(r)) - a.cmin;
+        if (k >= 0 && k < a.span) {
+          V e = tab[k];
+          if constexpr (INV) e.y = -e.y;
+          u[r] = vmul(u[r], e);
+        } else {
+          miss |= 1u << r;
+        }
+      }
+    } else {
+      miss = R == 32 ? 0xffffffffu : ((1u << R) - 1);
+    }
+    if (miss) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (!((miss >> r) & 1u)) continue;
+        V e = phase_direct(layer, cost_f(Cs, f64, idx(r)));
+        if constexpr (INV) e.y = -e.y;
+        u[r] = vmul(u[r], e);
       }
     }
   }
@@ -693,12 +737,18 @@ struct Lean : Sweeper<CF, FX, TWO> {
         this->block_add(xacc, 2.0 * i128_to_double(xs, 2 * this->a.fx_shift + t - 32 - this->lam_shift), 0.0, false);
       }
     }
-    if (t >= 3) {
-      dmul_l<L, true>(this->v, gl, t);
-      if constexpr (TWO) if (lam) dmul_l<L, true>(this->w, gl, t);
+    // lean sweeps run only on groups of >= 3 qubits, so the shift form of the multiply
+    // applies; the two-buffer kernels keep the branch (it schedules better there)
+    if constexpr (TWO) {
+      if (t >= 3) {
+        dmul_l<L, true>(this->v, gl, t);
+        if (lam) dmul_l<L, true>(this->w, gl, t);
+      } else {
+        dmul_l<L, false>(this->v, gl, t);
+        if (lam) dmul_l<L, false>(this->w, gl, t);
+      }
     } else {
-      dmul_l<L, false>(this->v, gl, t);
-      if constexpr (TWO) if (lam) dmul_l<L, false>(this->w, gl, t);
+      dmul_l<L, true>(this->v, gl, t);
     }
     fx_back<L>(lam);
   }
@@ -1264,9 +1314,8 @@ __global__ void expect_kernel(const void* __restrict__ psi, const void* __restri
 
 }  // namespace
 
-int sweep_tile_bits(int dtype, bool two) {
-  if (dtype == QAOA_C128) return 12;
-  return two ? 12 : 13;
+int sweep_tile_bits(int dtype, bool /*two*/) {
+  return dtype == QAOA_C128 ? 12 : 13;
 }
 
 // values stay below 2^61 through a group's Walsh-Hadamard transform (growth 2^(t/2)) for
@@ -1278,7 +1327,7 @@ int sweep_grid(int dtype, bool two, int tile_bits, int cost_bytes, int64_t tiles
   if (dtype == QAOA_C128) {
     per_sm = two ? blocks_per_sm<CfgX2, true, true>(cost_bytes) : blocks_per_sm<CfgX1, true, false>(cost_bytes);
   } else if (two) {
-    per_sm = blocks_per_sm<CfgF2, false, true>(cost_bytes);
+    per_sm = blocks_per_sm<CfgF3, false, true>(cost_bytes);
   } else {
     per_sm = tile_bits == 12 ? blocks_per_sm<CfgF2, false, false>(cost_bytes)
                              : blocks_per_sm<CfgF1, false, false>(cost_bytes);
@@ -1293,7 +1342,7 @@ cudaError_t launch_sweep(int dtype, bool two, const SweepArgs& a, cudaStream_t s
     if (two) launch_t<CfgX2, true, true>(a, s);
     else launch_t<CfgX1, true, false>(a, s);
   } else {
-    if (two) launch_t<CfgF2, false, true>(a, s);
+    if (two) launch_t<CfgF3, false, true>(a, s);
     else if (a.tile_bits == 12) launch_t<CfgF2, false, false>(a, s);
     else launch_t<CfgF1, false, false>(a, s);
   }
