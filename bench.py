@@ -68,6 +68,22 @@ def make_instance(a):
     return e, w, integer, gam, bet
 
 
+def reduce_max(x: float, device=None) -> float:
+    """Max of a per-rank scalar over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time (weak scaling)."""
+    return world * units_per_rank / seconds_max
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -311,14 +327,10 @@ def run_ours(a):
     launches = q.launch_count()
     q.timing_enable(False)
     kms, kla, kby, dropped = q.timing_read()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ev0.elapsed_time(ev1), dev)
     step_ms = ms / a.steps
     layers_per_step = 3 * a.p
-    value = world * layers_per_step * a.steps / (ms / 1e3)
+    value = job_throughput(layers_per_step * a.steps, world, ms / 1e3)
 
     # ---- end-to-end region (host buffers through the C ABI)
     for _ in range(1):
@@ -329,12 +341,8 @@ def run_ours(a):
     for _ in range(a.steps):
         step_e2e()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * layers_per_step * a.steps / e2e_s
+    e2e_s = reduce_max(time.perf_counter() - t0, dev)
+    e2e_value = job_throughput(layers_per_step * a.steps, world, e2e_s)
     h2d = e.nbytes + (w.nbytes if w is not None else 0) + gam.nbytes + bet.nbytes
     d2h = 16 + shots * 16 + (2 * a.p + 2) * 8
 
