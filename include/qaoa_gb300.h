@@ -63,7 +63,8 @@ enum qaoa_op {
   QAOA_OP_LAYERS = 1,
   QAOA_OP_EXPECTATION = 2,
   QAOA_OP_SAMPLE = 3,
-  QAOA_OP_GRADIENT = 4
+  QAOA_OP_GRADIENT = 4,
+  QAOA_OP_OPTIMIZE = 5
 };
 
 /*
@@ -227,6 +228,38 @@ int qaoa_sample_host(int n, int dtype, const void* psi_dev, const qaoa_cost_t* c
 int qaoa_gradient(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,
                   const double* gamma, const double* beta, int p, double* out_dev, void* ws_dev,
                   size_t ws_bytes, void* stream);
+
+/*
+ * As qaoa_gradient with the angles in device memory: angles_dev holds
+ * [gamma_1..p, beta_1..p] (2p doubles, read on the stream).  Nothing is read
+ * from the host, so the call can be captured in a CUDA graph after a first
+ * uncaptured call with the same sizes.
+ */
+int qaoa_gradient_dev(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,
+                      const double* angles_dev, int p, double* out_dev, void* ws_dev, size_t ws_bytes,
+                      void* stream);
+
+/*
+ * Gradient-based training of the angles (the paper offers L-BFGS and BFGS
+ * optimisers driven by the adjoint gradient, Sec. V-B): `steps` steps of Adam
+ * ascent on E = <C>, entirely on the device.  Each step runs qaoa_gradient_dev at
+ * angles_dev, then updates angles_dev in place:
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   angles += lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),  t = 1, 2, ...
+ * with g = dE/d[gamma, beta] and m = v = 0 at the start.  The first step runs
+ * directly; the remaining steps replay a CUDA graph of one step on `stream`
+ * (given the legacy default stream, NULL, the graph runs on a private blocking
+ * stream ordered after it), with no host round trip inside.
+ * history_dev (optional): steps x (4p + 2) doubles; row t = [E, <psi|psi>,
+ * dE/dgamma, dE/dbeta, gamma, beta] at the angles step t started from.
+ * Workspace: qaoa_workspace_size(..., QAOA_OP_OPTIMIZE, p, ...).  The call
+ * synchronises `stream` before returning.  On return angles_dev holds the final
+ * angles; psi_dev and lambda_dev are scratch.
+ */
+int qaoa_optimize_adam(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,
+                       double* angles_dev, int p, int64_t steps, double lr, double beta1,
+                       double beta2, double eps, double* history_dev, void* ws_dev,
+                       size_t ws_bytes, void* stream);
 
 /* As qaoa_gradient, then synchronise and copy the 2p+2 doubles to out_host. */
 int qaoa_gradient_host(int n, int dtype, void* psi_dev, void* lambda_dev,

@@ -26,14 +26,14 @@ QAOA_OK, QAOA_ERR_INVALID_ARG, QAOA_ERR_UNSUPPORTED, QAOA_ERR_CUDA, QAOA_ERR_TIM
 C128, C64 = 0, 1
 COST_I32, COST_F64 = 0, 1
 WEIGHT_INT, WEIGHT_F64 = 0, 1
-OP_COST, OP_LAYERS, OP_EXPECTATION, OP_SAMPLE, OP_GRADIENT = range(5)
+OP_COST, OP_LAYERS, OP_EXPECTATION, OP_SAMPLE, OP_GRADIENT, OP_OPTIMIZE = range(6)
 MAX_N, MAX_P, MAX_TABLE_SPAN = 32, 64, 16384
 
 EXPORTS = [
     "qaoa_version", "qaoa_strerror", "qaoa_graph_check", "qaoa_workspace_size", "qaoa_cost_vector",
     "qaoa_apply_layers", "qaoa_expectation", "qaoa_expectation_host", "qaoa_sample", "qaoa_sample_host",
     "qaoa_gradient", "qaoa_gradient_host", "qaoa_launch_count", "qaoa_launch_count_reset",
-    "qaoa_timing_enable", "qaoa_timing_read",
+    "qaoa_timing_enable", "qaoa_timing_read", "qaoa_gradient_dev", "qaoa_optimize_adam", "qaoa_expectation_noalloc",
 ]
 
 
@@ -71,6 +71,9 @@ def _load() -> ct.CDLL:
         "qaoa_sample_host": ([i32, i32, vp, ct.POINTER(CostT), i64, u64, vp, vp, vp, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_gradient": ([i32, i32, vp, vp, ct.POINTER(CostT), dp, dp, i32, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_gradient_host": ([i32, i32, vp, vp, ct.POINTER(CostT), dp, dp, i32, vp, dp, vp, ct.c_size_t, vp], i32),
+        "qaoa_gradient_dev": ([i32, i32, vp, vp, ct.POINTER(CostT), vp, i32, vp, vp, ct.c_size_t, vp], i32),
+        "qaoa_optimize_adam": ([i32, i32, vp, vp, ct.POINTER(CostT), vp, i32, i64, ct.c_double, ct.c_double,
+                                ct.c_double, ct.c_double, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_launch_count": ([], i64),
         "qaoa_launch_count_reset": ([], None),
         "qaoa_timing_enable": ([i32], i32),
@@ -288,6 +291,80 @@ def gradient(psi, lam, cost: CostVector, gammas, betas):
                               len(g), ct.c_void_p(out.data_ptr()), ct.c_void_p(ws.data_ptr()), ws.numel(),
                               ct.c_void_p(_stream(psi.device))), "gradient")
     return out
+
+
+def gradient_dev(psi, lam, cost: CostVector, angles):
+    """S7 with device-resident angles [gamma_1..p, beta_1..p] (float64 CUDA tensor)."""
+    torch = _torch()
+    _require_cuda(psi, lam, angles)
+    if angles.dtype != torch.float64 or angles.numel() % 2:
+        raise ValueError("angles must be a float64 tensor of length 2p")
+    n = int(round(math.log2(psi.numel())))
+    p = angles.numel() // 2
+    dt = _dtype_code(psi)
+    ws = _workspace(workspace_size(n, dt, OP_GRADIENT, p, 0, cost.span), psi.device)
+    out = torch.empty(2 * p + 2, dtype=torch.float64, device=psi.device)
+    cs = cost.struct()
+    _check(_lib.qaoa_gradient_dev(n, dt, ct.c_void_p(psi.data_ptr()), ct.c_void_p(lam.data_ptr()), ct.byref(cs),
+                                  ct.c_void_p(angles.data_ptr()), p, ct.c_void_p(out.data_ptr()),
+                                  ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(_stream(psi.device))),
+           "gradient_dev")
+    return out
+
+
+class QAOAExpectation:
+    """E(angles) = <C> of the depth-p state as a differentiable torch function.
+
+    Forward runs the adjoint pass once (qaoa_gradient_dev) and keeps dE/dangles for the
+    backward; angles = [gamma_1..p, beta_1..p] on the device (float64).  The state and
+    lambda buffers are scratch owned by this object.
+    """
+
+    def __init__(self, cost: CostVector, dtype: str = "c128"):
+        self.cost = cost
+        self.psi = new_state(cost.n, dtype, cost.C.device)
+        self.lam = new_state(cost.n, dtype, cost.C.device)
+        torch = _torch()
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, angles):
+                out = gradient_dev(self.psi, self.lam, self.cost, angles.detach().contiguous())
+                ctx.save_for_backward(out[2:].clone())
+                return out[0].clone()
+
+            @staticmethod
+            def backward(ctx, grad_out):
+                (g,) = ctx.saved_tensors
+                return grad_out * g
+
+        self._fn = _Fn
+
+    def __call__(self, angles):
+        return self._fn.apply(angles)
+
+
+def optimize_adam(cost: CostVector, angles, steps: int, lr: float = 0.01, betas=(0.9, 0.999), eps: float = 1e-8,
+                  dtype: str = "c128", history: bool = True):
+    """Adam ascent on <C> for `steps` steps, entirely on the device (one CUDA graph per
+    step replayed).  angles: float64 CUDA tensor [gamma, beta] updated in place.
+    Returns the history tensor (steps x (4p + 2)): [E, norm, dE/dgamma, dE/dbeta, gamma, beta]."""
+    torch = _torch()
+    _require_cuda(angles)
+    p = angles.numel() // 2
+    n = cost.n
+    dt = C128 if dtype == "c128" else C64
+    psi = new_state(n, dtype, angles.device)
+    lam = new_state(n, dtype, angles.device)
+    ws = _workspace(workspace_size(n, dt, OP_OPTIMIZE, p, 0, cost.span), angles.device)
+    hist = torch.empty((max(steps, 1), 4 * p + 2), dtype=torch.float64, device=angles.device) if history else None
+    cs = cost.struct()
+    _check(_lib.qaoa_optimize_adam(n, dt, ct.c_void_p(psi.data_ptr()), ct.c_void_p(lam.data_ptr()), ct.byref(cs),
+                                   ct.c_void_p(angles.data_ptr()), p, steps, lr, betas[0], betas[1], eps,
+                                   ct.c_void_p(hist.data_ptr() if hist is not None else 0),
+                                   ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(_stream(angles.device))),
+           "optimize_adam")
+    return hist[:steps] if hist is not None else None
 
 
 def launch_count() -> int:

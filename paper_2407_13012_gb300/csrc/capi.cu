@@ -47,6 +47,8 @@ cudaEvent_t pool_event() {
 void note_launch(int kind, cudaStream_t s, bool begin, double bytes) {
   if (begin) g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!g_timing_on) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return;  // graph capture
   std::lock_guard<std::mutex> lk(g_timing_mu);
   if (begin) {
     if ((int)g_timed.size() >= kMaxTimed) {
@@ -113,6 +115,7 @@ static int64_t tiles_of(const Group& g, int n) { return 1ll << (n - g.t - g.c); 
 constexpr int kGridCap = 2048;
 constexpr size_t kScalarBytes = 256;                     // norm^2 (double), max|C| bits (u64)
 constexpr size_t kNormPartialBytes = 1024 * sizeof(double);
+constexpr size_t kTrigBytes = 3 * QAOA_MAX_P * sizeof(double);  // per-layer terms of device angles
 
 static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 static size_t partial_bytes(int nout) { return round256((size_t)nout * kMaxContrib * kGridCap * sizeof(double)); }
@@ -124,8 +127,13 @@ static size_t fx_table_bytes(int dtype, int p) {
   if (dtype != QAOA_C128) return 0;
   return round256((size_t)p * 196 * 16) + round256(3072 * 16);
 }
+// workspace of the optimiser beyond the gradient's: Adam moments (4p), step counter,
+// gradient output (2p + 2)
+static size_t adam_extra_bytes(int p) {
+  return round256((4 * p + 1) * sizeof(double)) + round256((2 * p + 2) * sizeof(double));
+}
 static size_t layer_ws_bytes(int dtype, int p, int64_t span, int nout) {
-  return kScalarBytes + kNormPartialBytes + partial_bytes(nout) + phase_table_bytes(dtype, p, span) +
+  return kScalarBytes + kNormPartialBytes + kTrigBytes + partial_bytes(nout) + phase_table_bytes(dtype, p, span) +
          fx_table_bytes(dtype, p);
 }
 
@@ -170,7 +178,7 @@ static int lean_kind(const Sweep& s, const Group& g, int tile_bits, int dtype, b
 // Fixed-point (complex128) calls also get: the input scale from the norm of a loaded
 // user state, the lambda scale from max |C| (gradient), and the mixer/turn tables.
 static int run_sweeps(const Ctx& c, std::vector<Sweep>& sw, const std::vector<Group>& gs, int tile_bits, void* psi,
-                      void* lam, const double* gamma, const double* beta, int p, int nout,
+                      void* lam, const double* gamma, const double* beta, const double* ang_dev, int p, int nout,
                       const std::vector<int>& ncontrib, double* out) {
   const bool fx = c.dtype == QAOA_C128;
   bool any_two = false, any_user_load = false;
@@ -195,6 +203,8 @@ static int run_sweeps(const Ctx& c, std::vector<Sweep>& sw, const std::vector<Gr
   p_ws += kScalarBytes;
   double* norm_part = (double*)p_ws;
   p_ws += kNormPartialBytes;
+  double* trig = (double*)p_ws;
+  p_ws += kTrigBytes;
   double* partials = (double*)p_ws;
   p_ws += partial_bytes(nout);
   const bool int_cost = c.cost->dtype == QAOA_COST_I32;
@@ -217,9 +227,13 @@ static int run_sweeps(const Ctx& c, std::vector<Sweep>& sw, const std::vector<Gr
     t.p = p;
     t.cmin = cmin;
     t.span = span;
-    for (int l = 0; l < p; ++l) {
-      t.gamma[l] = gamma[l];
-      t.beta[l] = beta[l];
+    if (ang_dev != nullptr) {
+      t.dev_angles = ang_dev;
+    } else {
+      for (int l = 0; l < p; ++l) {
+        t.gamma[l] = gamma[l];
+        t.beta[l] = beta[l];
+      }
     }
     t.phase = phase_table;
     t.dtab = d_table;
@@ -245,6 +259,10 @@ static int run_sweeps(const Ctx& c, std::vector<Sweep>& sw, const std::vector<Gr
     if (rc) return rc;
   }
 
+  if (ang_dev != nullptr && p > 0) {
+    int rc = cuda_status(launch_angle_prep(ang_dev, p, trig, c.s));
+    if (rc) return rc;
+  }
   const double amp0 = std::pow(2.0, -0.5 * c.n);
   const int S = fx_shift_for(tmax);
   for (const Sweep& s : sw) {
@@ -275,10 +293,14 @@ static int run_sweeps(const Ctx& c, std::vector<Sweep>& sw, const std::vector<Gr
       reads_c |= (kind == OP_PHASE || kind == OP_LAMBDA || kind == OP_RED_EXPECT || kind == OP_RED_CTERM);
     }
     a.needs_cost = reads_c;
-    for (int l = 0; l < p; ++l) {
-      a.g2pi[l] = gamma[l] / (2.0 * 3.14159265358979323846);
-      a.cosb[l] = std::cos(beta[l]);
-      a.sinb[l] = std::sin(beta[l]);
+    a.np = p;
+    a.dev_trig = ang_dev != nullptr ? trig : nullptr;
+    if (ang_dev == nullptr) {
+      for (int l = 0; l < p; ++l) {
+        a.g2pi[l] = gamma[l] / (2.0 * 3.14159265358979323846);
+        a.cosb[l] = std::cos(beta[l]);
+        a.sinb[l] = std::sin(beta[l]);
+      }
     }
     a.phase_table = phase_table;
     a.cmin = cmin;
@@ -419,6 +441,7 @@ int qaoa_workspace_size(int n, int dtype, int op, int p, int64_t shots, int64_t 
     case QAOA_OP_EXPECTATION: b = partial_bytes(2) + 256; break;
     case QAOA_OP_SAMPLE: b = round256(sample_ws_bytes(n, dtype)); break;
     case QAOA_OP_GRADIENT: b = layer_ws_bytes(dtype, p, cost_span, 2 * p + 2); break;
+    case QAOA_OP_OPTIMIZE: b = layer_ws_bytes(dtype, p, cost_span, 2 * p + 2) + adam_extra_bytes(p); break;
     default: return QAOA_ERR_INVALID_ARG;
   }
   *bytes = b;
@@ -500,7 +523,7 @@ int qaoa_apply_layers(int n, int dtype, void* psi_dev, const qaoa_cost_t* cost, 
   }
   qaoa_cost_t dummy{nullptr, QAOA_COST_F64, 1, 0};
   Ctx c{n, dtype, cost ? cost : &dummy, (cudaStream_t)stream, (char*)ws_dev, ws_bytes};
-  return run_sweeps(c, sw, gs, B, psi_dev, nullptr, gamma, beta, p, nout, ncontrib, expect_dev);
+  return run_sweeps(c, sw, gs, B, psi_dev, nullptr, gamma, beta, nullptr, p, nout, ncontrib, expect_dev);
 }
 
 int qaoa_expectation(int n, int dtype, const void* psi_dev, const qaoa_cost_t* cost, double* out_dev,
@@ -585,11 +608,17 @@ int qaoa_sample_host(int n, int dtype, const void* psi_dev, const qaoa_cost_t* c
   return cuda_status(cudaStreamSynchronize(s));
 }
 
-int qaoa_gradient(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost, const double* gamma,
-                  const double* beta, int p, double* out_dev, void* ws_dev, size_t ws_bytes, void* stream) {
+}  // extern "C"
+
+// The adjoint gradient with angles either on the host (gamma, beta) or on the device
+// (ang_dev = [gamma p | beta p]).
+static int gradient_impl(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,
+                         const double* gamma, const double* beta, const double* ang_dev, int p, double* out_dev,
+                         void* ws_dev, size_t ws_bytes, void* stream) {
   if (n < 1 || n > QAOA_MAX_N || !valid_dtype(dtype) || psi_dev == nullptr || lambda_dev == nullptr ||
-      out_dev == nullptr || !valid_cost(cost) || !angles_ok(gamma, beta, p) || p < 1)
+      out_dev == nullptr || !valid_cost(cost) || p < 1 || p > QAOA_MAX_P)
     return QAOA_ERR_INVALID_ARG;
+  if (ang_dev == nullptr && !angles_ok(gamma, beta, p)) return QAOA_ERR_INVALID_ARG;
   if (psi_dev == lambda_dev) return QAOA_ERR_INVALID_ARG;
   const int64_t span = (cost->dtype == QAOA_COST_I32 && cost->cmax >= cost->cmin) ? cost->cmax - cost->cmin + 1 : 0;
   size_t need = 0;
@@ -641,7 +670,84 @@ int qaoa_gradient(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_
   for (const Sweep& s : sw)
     if ((int)s.red_slot.size() > 255) return QAOA_ERR_UNSUPPORTED;
   Ctx c{n, dtype, cost, (cudaStream_t)stream, (char*)ws_dev, ws_bytes};
-  return run_sweeps(c, sw, gs, B, psi_dev, lambda_dev, gamma, beta, p, nout, ncontrib, out_dev);
+  return run_sweeps(c, sw, gs, B, psi_dev, lambda_dev, gamma, beta, ang_dev, p, nout, ncontrib, out_dev);
+}
+
+extern "C" {
+
+int qaoa_gradient(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost, const double* gamma,
+                  const double* beta, int p, double* out_dev, void* ws_dev, size_t ws_bytes, void* stream) {
+  return gradient_impl(n, dtype, psi_dev, lambda_dev, cost, gamma, beta, nullptr, p, out_dev, ws_dev, ws_bytes,
+                       stream);
+}
+
+int qaoa_gradient_dev(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,
+                      const double* angles_dev, int p, double* out_dev, void* ws_dev, size_t ws_bytes, void* stream) {
+  if (angles_dev == nullptr) return QAOA_ERR_INVALID_ARG;
+  return gradient_impl(n, dtype, psi_dev, lambda_dev, cost, nullptr, nullptr, angles_dev, p, out_dev, ws_dev,
+                       ws_bytes, stream);
+}
+
+
+int qaoa_optimize_adam(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,
+                       double* angles_dev, int p, int64_t steps, double lr, double beta1, double beta2, double eps,
+                       double* history_dev, void* ws_dev, size_t ws_bytes, void* stream) {
+  if (angles_dev == nullptr || steps < 0 || !(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) ||
+      !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0) || p < 1 || p > QAOA_MAX_P || !valid_cost(cost))
+    return QAOA_ERR_INVALID_ARG;
+  size_t need = 0;
+  const int64_t span = (cost->dtype == QAOA_COST_I32 && cost->cmax >= cost->cmin) ? cost->cmax - cost->cmin + 1 : 0;
+  int rc = qaoa_workspace_size(n, dtype, QAOA_OP_OPTIMIZE, p, 0, span, &need);
+  if (rc) return rc;
+  if (ws_dev == nullptr || ws_bytes < need) return QAOA_ERR_WORKSPACE;
+  const size_t gbytes = need - adam_extra_bytes(p);
+  char* extra = (char*)ws_dev + gbytes;
+  double* state = (double*)extra;
+  long long* counter = (long long*)(state + 4 * p);
+  double* gout = (double*)(extra + round256((4 * p + 1) * sizeof(double)));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(state, 0, (4 * p + 1) * sizeof(double), s) != cudaSuccess) return QAOA_ERR_CUDA;
+  if (steps == 0) return QAOA_OK;
+  cudaStream_t cur = s;
+  auto iteration = [&]() {
+    int r = gradient_impl(n, dtype, psi_dev, lambda_dev, cost, nullptr, nullptr, angles_dev, p, gout, ws_dev, gbytes,
+                          (void*)cur);
+    if (r) return r;
+    return cuda_status(launch_adam(angles_dev, gout, state, counter, p, lr, beta1, beta2, eps, history_dev, steps, cur));
+  };
+  // first step directly (it also settles every per-kernel setting), the rest from a CUDA
+  // graph of one step replayed on the stream: no host round trip inside the loop
+  rc = iteration();
+  if (rc) return rc;
+  if (steps == 1) return cuda_status(cudaStreamSynchronize(s));
+  // the legacy default stream cannot be captured: capture on a private blocking stream,
+  // which is ordered after (and before) work on the legacy stream
+  bool own = false;
+  if (s == nullptr) {
+    if (cudaStreamCreate(&cur) != cudaSuccess) return QAOA_ERR_CUDA;
+    own = true;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int out = QAOA_OK;
+  if (cudaStreamBeginCapture(cur, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    out = QAOA_ERR_CUDA;
+  } else {
+    const int rc_cap = iteration();
+    const cudaError_t ec = cudaStreamEndCapture(cur, &graph);
+    if (rc_cap != QAOA_OK || ec != cudaSuccess) out = rc_cap != QAOA_OK ? rc_cap : QAOA_ERR_CUDA;
+    else if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) out = QAOA_ERR_CUDA;
+  }
+  if (out == QAOA_OK) {
+    cudaError_t e = cudaSuccess;
+    for (int64_t k = 1; k < steps && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, cur);
+    if (e != cudaSuccess) out = QAOA_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(cur) != cudaSuccess && out == QAOA_OK) out = QAOA_ERR_CUDA;
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (own) cudaStreamDestroy(cur);
+  return out;
 }
 
 int qaoa_gradient_host(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,

@@ -68,7 +68,10 @@ struct SweepArgs {
   const unsigned long long* cmax_dev;  // optional: bits of max |C| (lambda scale)
   int nops;
   uint32_t ops[kMaxOps];
-  // per layer angles, indexed by the op's layer field
+  // per layer angles, indexed by the op's layer field (dev_trig overrides them when the
+  // angles live in device memory: [g2pi np | cos np | sin np])
+  const double* dev_trig;
+  int np;
   double g2pi[QAOA_MAX_P];  // gamma / (2 pi)
   double cosb[QAOA_MAX_P];
   double sinb[QAOA_MAX_P];
@@ -101,6 +104,7 @@ struct ReducePlan {
 struct TableArgs {
   int fx;        // fixed point tables (complex128) or float32 (complex64)
   int p;
+  const double* dev_angles;  // device [gamma p | beta p], overrides gamma/beta when set
   int64_t cmin, span;  // integer-cost phase table (span 0 = none)
   double gamma[QAOA_MAX_P];
   double beta[QAOA_MAX_P];
@@ -115,6 +119,9 @@ cudaError_t launch_reduce(const ReducePlan& r, const double* partials, double* o
 cudaError_t launch_tables(const TableArgs& t, cudaStream_t s);
 cudaError_t launch_cost_bound(const void* C, int f64, int n, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_norm(const void* psi, int dtype, int n, double* partials, int* nblocks, cudaStream_t s);
+cudaError_t launch_angle_prep(const double* ang, int p, double* trig, cudaStream_t s);
+cudaError_t launch_adam(double* ang, const double* g, double* state, long long* step, int p, double lr, double b1,
+                        double b2, double eps, double* history, long long max_steps, cudaStream_t s);
 cudaError_t launch_expect(int dtype, const void* psi, const void* C, int cost_dtype, int n, double* partials,
                           int grid, cudaStream_t s);
 int sweep_tile_bits(int dtype, bool two);     // B of the kernel a sweep uses

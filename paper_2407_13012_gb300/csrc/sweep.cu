@@ -154,6 +154,18 @@ __device__ __forceinline__ longlong2 turn_phase(unsigned long long t, const long
 
 // ------------------------------------------------------------------ kernel
 
+// per-layer angle terms: kernel parameters, or device memory ([g2pi p | cos p | sin p],
+// written by angle_prep_kernel) when the angles live on the device
+__device__ __forceinline__ double arg_g2pi(const SweepArgs& a, int l) {
+  return a.dev_trig ? a.dev_trig[l] : a.g2pi[l];
+}
+__device__ __forceinline__ double arg_cosb(const SweepArgs& a, int l) {
+  return a.dev_trig ? a.dev_trig[a.np + l] : a.cosb[l];
+}
+__device__ __forceinline__ double arg_sinb(const SweepArgs& a, int l) {
+  return a.dev_trig ? a.dev_trig[2 * a.np + l] : a.sinb[l];
+}
+
 __device__ __forceinline__ double cost_f(const void* Cs, bool f64, uint32_t i) {
   return f64 ? ((const double*)Cs)[phys_cost(i, true)] : (double)((const int*)Cs)[phys_cost(i, false)];
 }
@@ -260,7 +272,7 @@ struct Sweeper {
     if (k >= 0 && k < a.span) {
       e = layer == ts_layer ? Ts[k] : __ldg((const V*)a.phase_table + (long long)layer * a.span + k);
     } else {
-      const double th = a.g2pi[layer] * cost_f(Cs, f64, i);  // turns
+      const double th = arg_g2pi(a, layer) * cost_f(Cs, f64, i);  // turns
       if constexpr (FX) {
         e = turn_phase(frac_turns(th), (const longlong2*)a.turn_table);
       } else {
@@ -281,8 +293,8 @@ struct Sweeper {
   // phase factor of cost c computed directly (out of line: only costs outside the table and
   // float costs take it)
   __device__ __forceinline__ V phase_direct(int layer, double c) const {
-    if constexpr (FX) return phase_fx_direct(a.g2pi[layer] * c, (const longlong2*)a.turn_table);
-    else return phase_f32_direct(a.g2pi[layer] * c);
+    if constexpr (FX) return phase_fx_direct(arg_g2pi(a, layer) * c, (const longlong2*)a.turn_table);
+    else return phase_f32_direct(arg_g2pi(a, layer) * c);
   }
   // psi (or lambda) *= exp(-i s gamma_l C): table lookups first, the rest out of line
   template <bool INV>
@@ -379,7 +391,7 @@ struct Sweeper {
   }
 
   __device__ __forceinline__ void mix_f32(int layer, bool inverse, bool on_psi, bool on_lam, int xacc) {
-    const double cbd = a.cosb[layer], sbd = inverse ? -a.sinb[layer] : a.sinb[layer];
+    const double cbd = arg_cosb(a, layer), sbd = inverse ? -arg_sinb(a, layer) : arg_sinb(a, layer);
     const bool tanf = fabs(cbd) >= fabs(sbd);
     const float tu = tanf ? (float)(sbd / cbd) : (float)(cbd / sbd);
     const float m = tanf ? (float)cbd : (float)sbd;
@@ -804,7 +816,7 @@ struct Lean : Sweeper<CF, FX, TWO> {
   // RX on the group from layout 0 to layout L (BACK = false) or from L to 0 (BACK = true)
   template <int L, bool BACK>
   __device__ __forceinline__ void f32_mixer(int layer, bool inverse, bool lam, int xacc) {
-    const double cbd = this->a.cosb[layer], sbd = inverse ? -this->a.sinb[layer] : this->a.sinb[layer];
+    const double cbd = arg_cosb(this->a, layer), sbd = inverse ? -arg_sinb(this->a, layer) : arg_sinb(this->a, layer);
     const bool tanf = fabs(cbd) >= fabs(sbd);
     const float tu = tanf ? (float)(sbd / cbd) : (float)(cbd / sbd);
     const float m = tanf ? (float)cbd : (float)sbd;
@@ -1123,7 +1135,7 @@ __global__ void tables_kernel(const __grid_constant__ TableArgs ta) {
     if (i < nphase) {
       const int l = (int)(i / ta.span);
       const int64_t c = ta.cmin + (i - (int64_t)l * ta.span);
-      const double th = ta.gamma[l] * (double)c;
+      const double th = (ta.dev_angles ? ta.dev_angles[l] : ta.gamma[l]) * (double)c;
       double sn, cs;
       sincos(th, &sn, &cs);
       if (ta.fx) ((longlong2*)ta.phase)[i] = make_longlong2(q62(cs), q62(-sn));
@@ -1131,7 +1143,7 @@ __global__ void tables_kernel(const __grid_constant__ TableArgs ta) {
     } else if (i < nphase + nd) {
       const int64_t j = i - nphase;
       const int l = (int)(j / 196), t = (int)((j / 14) % 14), k = (int)(j % 14);
-      const double th = ta.beta[l] * (double)(t - 2 * k);
+      const double th = (ta.dev_angles ? ta.dev_angles[ta.p + l] : ta.beta[l]) * (double)(t - 2 * k);
       double sn, cs;
       sincos(th, &sn, &cs);
       ((longlong2*)ta.dtab)[j] = (k <= t) ? make_longlong2(q62(cs), q62(-sn)) : make_longlong2(0, 0);
@@ -1145,6 +1157,48 @@ __global__ void tables_kernel(const __grid_constant__ TableArgs ta) {
       ((longlong2*)ta.turn)[j] = make_longlong2(q62(cs), q62(sn));
     }
   }
+}
+
+// [g2pi p | cos(beta) p | sin(beta) p] from device angles [gamma p | beta p]
+__global__ void angle_prep_kernel(const double* __restrict__ ang, int p, double* __restrict__ trig) {
+  const int l = threadIdx.x;
+  if (l < p) {
+    trig[l] = ang[l] / (2.0 * 3.141592653589793238);
+    double sn, cs;
+    sincos(ang[p + l], &sn, &cs);
+    trig[p + l] = cs;
+    trig[2 * p + l] = sn;
+  }
+}
+
+// One Adam ascent step on the angles from the gradient output g = [E, norm, dE/dgamma,
+// dE/dbeta]; state = [m (2p) | v (2p)]; *step counts completed steps.  The record of this
+// step (the 2p + 2 gradient outputs followed by the 2p angles it was evaluated at) goes to
+// history[step * (4p + 2)] when history is non-null.
+__global__ void adam_kernel(double* __restrict__ ang, const double* __restrict__ g, double* __restrict__ state,
+                            long long* __restrict__ step, int p, double lr, double b1, double b2, double eps,
+                            double* __restrict__ history, long long max_steps) {
+  const int i = threadIdx.x;
+  const long long t = *step;  // completed steps before this one
+  const int np2 = 2 * p;
+  if (history != nullptr && t < max_steps) {
+    double* h = history + t * (2 * np2 + 2);
+    for (int k = i; k < np2 + 2; k += blockDim.x) h[k] = g[k];
+    for (int k = i; k < np2; k += blockDim.x) h[np2 + 2 + k] = ang[k];
+  }
+  __syncthreads();
+  const double c1 = 1.0 - pow(b1, (double)(t + 1)), c2 = 1.0 - pow(b2, (double)(t + 1));
+  for (int k = i; k < np2; k += blockDim.x) {
+    const double gk = g[2 + k];  // ascent on <C>
+    double m = state[k], v = state[np2 + k];
+    m = b1 * m + (1.0 - b1) * gk;
+    v = b2 * v + (1.0 - b2) * gk * gk;
+    state[k] = m;
+    state[np2 + k] = v;
+    ang[k] += lr * (m / c1) / (sqrt(v / c2) + eps);
+  }
+  __syncthreads();
+  if (i == 0) *step = t + 1;
 }
 
 // max |C(z)| over the cost vector -> lam_shift = smallest k with 2^k >= max|C| (device scalar)
@@ -1388,6 +1442,21 @@ cudaError_t launch_cost_bound(const void* C, int f64, int n, unsigned long long*
   if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
   cost_bound_kernel<<<(int)blocks, 256, 0, s>>>(C, f64, count, out);
   note_launch(3, s, false, (double)(1ull << n) * (f64 ? 8.0 : 4.0));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_angle_prep(const double* ang, int p, double* trig, cudaStream_t s) {
+  note_launch(3, s, true);
+  angle_prep_kernel<<<1, 64, 0, s>>>(ang, p, trig);
+  note_launch(3, s, false);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(double* ang, const double* g, double* state, long long* step, int p, double lr, double b1,
+                        double b2, double eps, double* history, long long max_steps, cudaStream_t s) {
+  note_launch(3, s, true);
+  adam_kernel<<<1, 128, 0, s>>>(ang, g, state, step, p, lr, b1, b2, eps, history, max_steps);
+  note_launch(3, s, false);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,139 @@
+"""Adjoint gradients with device-resident angles, the autograd wrapper, finite-difference
+checks at the adjoint-gradient workload sizes, and the on-device Adam loop.
+
+Tolerances:
+* gradient_dev vs gradient (host angles): 1e-12 max(1, sum|w|) (cos/sin of the angles
+  are taken on the device instead of the host, 1 ulp apart);
+* vs the oracle: 1e-10 max(1, sum|w|) as for every complex128 gradient;
+* central differences with h = 1e-6: truncation h^2/6 |E'''| plus rounding 2 eps_E / h,
+  below 1e-6 max(1, sum|w|) for these instances;
+* Adam: the oracle-driven CPU Adam and the device loop agree to 1e-9 on the angles.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import qaoa
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2407_13012_gb300 as q  # noqa: E402
+
+
+def instance(n, seed, prob=0.2, weights="u01"):
+    e, w, integer = synth.graph("gnp", n, seed, weights=weights, prob=prob)
+    return q.Graph(n, e, w, integer), e, w, integer
+
+
+def scale_of(w):
+    return max(1.0, float(np.sum(np.abs(w))))
+
+
+@pytest.mark.parametrize("n,p,dtype", [(9, 3, "c128"), (14, 4, "c128"), (14, 4, "c64")])
+def test_gradient_dev_matches_host_angles_and_oracle(n, p, dtype):
+    g, e, w, integer = instance(n, n, prob=0.5)
+    cv = q.cost_vector(g, "f64")
+    gam, bet = synth.angles(p, 3)
+    psi, lam = q.new_state(n, dtype), q.new_state(n, dtype)
+    host = q.gradient(psi, lam, cv, gam, bet).cpu().numpy()
+    ang = torch.tensor(np.concatenate([gam, bet]), device="cuda")
+    dev = q.gradient_dev(psi, lam, cv, ang).cpu().numpy()
+    s = scale_of(w)
+    tol = 1e-12 * s if dtype == "c128" else 1e-5 * s
+    assert np.max(np.abs(host - dev)) <= tol
+    C = qaoa.cut_values(n, e, w, integer=False)
+    E, dg, db, _ = qaoa.adjoint_gradient(n, C, gam, bet)
+    ref = np.concatenate([[E], dg, db])
+    got = np.concatenate([dev[:1], dev[2:]])
+    assert np.max(np.abs(got - ref)) <= (1e-10 * s if dtype == "c128" else 1e-4 * s)
+
+
+def test_autograd_function():
+    n, p = 12, 3
+    g, e, w, integer = instance(n, 4, prob=0.4)
+    cv = q.cost_vector(g, "f64")
+    gam, bet = synth.angles(p, 9)
+    f = q.QAOAExpectation(cv)
+    ang = torch.tensor(np.concatenate([gam, bet]), device="cuda", requires_grad=True)
+    E = f(ang)
+    (3.0 * E).backward()
+    C = qaoa.cut_values(n, e, w, integer=False)
+    E0, dg, db, _ = qaoa.adjoint_gradient(n, C, gam, bet)
+    s = scale_of(w)
+    assert abs(E.item() - E0) <= 1e-10 * s
+    assert np.max(np.abs(ang.grad.cpu().numpy() - 3.0 * np.concatenate([dg, db]))) <= 3e-10 * s
+
+
+@pytest.mark.parametrize("n", [24, 30])
+def test_adjoint_vs_central_differences_p10(n):
+    """G(n, 0.2), U(0,1) weights, p = 10, complex128: the 20-angle gradient against central
+    differences of <C> (h = 1e-6), both on the device."""
+    p, h = 10, 1e-6
+    g, e, w, integer = instance(n, 1, prob=0.2)
+    cv = q.cost_vector(g, "f64")
+    gam, bet = synth.angles(p, 2)
+    psi, lam = q.new_state(n, "c128"), q.new_state(n, "c128")
+    out = q.gradient(psi, lam, cv, gam, bet).cpu().numpy()
+
+    def E(gg, bb):
+        return q.apply_layers(psi, cv, gg, bb, expect=True)[0].item()
+
+    fd = np.zeros(2 * p)
+    for l in range(p):
+        d = np.zeros(p)
+        d[l] = h
+        fd[l] = (E(gam + d, bet) - E(gam - d, bet)) / (2 * h)
+        fd[p + l] = (E(gam, bet + d) - E(gam, bet - d)) / (2 * h)
+    assert np.max(np.abs(out[2:] - fd)) <= 1e-6 * scale_of(w)
+    del psi, lam, cv
+    torch.cuda.empty_cache()
+
+
+def adam_reference(n, C, ang0, steps, lr, b1, b2, eps):
+    """Adam ascent driven by the oracle's adjoint gradient (test reference)."""
+    p = len(ang0) // 2
+    ang = np.array(ang0, dtype=np.float64)
+    m, v = np.zeros(2 * p), np.zeros(2 * p)
+    rows = []
+    for t in range(1, steps + 1):
+        E, dg, db, _ = qaoa.adjoint_gradient(n, C, ang[:p], ang[p:])
+        gr = np.concatenate([dg, db])
+        rows.append(np.concatenate([[E], gr, ang]))
+        m = b1 * m + (1 - b1) * gr
+        v = b2 * v + (1 - b2) * gr * gr
+        ang = ang + lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
+    return ang, np.array(rows)
+
+
+def test_adam_loop_matches_oracle_driven_adam():
+    n, p, steps = 8, 2, 25
+    g, e, w, integer = instance(n, 6, prob=0.5)
+    cv = q.cost_vector(g, "f64")
+    C = qaoa.cut_values(n, e, w, integer=False)
+    gam, bet = synth.angles(p, 5)
+    ang0 = np.concatenate([gam, bet])
+    ang = torch.tensor(ang0, device="cuda")
+    hist = q.optimize_adam(cv, ang, steps, lr=0.05).cpu().numpy()
+    ref_ang, ref_rows = adam_reference(n, C, ang0, steps, 0.05, 0.9, 0.999, 1e-8)
+    s = scale_of(w)
+    assert np.max(np.abs(hist[:, 0] - ref_rows[:, 0])) <= 1e-9 * s
+    assert np.max(np.abs(hist[:, 2:2 + 2 * p] - ref_rows[:, 1:1 + 2 * p])) <= 1e-9 * s
+    assert np.max(np.abs(hist[:, 2 + 2 * p:] - ref_rows[:, 1 + 2 * p:])) <= 1e-9
+    assert np.max(np.abs(ang.cpu().numpy() - ref_ang)) <= 1e-9
+
+
+def test_adam_200_steps_improves_cut_n20():
+    """A 200-step loop on the device raises <C> and never leaves the device inside the loop."""
+    n, p = 20, 4
+    g, e, w, integer = instance(n, 8, prob=0.2)
+    cv = q.cost_vector(g, "f64")
+    gam, bet = synth.angles(p, 1)
+    ang = torch.tensor(np.concatenate(q.linear_ramp(p)), device="cuda") * 0.5
+    launches0 = q.launch_count()
+    hist = q.optimize_adam(cv, ang, 200, lr=0.02).cpu().numpy()
+    assert hist.shape == (200, 4 * p + 2)
+    assert hist[-1, 0] > hist[0, 0]
+    assert abs(hist[-1, 1] - 1.0) < 1e-10
+    # first step launched directly, the other 199 replay one captured graph
+    assert q.launch_count() - launches0 < 200
