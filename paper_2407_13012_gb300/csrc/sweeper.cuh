@@ -1,0 +1,782 @@
+// Tile machinery shared by the layer sweeps and the batched kernel: tile layouts, the
+// per-tile state (Sweeper) with its phase, mixer, lambda and reduction operations.
+//
+// A sweep streams every tile of the state once.  A tile holds the 2^t combinations of
+// one group of qubits (local bits [c, c + t)) together with the 2^c lowest index bits
+// (local bits [0, c), kept for coalesced access); the other index bits are fixed per
+// tile.  Each thread holds R = 2^RB amplitudes of the tile in registers.  In "layout" k
+// the register index is the local bit range [lo(k), lo(k) + RB) and the thread index
+// is the rest, so butterflies on the qubits of that range run in registers; moving
+// to the next layout is one swizzled shared-memory exchange.  A sweep runs a short
+// program of operations on each tile (phase, mixer, lambda init, reductions) and
+// writes the tile back.  The grid is persistent over tiles and every reduction has a
+// fixed order, so results are deterministic for a given device.
+//
+// Arithmetic.
+//  * complex64: float32 throughout; the mixer applies RX(2 beta) = cos(b) I - i sin(b) X
+//    as one butterfly per qubit.
+//  * complex128: the state lives in int64 fixed point with scale 2^S inside a call
+//    (GB300 retires ~1.75 float64 FMA per SM clock, 1/73 of its float32 rate, so
+//    float64 butterflies would cost ~20x the sweep's memory time).  The mixer on a
+//    group of t qubits uses RX(2b)^{(x)t} = H^{(x)t} D H^{(x)t} = 2^-t W D W, where W is
+//    the unnormalised Walsh-Hadamard transform on the group (exact integer add/sub
+//    butterflies) and D = diag(exp(-i b (t - 2 popcount(g)))) is one complex multiply
+//    per amplitude, rounded once.  Phase factors are Q62 fixed point.  Reductions
+//    accumulate exact int128 products per thread and per tile and are converted to
+//    float64 once per tile.
+#pragma once
+
+#include "internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "fixedpoint.cuh"
+
+namespace qaoa {
+namespace {
+
+
+// ------------------------------------------------------------------ tile layouts
+
+template <int B_, int RB_, int SW_, int SWW_, int MINB_>
+struct Cfg {
+  static constexpr int MINB = MINB_;        // blocks per SM the register budget is sized for
+  static constexpr int B = B_;              // tile bits
+  static constexpr int RB = RB_;            // register bits per layout
+  static constexpr int R = 1 << RB_;        // amplitudes per thread (per buffer)
+  static constexpr int NT = 1 << (B_ - RB_);  // threads per block
+  static constexpr int NR = (B_ + RB_ - 1) / RB_;  // layouts (rounds)
+  __host__ __device__ static constexpr int lo(int k) {
+    const int v = B - RB * (k + 1);
+    return v < 0 ? 0 : v;
+  }
+  // first local bit of round k that no earlier round covers: round k processes
+  // [lo(k), newhi(k)) where newhi(0) = B and newhi(k) = lo(k - 1)
+  __host__ __device__ static constexpr int newhi(int k) { return k == 0 ? B : lo(k - 1); }
+  __host__ __device__ static constexpr uint32_t idx(int k, uint32_t tid, int r) {
+    const int l = lo(k);
+    return (tid & ((1u << l) - 1)) | ((uint32_t)r << l) | ((tid >> l) << (l + RB));
+  }
+  // shared-memory slot of local index i: XOR-fold higher bits into the bank bits
+  __host__ __device__ static constexpr uint32_t phys(uint32_t i) { return i ^ ((i >> SW_) & ((1u << SWW_) - 1)); }
+};
+
+// complex64 single buffer: 8192-amplitude tiles, 32 per thread, 256 threads
+using CfgF1 = Cfg<13, 5, 5, 4, 2>;
+// complex64 two buffers (gradient): 4096-amplitude tiles, 16 per thread per buffer
+using CfgF2 = Cfg<12, 4, 4, 4, 2>;
+// complex64 two buffers (gradient) with 8192-amplitude tiles: 32 amplitudes per thread per
+// buffer, one block per SM; at n = 32 this keeps >= 3 carried low bits (64-byte rows)
+using CfgF3 = Cfg<13, 5, 5, 4, 1>;
+// complex128 fixed point single buffer: 4096-amplitude tiles, 16 per thread
+using CfgX1 = Cfg<12, 4, 4, 3, 2>;
+// complex128 fixed point two buffers: 4096-amplitude tiles, 8 per thread per buffer, 512 threads
+using CfgX2 = Cfg<12, 3, 3, 3, 1>;
+
+// cost-tile slot of local index i; the XOR leaves the bits inside a 16-byte chunk alone so
+// the tile can be fetched with 16-byte asynchronous copies
+__device__ __forceinline__ uint32_t phys_cost(uint32_t i, bool f64) {
+  return f64 ? (i ^ ((i >> 3) & 14)) : (i ^ ((i >> 3) & 28));
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ uint64_t tile_base(const SweepGeom& g, int64_t tile) {
+  const int lowrest_bits = g.j0 - g.c;
+  const uint64_t lowrest = (uint64_t)tile & ((1ull << lowrest_bits) - 1);
+  const uint64_t highrest = (uint64_t)tile >> lowrest_bits;
+  return (lowrest << g.c) | (highrest << (g.j0 + g.t));
+}
+
+__device__ __forceinline__ uint64_t local_to_z(const SweepGeom& g, uint64_t base, uint32_t i) {
+  const uint32_t l = i & ((1u << g.c) - 1);
+  const uint64_t q = i >> g.c;
+  return base | l | (q << g.j0);
+}
+
+// ------------------------------------------------------------------ fixed point helpers
+
+using i128 = __int128;
+using fx::round_shift;
+
+// (x * e) / 2^(62 + extra) for a state value x (|re|, |im| < 2^61) and a Q62 unit complex e
+__device__ __forceinline__ longlong2 cmul_fx(longlong2 x, longlong2 e, int extra) {
+  const fx::C64 o = fx::cmul_q62(x.x, x.y, e.x, e.y, extra);
+  return make_longlong2(o.x, o.y);
+}
+// the same with 128-bit products, for operands up to 2^63 (products of two Q62 factors)
+__device__ __forceinline__ longlong2 cmul_fx_wide(longlong2 x, longlong2 e, int extra) {
+  const fx::C64 o = fx::cmul_q62_exact(x.x, x.y, e.x, e.y, extra);
+  return make_longlong2(o.x, o.y);
+}
+__device__ __forceinline__ double fx_to_double(long long x, int s) { return fx::to_double(x, s); }
+__device__ __forceinline__ double i128_to_double(i128 v, int s) { return fx::i128_to_double(v, s); }
+__device__ __forceinline__ long long double_to_fx(double d, int s) { return fx::from_double(d, s); }
+__device__ __forceinline__ unsigned long long frac_turns(double d) { return fx::frac_turns(d); }
+
+// exp(-2 pi i th) in float32 for a turn count th (the rare path of float costs or costs
+// outside the table); kept out of line so it does not raise the register budget of the
+// common path
+__device__ __noinline__ float2 phase_f32_direct(double th) {
+  const float f = (float)(th - rint(th));
+  float s, c;
+  sincospif(2.0f * f, &s, &c);
+  return make_float2(c, -s);
+}
+
+__device__ __forceinline__ longlong2 turn_phase(unsigned long long t, const longlong2* __restrict__ tt);
+
+// exp(-2 pi i th) in Q62 for a turn count th (out of line, like phase_f32_direct)
+__device__ __noinline__ longlong2 phase_fx_direct(double th, const longlong2* __restrict__ tt) {
+  return turn_phase(frac_turns(th), tt);
+}
+
+// exp(-2 pi i t / 2^64) in Q62 from three 1024-entry tables and a first-order residual
+__device__ __forceinline__ longlong2 turn_phase(unsigned long long t, const longlong2* __restrict__ tt) {
+  const longlong2 e1 = tt[t >> 54];
+  const longlong2 e2 = tt[1024 + ((t >> 44) & 1023)];
+  const longlong2 e3 = tt[2048 + ((t >> 34) & 1023)];
+  longlong2 e = cmul_fx_wide(e1, e2, 0);
+  e = cmul_fx_wide(e, e3, 0);
+  // residual angle rho = 2 pi r 2^-64 < 2 pi 2^-30; exp(-i rho) = 1 - i rho to 2e-17
+  const unsigned long long r = t & ((1ull << 34) - 1);
+  const long long rho = (long long)(((r >> 2) * 3373259426ull) >> 29);  // rho * 2^62, 3373259426 = round(pi/2 2^31)
+  const long long dre = round_shift((i128)rho * e.y, 62);
+  const long long dim = round_shift((i128)rho * e.x, 62);
+  return make_longlong2(e.x + dre, e.y - dim);
+}
+
+// ------------------------------------------------------------------ kernel
+
+// per-layer angle terms: kernel parameters, or device memory ([g2pi p | cos p | sin p],
+// written by angle_prep_kernel) when the angles live on the device
+__device__ __forceinline__ double arg_g2pi(const SweepArgs& a, int l) {
+  return a.dev_trig ? a.dev_trig[l] : a.g2pi[l];
+}
+__device__ __forceinline__ double arg_cosb(const SweepArgs& a, int l) {
+  return a.dev_trig ? a.dev_trig[a.np + l] : a.cosb[l];
+}
+__device__ __forceinline__ double arg_sinb(const SweepArgs& a, int l) {
+  return a.dev_trig ? a.dev_trig[2 * a.np + l] : a.sinb[l];
+}
+
+__device__ __forceinline__ double cost_f(const void* Cs, bool f64, uint32_t i) {
+  return f64 ? ((const double*)Cs)[phys_cost(i, true)] : (double)((const int*)Cs)[phys_cost(i, false)];
+}
+__device__ __forceinline__ int cost_i(const void* Cs, uint32_t i) { return ((const int*)Cs)[phys_cost(i, false)]; }
+
+template <class CF, bool FX, bool TWO>
+struct Sweeper {
+  using V = typename std::conditional<FX, longlong2, float2>::type;
+  static constexpr int R = CF::R;
+
+  const SweepArgs& a;
+  V v[R];        // register tile of psi (layout cur)
+  V w[R];        // register tile of lambda (two-buffer sweeps)
+  V* X;          // exchange buffer, 2^B slots
+  void* Cs;      // cost tile, 2^B slots
+  const V* Ts;   // shared-memory copy of one layer's phase table (or nullptr)
+  longlong2* Ds; // shared-memory mixer diagonal of the current fixed-point mixer (14 entries)
+  int ts_layer;  // layer whose table Ts holds (-1: none)
+  double* blk;   // block accumulators
+  double* red;   // reduction scratch [2][NT/32]
+  int cur;       // current layout
+  int lam_shift;  // lambda scale exponent (fixed point)
+  int in_shift;   // extra input scale exponent of a user state (fixed point)
+  uint32_t evalid;
+  uint64_t base;
+  const uint32_t tid;
+
+  __device__ Sweeper(const SweepArgs& a_, V* X_, void* Cs_, double* blk_, double* red_)
+      : a(a_), X(X_), Cs(Cs_), Ts(nullptr), Ds(nullptr), ts_layer(-1), blk(blk_), red(red_), cur(0), lam_shift(0),
+        in_shift(0), evalid(0), base(0), tid(threadIdx.x) {}
+
+  __device__ __forceinline__ uint32_t idx(int r) const { return CF::idx(cur, tid, r); }
+
+  // move u from layout F to layout T through the shared exchange buffer; layouts known at
+  // compile time so each slot address is one base plus an immediate
+  // The swizzle is linear over GF(2) and idx(k, tid, r) = idx(k, tid, 0) | (r << lo(k)) with
+  // disjoint bits, so a slot is the thread's base slot XOR a compile-time constant.
+  template <int F, int T>
+  __device__ __forceinline__ void ex(V (&u)[R]) {
+    const uint32_t pf = CF::phys(CF::idx(F, tid, 0)), pt = CF::phys(CF::idx(T, tid, 0));
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) X[pf ^ CF::phys((uint32_t)r << CF::lo(F))] = u[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) u[r] = X[pt ^ CF::phys((uint32_t)r << CF::lo(T))];
+  }
+  template <int F>
+  __device__ __forceinline__ void ex_from(V (&u)[R], int to) {
+    switch (to) {
+      case 0: ex<F, 0>(u); break;
+      case 1: if constexpr (CF::NR > 1) ex<F, (CF::NR > 1 ? 1 : 0)>(u); break;
+      case 2: if constexpr (CF::NR > 2) ex<F, (CF::NR > 2 ? 2 : 0)>(u); break;
+      default: if constexpr (CF::NR > 3) ex<F, (CF::NR > 3 ? 3 : 0)>(u); break;
+    }
+  }
+  __device__ __forceinline__ void exchange_one(V (&u)[R], int to) {
+    switch (cur) {
+      case 0: ex_from<0>(u, to); break;
+      case 1: if constexpr (CF::NR > 1) ex_from<(CF::NR > 1 ? 1 : 0)>(u, to); break;
+      case 2: if constexpr (CF::NR > 2) ex_from<(CF::NR > 2 ? 2 : 0)>(u, to); break;
+      default: if constexpr (CF::NR > 3) ex_from<(CF::NR > 3 ? 3 : 0)>(u, to); break;
+    }
+  }
+  // both buffers always share one layout
+  __device__ __forceinline__ void go(int to) {
+    if (to == cur) return;
+    exchange_one(v, to);
+    if (TWO) exchange_one(w, to);
+    cur = to;
+  }
+
+  // block-reduce and add to blk[r] (and blk[r + 1])
+  __device__ __forceinline__ void block_add(int r, double v0, double v1, bool pair) {
+    const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v0 += __shfl_down_sync(0xffffffffu, v0, o);
+      v1 += __shfl_down_sync(0xffffffffu, v1, o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+      red[warp] = v0;
+      red[CF::NT / 32 + warp] = v1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int k = 0; k < CF::NT / 32; ++k) {
+        s0 += red[k];
+        s1 += red[CF::NT / 32 + k];
+      }
+      blk[r] += s0;
+      if (pair) blk[r + 1] += s1;
+    }
+  }
+
+  // ---------------------------------------------------------------- phase
+  __device__ __forceinline__ V phase_factor(int layer, bool inverse, uint32_t i) const {
+    const bool f64 = a.cost_dtype == QAOA_COST_F64;
+    long long k = -1;
+    if (!f64 && a.phase_table != nullptr) k = (long long)cost_i(Cs, i) - a.cmin;
+    V e;
+    if (k >= 0 && k < a.span) {
+      e = layer == ts_layer ? Ts[k] : __ldg((const V*)a.phase_table + (long long)layer * a.span + k);
+    } else {
+      const double th = arg_g2pi(a, layer) * cost_f(Cs, f64, i);  // turns
+      if constexpr (FX) {
+        e = turn_phase(frac_turns(th), (const longlong2*)a.turn_table);
+      } else {
+        e = phase_f32_direct(th);
+      }
+    }
+    if (inverse) e.y = -e.y;
+    return e;
+  }
+
+  __device__ __forceinline__ static V vmul(V x, V e) {
+    if constexpr (FX) {
+      return cmul_fx(x, e, 0);
+    } else {
+      return make_float2(x.x * e.x - x.y * e.y, x.x * e.y + x.y * e.x);
+    }
+  }
+  // phase factor of cost c computed directly (out of line: only costs outside the table and
+  // float costs take it)
+  __device__ __forceinline__ V phase_direct(int layer, double c) const {
+    if constexpr (FX) return phase_fx_direct(arg_g2pi(a, layer) * c, (const longlong2*)a.turn_table);
+    else return phase_f32_direct(arg_g2pi(a, layer) * c);
+  }
+  // psi (or lambda) *= exp(-i s gamma_l C): table lookups first, the rest out of line
+  template <bool INV>
+  __device__ __forceinline__ void phase_apply(V (&u)[R], int layer) {
+    const bool f64 = a.cost_dtype == QAOA_COST_F64;
+    unsigned miss = 0;
+    if (!f64 && a.phase_table != nullptr) {
+      const V* tab = layer == ts_layer ? Ts : (const V*)a.phase_table + (long long)layer * a.span;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const long long k = (long long)cost_i(Cs, idx(r)) - a.cmin;
+        if (k >= 0 && k < a.span) {
+          V e = tab[k];
+          if constexpr (INV) e.y = -e.y;
+          u[r] = vmul(u[r], e);
+        } else {
+          miss |= 1u << r;
+        }
+      }
+    } else {
+      miss = R == 32 ? 0xffffffffu : ((1u << R) - 1);
+    }
+    if (miss) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (!((miss >> r) & 1u)) continue;
+        V e = phase_direct(layer, cost_f(Cs, f64, idx(r)));
+        if constexpr (INV) e.y = -e.y;
+        u[r] = vmul(u[r], e);
+      }
+    }
+  }
+
+  __device__ __forceinline__ void op_phase(int layer, bool inverse, bool on_psi, bool on_lam) {
+    if (inverse) {
+      if (on_psi) phase_apply<true>(v, layer);
+      if (TWO && on_lam) phase_apply<true>(w, layer);
+    } else {
+      if (on_psi) phase_apply<false>(v, layer);
+      if (TWO && on_lam) phase_apply<false>(w, layer);
+    }
+  }
+
+  // ---------------------------------------------------------------- mixer, float32: RX butterflies
+  // RX(2b) = cos(b) (I - i tan(b) X) = -i sin(b) (X + i cot(b) I).  For |tan b| <= 1 a pair
+  // (x, y) goes to (x - i t y, y - i t x) with t = tan b and the factor cos b; otherwise to
+  // (y + i u x, x + i u y) with u = cot b and the factor -i sin b.  Either way a butterfly
+  // is 4 FMAs with |t|, |u| <= 1; the per-qubit factors of a round are applied once at its end.
+  __device__ __forceinline__ void bf_tan(float2& x, float2& y, float t) {
+    const float2 p = x, q = y;
+    x = make_float2(fmaf(t, q.y, p.x), fmaf(-t, q.x, p.y));
+    y = make_float2(fmaf(t, p.y, q.x), fmaf(-t, p.x, q.y));
+  }
+  __device__ __forceinline__ void bf_cot(float2& x, float2& y, float u) {
+    const float2 p = x, q = y;
+    x = make_float2(fmaf(-u, p.y, q.x), fmaf(u, p.x, q.y));
+    y = make_float2(fmaf(-u, q.y, p.x), fmaf(u, q.x, p.y));
+  }
+  // butterflies on the register bits set in todo, branch-free inside the pair loops
+  template <bool TAN>
+  __device__ __forceinline__ void bf_round(V (&u)[R], unsigned todo, float tu) {
+#pragma unroll
+    for (int rb = 0; rb < CF::RB; ++rb) {
+      if (!((todo >> rb) & 1u)) continue;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (r & (1 << rb)) continue;
+        const int q = r | (1 << rb);
+        if constexpr (TAN) bf_tan(u[r], u[q], tu);
+        else bf_cot(u[r], u[q], tu);
+      }
+    }
+  }
+
+  // multiply every amplitude of u by the complex factor f
+  __device__ __forceinline__ void scale_f32(V (&u)[R], float2 f) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float2 z = u[r];
+      u[r] = make_float2(z.x * f.x - z.y * f.y, z.x * f.y + z.y * f.x);
+    }
+  }
+  // (m)^nb (tangent form) or (-i m)^nb (cotangent form)
+  __device__ __forceinline__ static float2 round_factor(bool tanf, float m, int nb) {
+    float f = 1.f;
+    for (int j = 0; j < nb; ++j) f *= m;
+    if (tanf) return make_float2(f, 0.f);
+    switch (nb & 3) {
+      case 0: return make_float2(f, 0.f);
+      case 1: return make_float2(0.f, -f);
+      case 2: return make_float2(-f, 0.f);
+      default: return make_float2(0.f, f);
+    }
+  }
+
+  __device__ __forceinline__ void mix_f32(int layer, bool inverse, bool on_psi, bool on_lam, int xacc) {
+    const double cbd = arg_cosb(a, layer), sbd = inverse ? -arg_sinb(a, layer) : arg_sinb(a, layer);
+    const bool tanf = fabs(cbd) >= fabs(sbd);
+    const float tu = tanf ? (float)(sbd / cbd) : (float)(cbd / sbd);
+    const float m = tanf ? (float)cbd : (float)sbd;
+    const int gl = a.g.c, gh = a.g.c + a.g.t;
+    const bool rev = (cur == CF::NR - 1) && CF::NR > 1;
+    const bool xt = TWO && xacc >= 0;
+    float xs = 0.f;
+    int pending = 0;  // qubits whose factor is not applied yet
+    for (int s = 0; s < CF::NR; ++s) {
+      const int k = rev ? CF::NR - 1 - s : s;
+      const int l0 = CF::lo(k), l1 = CF::newhi(k);
+      if (l1 <= gl || l0 >= gh) continue;  // no group qubit in this round
+      go(k);
+      if (xt) {  // sum over this round's qubits of Im(conj(la) pb + conj(lb) pa); state exact here
+#pragma unroll
+        for (int rb = 0; rb < CF::RB; ++rb) {
+          const int b = l0 + rb;
+          if (!(b < l1 && b >= gl && b < gh)) continue;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            if (r & (1 << rb)) continue;
+            const int q = r | (1 << rb);
+            xs += w[r].x * v[q].y - w[r].y * v[q].x + w[q].x * v[r].y - w[q].y * v[r].x;
+          }
+        }
+      }
+      // which of this round's register bits are group qubits (uniform)
+      unsigned todo = 0;
+#pragma unroll
+      for (int rb = 0; rb < CF::RB; ++rb) {
+        const int b = l0 + rb;
+        if (b < l1 && b >= gl && b < gh) todo |= 1u << rb;
+      }
+      pending += __popc(todo);
+      if (tanf) {
+        if (on_psi) bf_round<true>(v, todo, tu);
+        if (TWO && on_lam) bf_round<true>(w, todo, tu);
+      } else {
+        if (on_psi) bf_round<false>(v, todo, tu);
+        if (TWO && on_lam) bf_round<false>(w, todo, tu);
+      }
+      if (xt && pending) {  // the X-terms of the next round need the exact state
+        const float2 f = round_factor(tanf, m, pending);
+        if (on_psi) scale_f32(v, f);
+        if (on_lam) scale_f32(w, f);
+        pending = 0;
+      }
+    }
+    if (pending) {
+      const float2 f = round_factor(tanf, m, pending);
+      if (on_psi) scale_f32(v, f);
+      if (TWO && on_lam) scale_f32(w, f);
+    }
+    if (xt) block_add(xacc, 2.0 * (double)xs, 0.0, false);
+  }
+
+  // ---------------------------------------------------------------- mixer, fixed point: W D W
+  template <int RBc>
+  __device__ __forceinline__ void wht_bit(V (&u)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r & (1 << RBc)) continue;
+      const int q = r | (1 << RBc);
+      const longlong2 x = u[r], y = u[q];
+      u[r] = make_longlong2(x.x + y.x, x.y + y.y);
+      u[q] = make_longlong2(x.x - y.x, x.y - y.y);
+    }
+  }
+  __device__ __forceinline__ void wht_round(int k, bool on_psi, bool on_lam) {
+    const int l0 = CF::lo(k), l1 = CF::newhi(k);
+    const int gl = a.g.c, gh = a.g.c + a.g.t;
+#pragma unroll
+    for (int rb = 0; rb < CF::RB; ++rb) {
+      const int b = l0 + rb;
+      if (b < l1 && b >= gl && b < gh) {
+        if (on_psi) {
+          if constexpr (FX) {
+            if (rb == 0) wht_bit<0>(v);
+            if (CF::RB > 1 && rb == 1) wht_bit<(CF::RB > 1 ? 1 : 0)>(v);
+            if (CF::RB > 2 && rb == 2) wht_bit<(CF::RB > 2 ? 2 : 0)>(v);
+            if (CF::RB > 3 && rb == 3) wht_bit<(CF::RB > 3 ? 3 : 0)>(v);
+            if (CF::RB > 4 && rb == 4) wht_bit<(CF::RB > 4 ? 4 : 0)>(v);
+          }
+        }
+        if (TWO && on_lam) {
+          if constexpr (FX) {
+            if (rb == 0) wht_bit<0>(w);
+            if (CF::RB > 1 && rb == 1) wht_bit<(CF::RB > 1 ? 1 : 0)>(w);
+            if (CF::RB > 2 && rb == 2) wht_bit<(CF::RB > 2 ? 2 : 0)>(w);
+            if (CF::RB > 3 && rb == 3) wht_bit<(CF::RB > 3 ? 3 : 0)>(w);
+            if (CF::RB > 4 && rb == 4) wht_bit<(CF::RB > 4 ? 4 : 0)>(w);
+          }
+        }
+      }
+    }
+  }
+
+  // D multiply on the register tile: u[r] *= Ds[popcount] / 2^t; E = t >= 3 selects the
+  // shift form of the limb multiply at compile time
+  template <bool BIG>
+  __device__ __forceinline__ void d_mul(V (&u)[R], const longlong2* Ds, int gl, int t) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int pc = __popc((idx(r) >> gl) & ((1u << t) - 1));
+      const longlong2 e = Ds[pc];
+      fx::C64 o;
+      if constexpr (BIG) {
+        const fx::Limbs xr = fx::split(u[r].x), xi = fx::split(u[r].y), nxi = fx::split(-u[r].y);
+        const fx::Limbs er = fx::split(e.x), ei = fx::split(e.y);
+        o.x = fx::dot2_q62(xr, er, nxi, ei, t);
+        o.y = fx::dot2_q62(xr, ei, xi, er, t);
+      } else {
+        o = fx::cmul_q62(u[r].x, u[r].y, e.x, e.y, t);
+      }
+      u[r] = make_longlong2(o.x, o.y);
+    }
+  }
+
+  __device__ __forceinline__ void mix_fx(int layer, bool inverse, bool on_psi, bool on_lam, int xacc) {
+    const int gl = a.g.c, gh = a.g.c + a.g.t, t = a.g.t;
+    // rounds that hold group qubits, walked from the current layout outwards
+    int ks[8], nk = 0;
+    const bool rev = (cur == CF::NR - 1) && CF::NR > 1;
+    for (int s = 0; s < CF::NR; ++s) {
+      const int k = rev ? CF::NR - 1 - s : s;
+      if (CF::newhi(k) <= gl || CF::lo(k) >= gh) continue;
+      ks[nk++] = k;
+    }
+    // this mixer's diagonal exp(-i s b (t - 2k)), k = 0..t, into shared memory (sign applied)
+    __syncthreads();
+    if (tid <= (uint32_t)t) {
+      longlong2 e = __ldg((const longlong2*)a.d_table + ((long long)layer * 14 + t) * 14 + tid);
+      if (inverse) e.y = -e.y;
+      Ds[tid] = e;
+    }
+    for (int j = 0; j < nk; ++j) {
+      go(ks[j]);
+      wht_round(ks[j], on_psi, on_lam);
+    }
+    __syncthreads();
+    if (TWO && xacc >= 0) {  // 2 Im <lam|sum_j X_j|psi> = 2 Im sum conj(lam~) (t - 2 popcount) psi~ 2^-t
+      i128 xs = 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int pc = __popc((idx(r) >> gl) & ((1u << t) - 1));
+        const i128 pr = (i128)w[r].x * v[r].y - (i128)w[r].y * v[r].x;  // Im(conj(lam~) psi~)
+        xs += (pr >> 32) * (t - 2 * pc);
+      }
+      // value = 2 * xs * 2^32 * 2^-t * 2^-2S (lambda carries the scale 2^lam_shift)
+      block_add(xacc, 2.0 * i128_to_double(xs, 2 * a.fx_shift + t - 32 - lam_shift), 0.0, false);
+    }
+    if (t >= 3) {
+      if (on_psi) d_mul<true>(v, Ds, gl, t);
+      if (TWO && on_lam) d_mul<true>(w, Ds, gl, t);
+    } else {
+      if (on_psi) d_mul<false>(v, Ds, gl, t);
+      if (TWO && on_lam) d_mul<false>(w, Ds, gl, t);
+    }
+    for (int j = nk - 1; j >= 0; --j) {
+      go(ks[j]);
+      wht_round(ks[j], on_psi, on_lam);
+    }
+  }
+
+  // ---------------------------------------------------------------- elementwise ops
+  // lambda := C psi; fixed point stores lambda / 2^lam_shift (2^lam_shift >= max |C|) so
+  // that lambda keeps the norm bound of the state
+  __device__ __forceinline__ void op_lambda() {
+    const bool f64 = a.cost_dtype == QAOA_COST_F64;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t i = idx(r);
+      if constexpr (FX) {
+        if (!f64) {
+          const long long c = cost_i(Cs, i);
+          w[r] = make_longlong2(round_shift((i128)v[r].x * c, lam_shift), round_shift((i128)v[r].y * c, lam_shift));
+        } else {
+          const long long cq = double_to_fx(cost_f(Cs, true, i), 62 - lam_shift);
+          w[r] = make_longlong2(round_shift((i128)v[r].x * cq, 62), round_shift((i128)v[r].y * cq, 62));
+        }
+      } else {
+        const float c = (float)cost_f(Cs, f64, i);
+        w[r] = make_float2(c * v[r].x, c * v[r].y);
+      }
+    }
+  }
+
+  __device__ __forceinline__ void op_expect(int acc) {
+    const bool f64 = a.cost_dtype == QAOA_COST_F64;
+    double e0 = 0.0, e1 = 0.0;
+    if constexpr (FX) {
+      i128 sc = 0, sn = 0;
+      double sf = 0.0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t i = idx(r);
+        if (i >= evalid) continue;
+        const i128 p2 = (i128)v[r].x * v[r].x + (i128)v[r].y * v[r].y;
+        sn += p2 >> 16;
+        if (!f64) sc += (p2 >> 32) * cost_i(Cs, i);
+        else sf += cost_f(Cs, true, i) * i128_to_double(p2, 2 * a.fx_shift);
+      }
+      e1 = i128_to_double(sn, 2 * (a.fx_shift - in_shift) - 16);
+      e0 = f64 ? ldexp(sf, 2 * in_shift) : i128_to_double(sc, 2 * (a.fx_shift - in_shift) - 32);
+    } else {
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t i = idx(r);
+        if (i >= evalid) continue;
+        const float p2 = v[r].x * v[r].x + v[r].y * v[r].y;
+        s0 += (float)cost_f(Cs, f64, i) * p2;
+        s1 += p2;
+      }
+      e0 = s0;
+      e1 = s1;
+    }
+    block_add(acc, e0, e1, true);
+  }
+
+  __device__ __forceinline__ void op_cterm(int acc) {
+    const bool f64 = a.cost_dtype == QAOA_COST_F64;
+    double e0 = 0.0;
+    if constexpr (FX) {
+      i128 sc = 0;
+      double sf = 0.0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t i = idx(r);
+        if (i >= evalid) continue;
+        const i128 pr = (i128)w[r].x * v[r].y - (i128)w[r].y * v[r].x;
+        if (!f64) sc += (pr >> 32) * cost_i(Cs, i);
+        else sf += cost_f(Cs, true, i) * i128_to_double(pr, 2 * a.fx_shift - lam_shift);
+      }
+      e0 = f64 ? sf : i128_to_double(sc, 2 * a.fx_shift - 32 - lam_shift);
+    } else {
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t i = idx(r);
+        if (i >= evalid) continue;
+        s += (float)cost_f(Cs, f64, i) * (w[r].x * v[r].y - w[r].y * v[r].x);
+      }
+      e0 = s;
+    }
+    block_add(acc, 2.0 * e0, 0.0, false);
+  }
+};
+
+// state loads: through the read-only path, or (COHERENT) through L2 for state that the same
+// launch wrote earlier
+template <bool COHERENT, class T>
+__device__ __forceinline__ T ld_state(const T* p) {
+  if constexpr (COHERENT) return __ldcg(p);
+  else return __ldg(p);
+}
+
+// One tile of a generic sweep: stage the cost tile, load (or create) the state in layout 0,
+// run the op program, store in layout 0.
+template <class CF, bool FX, bool TWO, bool COHERENT>
+__device__ __forceinline__ void sweep_tile(Sweeper<CF, FX, TWO>& s, const SweepArgs& a, int64_t tile, void* Cs) {
+  using V = typename Sweeper<CF, FX, TWO>::V;
+  constexpr int R = CF::R;
+  V (&v)[R] = s.v;
+  V (&w)[R] = s.w;
+  const SweepGeom& g = a.g;
+  const bool cf64 = a.cost_dtype == QAOA_COST_F64;
+  const uint32_t tid = threadIdx.x;
+  const uint64_t base = tile_base(g, tile);
+  s.base = base;
+  s.cur = 0;
+  // cost tile: 16-byte asynchronous copies when every chunk is contiguous in memory
+  // (the first group, or at least one chunk of carried low bits), element copies otherwise
+  if (a.needs_cost) {
+    __syncthreads();  // the previous tile's ops are done with Cs
+    const int per = cf64 ? 2 : 4;  // elements per 16-byte chunk
+    const bool chunky = (g.j0 == 0) || ((1 << g.c) >= per);
+    if (chunky && s.evalid >= (uint32_t)per) {
+      const uint32_t nch = s.evalid / per;
+      for (uint32_t ch = tid; ch < nch; ch += CF::NT) {
+        const uint32_t i = ch * per;
+        const uint64_t z = local_to_z(g, base, i);
+        const char* src = (const char*)a.C + z * (cf64 ? 8 : 4);
+        char* dst = (char*)Cs + (size_t)phys_cost(i, cf64) * (cf64 ? 8 : 4);
+        cp_async16(dst, src);
+      }
+    } else {
+      for (uint32_t i = tid; i < s.evalid; i += CF::NT) {
+        const uint64_t z = local_to_z(g, base, i);
+        if (cf64) ((double*)Cs)[phys_cost(i, true)] = __ldg((const double*)a.C + z);
+        else ((int*)Cs)[phys_cost(i, false)] = __ldg((const int*)a.C + z);
+      }
+    }
+    // slots past the tile's valid range hold cost 0 (phase 1) so their zero amplitudes
+    // stay zero
+    for (uint32_t i = s.evalid + tid; i < (1u << CF::B); i += CF::NT) {
+      if (cf64) ((double*)Cs)[phys_cost(i, true)] = 0.0;
+      else ((int*)Cs)[phys_cost(i, false)] = 0;
+    }
+  }
+  // state (layout 0): register r holds local index tb0 + (r << lo(0)), i.e. global index
+  // z0 + r * zs, since the register bits of layout 0 are group bits
+  // (when the carried low bits reach into the register bits, the general map is used)
+  {
+  const uint32_t tb0 = CF::idx(0, tid, 0);
+  const uint64_t z0 = local_to_z(g, base, tb0);
+  const bool affine = g.c <= CF::lo(0);
+  const uint64_t zs = affine ? (1ull << (CF::lo(0) - g.c + g.j0)) : 0ull;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t i = tb0 + ((uint32_t)r << CF::lo(0));
+    const bool ok = i < s.evalid;
+    const uint64_t z = affine ? z0 + (uint64_t)r * zs : local_to_z(g, base, i);
+    if constexpr (FX) {
+      if (!ok) v[r] = make_longlong2(0, 0);
+      else if (a.load_fmt == 2) v[r] = make_longlong2(a.init_fx, 0);
+      else if (a.load_fmt == 1) {
+        const double2 d = ld_state<COHERENT>((const double2*)a.psi + z);
+        v[r] = make_longlong2(double_to_fx(d.x, a.fx_shift - s.in_shift), double_to_fx(d.y, a.fx_shift - s.in_shift));
+      } else v[r] = ld_state<COHERENT>((const longlong2*)a.psi + z);
+      if (TWO) w[r] = (ok && a.load_lam) ? ld_state<COHERENT>((const longlong2*)a.lam + z) : make_longlong2(0, 0);
+    } else {
+      if (!ok) v[r] = make_float2(0.f, 0.f);
+      else if (a.load_fmt == 2) v[r] = make_float2(a.init_f32, 0.f);
+      else v[r] = ld_state<COHERENT>((const float2*)a.psi + z);
+      if (TWO) w[r] = (ok && a.load_lam) ? ld_state<COHERENT>((const float2*)a.lam + z) : make_float2(0.f, 0.f);
+    }
+  }
+  }
+
+  if (a.needs_cost) {
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  for (int k = 0; k < a.nops; ++k) {
+    const uint32_t op = a.ops[k];
+    const uint32_t kind = op & 0xff;
+    const int layer = (op >> 16) & 0xff;
+    const int acc = (int)((op >> 24) & 0xff);
+    const bool on_psi = op & F_PSI, on_lam = op & F_LAM, inv = op & F_SIGN;
+    const bool has_x = op & F_XTERM;
+    if (kind == OP_PHASE) {
+      s.op_phase(layer, inv, on_psi, on_lam);
+    } else if (kind == OP_MIX) {
+      if constexpr (FX) s.mix_fx(layer, inv, on_psi, on_lam, has_x ? acc : -1);
+      else s.mix_f32(layer, inv, on_psi, on_lam, has_x ? acc : -1);
+    } else if (kind == OP_LAMBDA) {
+      if constexpr (TWO) s.op_lambda();
+    } else if (kind == OP_RED_EXPECT) {
+      s.op_expect(acc);
+    } else if (kind == OP_RED_CTERM) {
+      if constexpr (TWO) s.op_cterm(acc);
+    }
+  }
+
+  // store (layout 0); addresses recomputed rather than kept live through the ops
+  s.go(0);
+  {
+  const uint32_t tb0 = CF::idx(0, tid, 0);
+  const uint64_t z0 = local_to_z(g, base, tb0);
+  const bool affine = g.c <= CF::lo(0);
+  const uint64_t zs = affine ? (1ull << (CF::lo(0) - g.c + g.j0)) : 0ull;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t i = tb0 + ((uint32_t)r << CF::lo(0));
+    if (i >= s.evalid) continue;
+    const uint64_t z = affine ? z0 + (uint64_t)r * zs : local_to_z(g, base, i);
+    if constexpr (FX) {
+      if (a.store_fmt == 1) {
+        ((double2*)a.psi)[z] = make_double2(fx_to_double(v[r].x, a.fx_shift - s.in_shift),
+                                            fx_to_double(v[r].y, a.fx_shift - s.in_shift));
+      } else if (a.store_fmt == 0) {
+        ((longlong2*)a.psi)[z] = v[r];
+      }
+      if (TWO && a.store_lam) ((longlong2*)a.lam)[z] = w[r];
+    } else {
+      if (a.store_fmt >= 0) ((float2*)a.psi)[z] = v[r];
+      if (TWO && a.store_lam) ((float2*)a.lam)[z] = w[r];
+    }
+  }
+  }
+}
+
+}  // namespace
+}  // namespace qaoa
