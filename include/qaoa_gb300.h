@@ -288,6 +288,54 @@ void qaoa_launch_count_reset(void);
 int qaoa_timing_enable(int on);
 int qaoa_timing_read(double* ms, int64_t* launches, double* bytes, int64_t* dropped);
 
+/*
+ * Batched adjoint gradients of many small graphs (the batched workload: thousands
+ * of graphs of uneven n, each with its own angles).  Each graph gets exactly
+ * what qaoa_gradient computes from |+>: [E, <psi|psi>, dE/dgamma_1..p,
+ * dE/dbeta_1..p] (Eq. 1, Sec. IV-D), here for integer-weight graphs only.
+ * All graphs run in one persistent launch per tile size: each CTA takes the
+ * next graph (largest n first) and runs its whole plan, so there is one launch
+ * for the batch instead of ~2p(k-1)+3 per graph.  The paper evaluates graphs
+ * one at a time; batching is this library's addition.
+ *  graphs      ngraphs host descriptors (QAOA_WEIGHT_INT, n <= QAOA_BATCH_MAX_N,
+ *              m <= QAOA_BATCH_MAX_EDGES); checked as by qaoa_graph_check.
+ *  angles      host, ngraphs x 2p doubles: row i = [gamma_1..p | beta_1..p]
+ *              of graph i.  1 <= p <= QAOA_BATCH_MAX_P.
+ *  tiles       optional host array of QAOA_MAX_N + 1 int32 indexed by n: 0 =
+ *              2^10-amplitude tiles, 1 = 2^12 (NULL: 0 for n <= 10, else 1),
+ *              e.g. from qaoa_batch_autotune.
+ *  out_dev     device, ngraphs x (2p + 2) doubles, row i for graph i.
+ *  ws_dev      at least qaoa_batch_workspace_size() bytes (256-byte aligned);
+ *              it holds every graph's cost vector, state and lambda buffers.
+ * Errors: QAOA_ERR_INVALID_ARG (a bad graph, angle or pointer),
+ * QAOA_ERR_UNSUPPORTED (float weights, or a graph past the limits),
+ * QAOA_ERR_WORKSPACE.  The graph and angle arrays are read before the call
+ * returns; the copy of them to the workspace is enqueued on `stream`.
+ */
+#define QAOA_BATCH_MAX_N 26
+#define QAOA_BATCH_MAX_P 12
+#define QAOA_BATCH_MAX_EDGES 512
+#define QAOA_BATCH_MAX_GRAPHS (1 << 20)
+int qaoa_batch_workspace_size(int dtype, int p, int ngraphs, const qaoa_graph_t* graphs,
+                              const int32_t* tiles, size_t* bytes);
+int qaoa_batch_gradient(int dtype, int ngraphs, const qaoa_graph_t* graphs, const double* angles,
+                        int p, const int32_t* tiles, double* out_dev, void* ws_dev, size_t ws_bytes,
+                        void* stream);
+
+/*
+ * Tile-size autotuner for qaoa_batch_gradient: for each n in [n_lo, n_hi]
+ * times a batch of graphs_per_n synthetic graphs of n vertices (a ring plus
+ * (u, u + 3) chords, integer weights 1..5) with 2^10 and with 2^12 tiles (one
+ * warm-up run each, then one run timed with CUDA events on `stream`) and sets
+ * tiles_out[n] (QAOA_MAX_N + 1 entries; entries outside [n_lo, n_hi] get the
+ * default) to the faster.  ms_out (optional, 2 * (QAOA_MAX_N + 1) doubles)
+ * receives the times at [2n + tile].  Synchronises `stream`.  Workspace:
+ * qaoa_batch_autotune_workspace_size().
+ */
+int qaoa_batch_autotune_workspace_size(int dtype, int p, int n_hi, int graphs_per_n, size_t* bytes);
+int qaoa_batch_autotune(int dtype, int p, int n_lo, int n_hi, int graphs_per_n, int32_t* tiles_out,
+                        double* ms_out, void* ws_dev, size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

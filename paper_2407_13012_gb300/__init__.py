@@ -28,12 +28,14 @@ COST_I32, COST_F64 = 0, 1
 WEIGHT_INT, WEIGHT_F64 = 0, 1
 OP_COST, OP_LAYERS, OP_EXPECTATION, OP_SAMPLE, OP_GRADIENT, OP_OPTIMIZE = range(6)
 MAX_N, MAX_P, MAX_TABLE_SPAN = 32, 64, 16384
+BATCH_MAX_N, BATCH_MAX_P, BATCH_MAX_EDGES = 26, 12, 512
 
 EXPORTS = [
     "qaoa_version", "qaoa_strerror", "qaoa_graph_check", "qaoa_workspace_size", "qaoa_cost_vector",
     "qaoa_apply_layers", "qaoa_expectation", "qaoa_expectation_host", "qaoa_sample", "qaoa_sample_host",
     "qaoa_gradient", "qaoa_gradient_host", "qaoa_launch_count", "qaoa_launch_count_reset",
     "qaoa_timing_enable", "qaoa_timing_read", "qaoa_gradient_dev", "qaoa_optimize_adam", "qaoa_expectation_noalloc",
+    "qaoa_batch_workspace_size", "qaoa_batch_gradient", "qaoa_batch_autotune_workspace_size", "qaoa_batch_autotune",
 ]
 
 
@@ -74,6 +76,10 @@ def _load() -> ct.CDLL:
         "qaoa_gradient_dev": ([i32, i32, vp, vp, ct.POINTER(CostT), vp, i32, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_optimize_adam": ([i32, i32, vp, vp, ct.POINTER(CostT), vp, i32, i64, ct.c_double, ct.c_double,
                                 ct.c_double, ct.c_double, vp, vp, ct.c_size_t, vp], i32),
+        "qaoa_batch_workspace_size": ([i32, i32, i32, ct.POINTER(GraphT), vp, szp], i32),
+        "qaoa_batch_gradient": ([i32, i32, ct.POINTER(GraphT), dp, i32, vp, vp, vp, ct.c_size_t, vp], i32),
+        "qaoa_batch_autotune_workspace_size": ([i32, i32, i32, i32, szp], i32),
+        "qaoa_batch_autotune": ([i32, i32, i32, i32, i32, vp, dp, vp, ct.c_size_t, vp], i32),
         "qaoa_launch_count": ([], i64),
         "qaoa_launch_count_reset": ([], None),
         "qaoa_timing_enable": ([i32], i32),
@@ -365,6 +371,54 @@ def optimize_adam(cost: CostVector, angles, steps: int, lr: float = 0.01, betas=
                                    ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(_stream(angles.device))),
            "optimize_adam")
     return hist[:steps] if hist is not None else None
+
+
+def _tiles_arg(tiles):
+    if tiles is None:
+        return None, None
+    arr = np.ascontiguousarray(np.asarray(tiles, dtype=np.int32).reshape(-1))
+    if len(arr) != MAX_N + 1:
+        raise ValueError(f"tiles must have {MAX_N + 1} entries (indexed by n)")
+    return arr, arr.ctypes.data_as(ct.c_void_p)
+
+
+def batch_gradient(graphs, angles, dtype: str = "c128", tiles=None, device="cuda"):
+    """Batched S7 for many small integer-weight graphs in one persistent launch.
+
+    graphs: sequence of Graph; angles: (ngraphs, 2p) host array, row i = [gamma | beta] of
+    graph i.  Returns a (ngraphs, 2p + 2) float64 device tensor, row i = [E, norm,
+    dE/dgamma_1..p, dE/dbeta_1..p] of graph i."""
+    torch = _torch()
+    ng = len(graphs)
+    ang = np.ascontiguousarray(np.asarray(angles, dtype=np.float64).reshape(ng, -1))
+    p = ang.shape[1] // 2
+    dt = C128 if dtype == "c128" else C64
+    structs = (GraphT * max(ng, 1))(*[g.as_struct() for g in graphs])
+    tarr, tptr = _tiles_arg(tiles)
+    nbytes = ct.c_size_t()
+    _check(_lib.qaoa_batch_workspace_size(dt, p, ng, structs, tptr, ct.byref(nbytes)), "batch_workspace_size")
+    ws = _workspace(nbytes.value, device)
+    out = torch.empty((max(ng, 1), 2 * p + 2), dtype=torch.float64, device=device)
+    _check(_lib.qaoa_batch_gradient(dt, ng, structs, ang.ctypes.data_as(ct.POINTER(ct.c_double)), p, tptr,
+                                    ct.c_void_p(out.data_ptr()), ct.c_void_p(ws.data_ptr()), ws.numel(),
+                                    ct.c_void_p(_stream(device))), "batch_gradient")
+    return out[:ng]
+
+
+def batch_autotune(dtype: str = "c128", p: int = 3, n_lo: int = 8, n_hi: int = 20, graphs_per_n: int = 304,
+                   device="cuda"):
+    """Measured tile choice per qubit count for batch_gradient: (tiles[MAX_N + 1], ms[(MAX_N + 1), 2])."""
+    dt = C128 if dtype == "c128" else C64
+    nbytes = ct.c_size_t()
+    _check(_lib.qaoa_batch_autotune_workspace_size(dt, p, n_hi, graphs_per_n, ct.byref(nbytes)),
+           "batch_autotune_workspace_size")
+    ws = _workspace(nbytes.value, device)
+    tiles = np.zeros(MAX_N + 1, dtype=np.int32)
+    ms = np.zeros(2 * (MAX_N + 1), dtype=np.float64)
+    _check(_lib.qaoa_batch_autotune(dt, p, n_lo, n_hi, graphs_per_n, ct.c_void_p(tiles.ctypes.data),
+                                    ms.ctypes.data_as(ct.POINTER(ct.c_double)), ct.c_void_p(ws.data_ptr()),
+                                    ws.numel(), ct.c_void_p(_stream(device))), "batch_autotune")
+    return tiles, ms.reshape(MAX_N + 1, 2)
 
 
 def launch_count() -> int:

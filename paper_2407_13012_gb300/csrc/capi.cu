@@ -372,6 +372,40 @@ static void plan_forward(int k, int p, bool init, std::vector<Sweep>& sw) {
   }
 }
 
+// Gradient schedule (Sec. IV-D): the p forward layers from |+>; in the last forward sweep
+// lambda = C psi and <C>; then the adjoint pass, layer by layer in reverse, visiting the
+// groups so that consecutive layers share a sweep.  new_acc(sweep, out0, outs) returns the
+// accumulator for `outs` consecutive outputs from out0 (0 = E, 1 = norm, 2 + l = dE/dgamma_l,
+// 2 + p + l = dE/dbeta_l).  The last sweep stores psi (uncomputed) and drops lambda.
+template <class F>
+static void plan_gradient(int k, int p, std::vector<Sweep>& sw, F new_acc) {
+  plan_forward(k, p, true, sw);
+  Sweep* cur = &sw.back();
+  cur->two = true;
+  cur->store_lam = true;
+  cur->ops.push_back(make_op(OP_LAMBDA, 0, 0));
+  cur->ops.push_back(make_op(OP_RED_EXPECT, F_PSI, 0, new_acc(*cur, 0, 2)));
+  for (int l = p - 1; l >= 0; --l) {
+    const int first = cur->group;
+    for (int idx = 0; idx < k; ++idx) {
+      const int gi = (first == 0) ? idx : k - 1 - idx;
+      if (idx > 0) {
+        Sweep s;
+        s.group = gi;
+        s.two = true;
+        s.load_lam = true;
+        s.store_lam = true;
+        sw.push_back(s);
+        cur = &sw.back();
+      }
+      cur->ops.push_back(make_op(OP_MIX, F_PSI | F_LAM | F_SIGN | F_XTERM, l, new_acc(*cur, 2 + p + l, 1)));
+    }
+    cur->ops.push_back(make_op(OP_RED_CTERM, F_PSI | F_LAM, l, new_acc(*cur, 2 + l, 1)));
+    cur->ops.push_back(make_op(OP_PHASE, F_PSI | F_LAM | F_SIGN, l));
+  }
+  cur->store_lam = false;
+}
+
 static bool valid_dtype(int d) { return d == QAOA_C128 || d == QAOA_C64; }
 static bool valid_cost(const qaoa_cost_t* c) {
   return c != nullptr && c->C_dev != nullptr && (c->dtype == QAOA_COST_I32 || c->dtype == QAOA_COST_F64);
@@ -628,43 +662,18 @@ static int gradient_impl(int n, int dtype, void* psi_dev, void* lambda_dev, cons
   const std::vector<Group> gs = plan_groups(n, B);
   const int k = (int)gs.size();
   std::vector<Sweep> sw;
-  plan_forward(k, p, true, sw);
   // outputs: 0 = E, 1 = norm, 2 + l = dE/dgamma_l, 2 + p + l = dE/dbeta_l
   const int nout = 2 * p + 2;
   std::vector<int> ncontrib(nout, 0);
-  auto new_acc = [&](Sweep& s, int out0, int outs) {
+  plan_gradient(k, p, sw, [&](Sweep& s, int out0, int outs) {
     const uint32_t acc = (uint32_t)s.red_slot.size();
     for (int i = 0; i < outs; ++i) {
       s.red_slot.push_back((out0 + i) * kMaxContrib + ncontrib[out0 + i]);
       ncontrib[out0 + i]++;
     }
     return acc;
-  };
-  Sweep* cur = &sw.back();
-  cur->two = true;
-  cur->store_lam = true;
-  cur->ops.push_back(make_op(OP_LAMBDA, 0, 0));
-  cur->ops.push_back(make_op(OP_RED_EXPECT, F_PSI, 0, new_acc(*cur, 0, 2)));
-  for (int l = p - 1; l >= 0; --l) {
-    const int first = cur->group;
-    for (int idx = 0; idx < k; ++idx) {
-      const int gi = (first == 0) ? idx : k - 1 - idx;
-      if (idx > 0) {
-        Sweep s;
-        s.group = gi;
-        s.two = true;
-        s.load_lam = true;
-        s.store_lam = true;
-        sw.push_back(s);
-        cur = &sw.back();
-      }
-      cur->ops.push_back(make_op(OP_MIX, F_PSI | F_LAM | F_SIGN | F_XTERM, l, new_acc(*cur, 2 + p + l, 1)));
-    }
-    cur->ops.push_back(make_op(OP_RED_CTERM, F_PSI | F_LAM, l, new_acc(*cur, 2 + l, 1)));
-    cur->ops.push_back(make_op(OP_PHASE, F_PSI | F_LAM | F_SIGN, l));
-  }
-  cur->store_lam = false;
-  cur->store_user = true;
+  });
+  sw.back().store_user = true;
   for (int o = 0; o < nout; ++o)
     if (ncontrib[o] > kMaxContrib) return QAOA_ERR_UNSUPPORTED;
   for (const Sweep& s : sw)
@@ -760,6 +769,307 @@ int qaoa_gradient_host(int n, int dtype, void* psi_dev, void* lambda_dev, const 
   if (cudaMemcpyAsync(out_host, out_dev, (2 * p + 2) * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return QAOA_ERR_CUDA;
   return cuda_status(cudaStreamSynchronize(s));
+}
+
+// ------------------------------------------------------------ batched gradients
+
+namespace {
+
+struct BatchLayout {
+  std::vector<BatchGraph> graphs;  // processing order: large-tile graphs, then small-tile, n descending
+  std::vector<BatchPlan> plans;
+  std::vector<int> edges;
+  std::vector<int64_t> blk_off;
+  std::vector<double> angles;      // processing order
+  int n_large = 0;                 // graphs [0, n_large) use 2^12 tiles, the rest 2^10
+  size_t off_graphs = 0, off_plans = 0, off_blk = 0, off_edges = 0, off_angles = 0, head_bytes = 0;
+  size_t off_queue = 0, off_trig = 0, off_psi = 0, off_lam = 0, off_C = 0, off_phase = 0, off_dtab = 0,
+         off_turn = 0, total = 0;
+};
+
+int default_tile(int n) { return n <= 10 ? 0 : 1; }
+
+// the gradient plan of n qubits on 2^B tiles, accumulators = output indices
+int batch_plan(int n, int B, int p, BatchPlan& P) {
+  std::memset(&P, 0, sizeof(P));
+  const std::vector<Group> gs = plan_groups(n, B);
+  std::vector<Sweep> sw;
+  plan_gradient((int)gs.size(), p, sw, [](Sweep&, int out0, int) { return (uint32_t)out0; });
+  if ((int)sw.size() > kBatchMaxSweeps) return QAOA_ERR_UNSUPPORTED;
+  int tmax = 1;
+  for (const Group& g : gs) tmax = std::max(tmax, g.t);
+  P.n = n;
+  P.fx_shift = fx_shift_for(tmax);
+  const double amp0 = std::pow(2.0, -0.5 * n);
+  P.init_fx = (long long)std::llrint(std::ldexp(amp0, P.fx_shift));
+  P.init_f32 = (float)amp0;
+  P.nsweeps = (int)sw.size();
+  for (int i = 0; i < P.nsweeps; ++i) {
+    const Sweep& s = sw[i];
+    BatchSweep& b = P.sw[i];
+    const Group& g = gs[s.group];
+    if ((int)s.ops.size() > kBatchMaxOps) return QAOA_ERR_UNSUPPORTED;
+    b.g = {n, g.j0, g.t, g.c, tiles_of(g, n)};
+    b.load_fmt = s.init ? 2 : 0;
+    // the final state is not needed: the last sweep stores nothing
+    b.store_fmt = (i == P.nsweeps - 1 || !s.store_psi) ? -1 : 0;
+    b.load_lam = s.two && s.load_lam;
+    b.store_lam = s.two && s.store_lam;
+    b.nops = (int)s.ops.size();
+    for (int k = 0; k < b.nops; ++k) {
+      b.ops[k] = s.ops[k];
+      const uint32_t kind = s.ops[k] & 0xff;
+      if (kind == OP_PHASE || kind == OP_LAMBDA || kind == OP_RED_EXPECT || kind == OP_RED_CTERM) b.needs_cost = 1;
+    }
+  }
+  return QAOA_OK;
+}
+
+int batch_layout(int dtype, int p, int ngraphs, const qaoa_graph_t* gs, const double* angles, const int32_t* tiles,
+                 BatchLayout& L) {
+  if (!valid_dtype(dtype) || p < 1 || p > QAOA_BATCH_MAX_P || ngraphs < 0 || ngraphs > QAOA_BATCH_MAX_GRAPHS)
+    return QAOA_ERR_INVALID_ARG;
+  if (ngraphs > 0 && gs == nullptr) return QAOA_ERR_INVALID_ARG;
+  const bool fx = dtype == QAOA_C128;
+  const size_t vs = fx ? 16 : 8;
+  std::vector<int64_t> cmin(ngraphs), cmax(ngraphs);
+  std::vector<int> tile(ngraphs);
+  for (int i = 0; i < ngraphs; ++i) {
+    const qaoa_graph_t& g = gs[i];
+    if (qaoa_graph_check(&g, &cmin[i], &cmax[i]) != QAOA_OK) return QAOA_ERR_INVALID_ARG;
+    if (g.weight_kind != QAOA_WEIGHT_INT) return QAOA_ERR_UNSUPPORTED;
+    if (g.n > QAOA_BATCH_MAX_N || g.m > QAOA_BATCH_MAX_EDGES) return QAOA_ERR_UNSUPPORTED;
+    tile[i] = tiles ? tiles[g.n] : default_tile(g.n);
+    if (tile[i] != 0 && tile[i] != 1) return QAOA_ERR_INVALID_ARG;
+  }
+  if (angles != nullptr)
+    for (int64_t i = 0; i < (int64_t)ngraphs * 2 * p; ++i)
+      if (!std::isfinite(angles[i])) return QAOA_ERR_INVALID_ARG;
+  std::vector<int> order(ngraphs);
+  for (int i = 0; i < ngraphs; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (tile[a] != tile[b]) return tile[a] > tile[b];
+    return gs[a].n > gs[b].n;
+  });
+  // plans per (n, tile)
+  int plan_of[2][QAOA_MAX_N + 1];
+  for (int t = 0; t < 2; ++t)
+    for (int n = 0; n <= QAOA_MAX_N; ++n) plan_of[t][n] = -1;
+  L = BatchLayout();
+  L.graphs.resize(ngraphs);
+  L.blk_off.assign(ngraphs + 1, 0);
+  L.angles.assign((size_t)ngraphs * 2 * p, 0.0);
+  int64_t amps = 0, tab = 0, edge = 0;
+  for (int k = 0; k < ngraphs; ++k) {
+    const int i = order[k];
+    const qaoa_graph_t& g = gs[i];
+    BatchGraph& G = L.graphs[k];
+    G.n = g.n;
+    G.m = (int)g.m;
+    G.out = i;
+    if (plan_of[tile[i]][g.n] < 0) {
+      BatchPlan P;
+      const int rc = batch_plan(g.n, batch_tile_bits(tile[i]), p, P);
+      if (rc) return rc;
+      plan_of[tile[i]][g.n] = (int)L.plans.size();
+      L.plans.push_back(P);
+    }
+    G.plan = plan_of[tile[i]][g.n];
+    const int64_t cb = std::max(std::llabs(cmin[i]), std::llabs(cmax[i]));
+    int ls = 0;
+    while (ls < 40 && ((int64_t)1 << ls) < cb) ++ls;
+    G.lam_shift = ls;
+    const int64_t span = cmax[i] - cmin[i] + 1;
+    G.cmin = (int)cmin[i];
+    G.span = (span >= 1 && span <= QAOA_MAX_TABLE_SPAN) ? (int)span : 0;
+    G.state = amps;
+    G.cost = amps;
+    amps += std::max<int64_t>((int64_t)1 << g.n, 64);  // 64-element (>= 256-byte) alignment
+    G.table = tab;
+    tab += (int64_t)p * G.span;
+    G.edge = edge;
+    for (int64_t e = 0; e < g.m; ++e) {
+      L.edges.push_back(g.uv[2 * e]);
+      L.edges.push_back(g.uv[2 * e + 1]);
+      L.edges.push_back(g.w ? (int)g.w[e] : 1);
+    }
+    edge += g.m;
+    L.blk_off[k + 1] = L.blk_off[k] + (((int64_t)1 << g.n) + (1 << kBatchCostBits) - 1) / (1 << kBatchCostBits);
+    if (angles != nullptr)
+      for (int j = 0; j < 2 * p; ++j) L.angles[(size_t)k * 2 * p + j] = angles[(size_t)i * 2 * p + j];
+    if (tile[i] == 1) L.n_large = k + 1;
+  }
+  if (L.edges.empty()) L.edges.push_back(0);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += round256(bytes);
+    return at;
+  };
+  L.off_graphs = take(sizeof(BatchGraph) * std::max(ngraphs, 1));
+  L.off_plans = take(sizeof(BatchPlan) * std::max<size_t>(L.plans.size(), 1));
+  L.off_blk = take(sizeof(int64_t) * (ngraphs + 1));
+  L.off_edges = take(sizeof(int) * L.edges.size());
+  L.off_angles = take(sizeof(double) * std::max<size_t>(L.angles.size(), 1));
+  L.head_bytes = o;
+  L.off_queue = take(256);
+  L.off_trig = take(sizeof(double) * 3 * p * std::max(ngraphs, 1));
+  L.off_psi = take(vs * std::max<int64_t>(amps, 1));
+  L.off_lam = take(vs * std::max<int64_t>(amps, 1));
+  L.off_C = take(4 * std::max<int64_t>(amps, 1));
+  L.off_phase = take(vs * std::max<int64_t>(tab, 1));
+  L.off_dtab = take(fx ? (size_t)16 * p * 196 * std::max(ngraphs, 1) : 0);
+  L.off_turn = take(fx ? (size_t)16 * 3072 : 0);
+  L.total = o;
+  return QAOA_OK;
+}
+
+int batch_run(int dtype, int p, const BatchLayout& L, double* out_dev, void* ws_dev, size_t ws_bytes, void* stream) {
+  if (ws_dev == nullptr || ws_bytes < L.total || ((uintptr_t)ws_dev & 255)) return QAOA_ERR_WORKSPACE;
+  const int ng = (int)L.graphs.size();
+  if (ng == 0) return QAOA_OK;
+  if (out_dev == nullptr) return QAOA_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ws = (char*)ws_dev;
+  // one upload of the host-built header
+  std::vector<char> head(L.head_bytes, 0);
+  std::memcpy(head.data() + L.off_graphs, L.graphs.data(), sizeof(BatchGraph) * ng);
+  std::memcpy(head.data() + L.off_plans, L.plans.data(), sizeof(BatchPlan) * L.plans.size());
+  std::memcpy(head.data() + L.off_blk, L.blk_off.data(), sizeof(int64_t) * L.blk_off.size());
+  std::memcpy(head.data() + L.off_edges, L.edges.data(), sizeof(int) * L.edges.size());
+  std::memcpy(head.data() + L.off_angles, L.angles.data(), sizeof(double) * L.angles.size());
+  if (cudaMemcpyAsync(ws, head.data(), L.head_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return QAOA_ERR_CUDA;
+  if (cudaMemsetAsync(ws + L.off_queue, 0, 256, s) != cudaSuccess) return QAOA_ERR_CUDA;
+  BatchArgs b;
+  std::memset(&b, 0, sizeof(b));
+  b.ngraphs = ng;
+  b.p = p;
+  b.dtype = dtype;
+  b.graphs = (const BatchGraph*)(ws + L.off_graphs);
+  b.plans = (const BatchPlan*)(ws + L.off_plans);
+  b.edges = (const int*)(ws + L.off_edges);
+  b.blk_off = (const int64_t*)(ws + L.off_blk);
+  b.angles = (const double*)(ws + L.off_angles);
+  b.psi = ws + L.off_psi;
+  b.lam = ws + L.off_lam;
+  b.C = (int*)(ws + L.off_C);
+  b.phase = ws + L.off_phase;
+  b.dtab = dtype == QAOA_C128 ? ws + L.off_dtab : nullptr;
+  b.turn = dtype == QAOA_C128 ? ws + L.off_turn : nullptr;
+  b.trig = (double*)(ws + L.off_trig);
+  b.out = out_dev;
+  int rc = cuda_status(launch_batch_prep(b, L.blk_off[ng], s));
+  if (rc) return rc;
+  int* queue = (int*)(ws + L.off_queue);
+  rc = cuda_status(launch_batch(b, 1, 0, L.n_large, queue, s));
+  if (rc) return rc;
+  return cuda_status(launch_batch(b, 0, L.n_large, ng - L.n_large, queue + 1, s));
+}
+
+}  // namespace
+
+int qaoa_batch_workspace_size(int dtype, int p, int ngraphs, const qaoa_graph_t* graphs, const int32_t* tiles,
+                              size_t* bytes) {
+  if (bytes == nullptr) return QAOA_ERR_INVALID_ARG;
+  BatchLayout L;
+  const int rc = batch_layout(dtype, p, ngraphs, graphs, nullptr, tiles, L);
+  if (rc) return rc;
+  *bytes = L.total;
+  return QAOA_OK;
+}
+
+int qaoa_batch_gradient(int dtype, int ngraphs, const qaoa_graph_t* graphs, const double* angles, int p,
+                        const int32_t* tiles, double* out_dev, void* ws_dev, size_t ws_bytes, void* stream) {
+  if (ngraphs > 0 && angles == nullptr) return QAOA_ERR_INVALID_ARG;
+  BatchLayout L;
+  const int rc = batch_layout(dtype, p, ngraphs, graphs, angles, tiles, L);
+  if (rc) return rc;
+  return batch_run(dtype, p, L, out_dev, ws_dev, ws_bytes, stream);
+}
+
+// synthetic tuning instances: a ring plus chords (u, u + 3), integer weights 1..5
+static void tune_graph(int n, int seed, std::vector<int>& uv, std::vector<double>& w) {
+  std::set<std::pair<int, int>> seen;
+  uv.clear();
+  w.clear();
+  for (int d : {1, 3})
+    for (int u = 0; u < n; ++u) {
+      const int v = (u + d) % n;
+      if (u == v) continue;
+      const std::pair<int, int> e{std::min(u, v), std::max(u, v)};
+      if (!seen.insert(e).second) continue;
+      uv.push_back(e.first);
+      uv.push_back(e.second);
+      w.push_back((double)(1 + (u * 7 + d + seed) % 5));
+    }
+}
+
+int qaoa_batch_autotune_workspace_size(int dtype, int p, int n_hi, int graphs_per_n, size_t* bytes) {
+  if (bytes == nullptr || n_hi < 2 || n_hi > QAOA_BATCH_MAX_N || graphs_per_n < 1 || graphs_per_n > 65536)
+    return QAOA_ERR_INVALID_ARG;
+  std::vector<int> uv;
+  std::vector<double> w;
+  tune_graph(n_hi, 0, uv, w);
+  std::vector<qaoa_graph_t> gs(graphs_per_n, qaoa_graph_t{n_hi, (int64_t)w.size(), uv.data(), w.data(), QAOA_WEIGHT_INT});
+  size_t b0 = 0, b1 = 0;
+  const int32_t zero[QAOA_MAX_N + 1] = {0};
+  int32_t one[QAOA_MAX_N + 1];
+  for (int& x : one) x = 1;
+  int rc = qaoa_batch_workspace_size(dtype, p, graphs_per_n, gs.data(), zero, &b0);
+  if (rc) return rc;
+  rc = qaoa_batch_workspace_size(dtype, p, graphs_per_n, gs.data(), one, &b1);
+  if (rc) return rc;
+  *bytes = std::max(b0, b1) + 256 + (size_t)graphs_per_n * (2 * p + 2) * sizeof(double);
+  return QAOA_OK;
+}
+
+int qaoa_batch_autotune(int dtype, int p, int n_lo, int n_hi, int graphs_per_n, int32_t* tiles_out, double* ms_out,
+                        void* ws_dev, size_t ws_bytes, void* stream) {
+  if (tiles_out == nullptr || n_lo < 2 || n_lo > n_hi) return QAOA_ERR_INVALID_ARG;
+  size_t need = 0;
+  int rc = qaoa_batch_autotune_workspace_size(dtype, p, n_hi, graphs_per_n, &need);
+  if (rc) return rc;
+  if (ws_dev == nullptr || ws_bytes < need) return QAOA_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* out = (double*)((char*)ws_dev + (need - (size_t)graphs_per_n * (2 * p + 2) * sizeof(double)));
+  for (int n = 0; n <= QAOA_MAX_N; ++n) tiles_out[n] = default_tile(n);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return QAOA_ERR_CUDA;
+  std::vector<double> ang((size_t)graphs_per_n * 2 * p);
+  for (size_t i = 0; i < ang.size(); ++i) ang[i] = 0.1 + 0.37 * (double)(i % 7);
+  rc = QAOA_OK;
+  for (int n = n_lo; n <= n_hi && rc == QAOA_OK; ++n) {
+    std::vector<std::vector<int>> uvs(graphs_per_n);
+    std::vector<std::vector<double>> ws(graphs_per_n);
+    std::vector<qaoa_graph_t> gs(graphs_per_n);
+    for (int i = 0; i < graphs_per_n; ++i) {
+      tune_graph(n, i, uvs[i], ws[i]);
+      gs[i] = qaoa_graph_t{n, (int64_t)ws[i].size(), uvs[i].data(), ws[i].data(), QAOA_WEIGHT_INT};
+    }
+    double best = 0.0;
+    for (int t = 0; t < 2 && rc == QAOA_OK; ++t) {
+      int32_t tiles[QAOA_MAX_N + 1];
+      for (int& x : tiles) x = t;
+      BatchLayout L;
+      rc = batch_layout(dtype, p, graphs_per_n, gs.data(), ang.data(), tiles, L);
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && rc == QAOA_OK; ++rep) {  // warm-up, then timed
+        cudaEventRecord(e0, s);
+        rc = batch_run(dtype, p, L, out, ws_dev, ws_bytes, stream);
+        cudaEventRecord(e1, s);
+        if (rc == QAOA_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = QAOA_ERR_CUDA;
+        if (rc == QAOA_OK) cudaEventElapsedTime(&ms, e0, e1);
+      }
+      if (ms_out) ms_out[2 * n + t] = ms;
+      if (rc == QAOA_OK && (t == 0 || ms < best)) {
+        best = ms;
+        tiles_out[n] = t;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
 }
 
 int64_t qaoa_launch_count(void) { return g_launches.load(); }

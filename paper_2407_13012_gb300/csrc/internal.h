@@ -163,4 +163,68 @@ size_t sample_ws_bytes(int n, int dtype);
 // after it; `bytes` (algorithmic HBM bytes of the launch) is read on the second call
 void note_launch(int kind, cudaStream_t s, bool begin, double bytes = 0.0);
 
+// ---------------------------------------------------------------- batched gradients
+//
+// Many small graphs in one persistent launch: each CTA takes the next graph from a work
+// counter (graphs sorted by n, largest first) and runs that graph's whole sweep plan
+// (forward layers, lambda, adjoint pass) over its own state, synchronising only within
+// the CTA; its reductions go straight to the graph's output row.
+
+constexpr int kBatchMaxOps = 64;     // ops per sweep of a batched plan
+constexpr int kBatchMaxSweeps = 32;  // sweeps per batched plan
+
+struct BatchSweep {
+  SweepGeom g;
+  int load_fmt, store_fmt, load_lam, store_lam, needs_cost, nops;
+  uint32_t ops[kBatchMaxOps];  // accumulator field = output index
+};
+
+// sweep plan of one qubit count on one tile configuration
+struct BatchPlan {
+  int n;
+  int fx_shift;
+  long long init_fx;
+  float init_f32;
+  int nsweeps;
+  BatchSweep sw[kBatchMaxSweeps];
+};
+
+struct BatchGraph {
+  int n, m;
+  int plan;        // index into the plans
+  int out;         // output row (the caller's graph index)
+  int lam_shift;   // fixed point: 2^lam_shift >= max |C|
+  int cmin, span;  // integer cost range covered by the phase table (span 0: no table)
+  int64_t state;   // element offset of psi and lambda in the state arenas
+  int64_t cost;    // element offset of C in the cost arena
+  int64_t table;   // entry offset of the p * span phase-table entries
+  int64_t edge;    // offset of the (u, v, w) triples in the edge array
+};
+
+struct BatchArgs {
+  int ngraphs;               // graphs in processing order
+  int p;
+  int dtype;
+  const BatchGraph* graphs;
+  const BatchPlan* plans;
+  const int* edges;          // (u, v, w) integer triples
+  const int64_t* blk_off;    // cost kernel: first block of each graph (ngraphs + 1)
+  const double* angles;      // [gamma p | beta p] per graph, processing order
+  void* psi;                 // state arenas (internal format)
+  void* lam;
+  int* C;                    // cost arena (int32)
+  void* phase;               // phase tables
+  void* dtab;                // fixed point: p * 196 mixer diagonals per graph
+  void* turn;                // fixed point: shared turn tables
+  double* trig;              // [g2pi p | cos p | sin p] per graph
+  double* out;               // (2p + 2) per graph, rows in the caller's order
+};
+
+constexpr int kBatchCostBits = 12;  // cost-kernel entries per block: 2^12
+
+cudaError_t launch_batch_prep(const BatchArgs& b, int64_t cost_blocks, cudaStream_t s);
+// tile: 0 = small tiles (2^10 amplitudes), 1 = large tiles (2^12)
+cudaError_t launch_batch(const BatchArgs& b, int tile, int first, int count, int* queue, cudaStream_t s);
+int batch_tile_bits(int tile);
+
 }  // namespace qaoa

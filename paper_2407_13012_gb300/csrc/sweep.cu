@@ -377,8 +377,6 @@ __global__ void reduce_kernel(const __grid_constant__ ReducePlan r, const double
   if (threadIdx.x == 0) out[o] = sh[0] * r.scale[o];
 }
 
-__device__ __forceinline__ long long q62(double x) { return llrint(ldexp(x, 62)); }
-
 // integer-cost phase tables exp(-i gamma_l c), c = cmin + k; then (fixed point) the
 // mixer diagonals exp(-i beta_l (t - 2k)) for t = 1..13, k = 0..t, and the turn tables
 __global__ void tables_kernel(const __grid_constant__ TableArgs ta) {
@@ -391,25 +389,14 @@ __global__ void tables_kernel(const __grid_constant__ TableArgs ta) {
       const int l = (int)(i / ta.span);
       const int64_t c = ta.cmin + (i - (int64_t)l * ta.span);
       const double th = (ta.dev_angles ? ta.dev_angles[l] : ta.gamma[l]) * (double)c;
-      double sn, cs;
-      sincos(th, &sn, &cs);
-      if (ta.fx) ((longlong2*)ta.phase)[i] = make_longlong2(q62(cs), q62(-sn));
-      else ((float2*)ta.phase)[i] = make_float2((float)cs, (float)(-sn));
+      if (ta.fx) ((longlong2*)ta.phase)[i] = unit_q62(th);
+      else ((float2*)ta.phase)[i] = unit_f32(th);
     } else if (i < nphase + nd) {
       const int64_t j = i - nphase;
-      const int l = (int)(j / 196), t = (int)((j / 14) % 14), k = (int)(j % 14);
-      const double th = (ta.dev_angles ? ta.dev_angles[ta.p + l] : ta.beta[l]) * (double)(t - 2 * k);
-      double sn, cs;
-      sincos(th, &sn, &cs);
-      ((longlong2*)ta.dtab)[j] = (k <= t) ? make_longlong2(q62(cs), q62(-sn)) : make_longlong2(0, 0);
+      const int l = (int)(j / 196);
+      ((longlong2*)ta.dtab)[j] = d_entry(ta.dev_angles ? ta.dev_angles[ta.p + l] : ta.beta[l], (int)(j % 196));
     } else {
-      const int64_t j = i - nphase - nd;
-      const int level = (int)(j / 1024), k = (int)(j % 1024);
-      // exp(-2 pi i k / 2^(10 (level + 1)))
-      const double th = -2.0 * 3.141592653589793238 * (double)k * ldexp(1.0, -10 * (level + 1));
-      double sn, cs;
-      sincos(th, &sn, &cs);
-      ((longlong2*)ta.turn)[j] = make_longlong2(q62(cs), q62(sn));
+      ((longlong2*)ta.turn)[i - nphase - nd] = turn_entry((int)(i - nphase - nd));
     }
   }
 }

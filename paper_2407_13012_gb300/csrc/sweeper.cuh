@@ -644,6 +644,32 @@ struct Sweeper {
   }
 };
 
+// ------------------------------------------------------------------ table entries
+//
+// Integer-cost phase tables hold exp(-i gamma c); fixed-point mixer diagonals hold
+// exp(-i beta (t - 2k)) at [(l * 14 + t) * 14 + k] for t = 1..13, k = 0..t (zero past t);
+// the turn tables hold exp(-2 pi i k / 2^(10 (level + 1))) for level 0..2, k < 1024.
+__device__ __forceinline__ long long q62(double x) { return llrint(ldexp(x, 62)); }
+__device__ __forceinline__ longlong2 unit_q62(double th) {
+  double sn, cs;
+  sincos(th, &sn, &cs);
+  return make_longlong2(q62(cs), q62(-sn));
+}
+__device__ __forceinline__ float2 unit_f32(double th) {
+  double sn, cs;
+  sincos(th, &sn, &cs);
+  return make_float2((float)cs, (float)(-sn));
+}
+// entry j = t * 14 + k of one layer's mixer diagonals
+__device__ __forceinline__ longlong2 d_entry(double beta, int j) {
+  const int t = j / 14, k = j % 14;
+  return k <= t ? unit_q62(beta * (double)(t - 2 * k)) : make_longlong2(0, 0);
+}
+__device__ __forceinline__ longlong2 turn_entry(int j) {
+  const int level = j / 1024, k = j % 1024;
+  return unit_q62(2.0 * 3.141592653589793238 * (double)k * ldexp(1.0, -10 * (level + 1)));
+}
+
 // state loads: through the read-only path, or (COHERENT) through L2 for state that the same
 // launch wrote earlier
 template <bool COHERENT, class T>

@@ -32,6 +32,7 @@ PURPOSE = {
     "angles": int.from_bytes(b"angles__", "little"),
     "sample": int.from_bytes(b"sample__", "little"),
     "state": int.from_bytes(b"state___", "little"),
+    "batch": int.from_bytes(b"batch-gr", "little"),
 }
 
 
@@ -182,3 +183,26 @@ def graph(family: str, n: int, seed: int, weights: str = "unit", prob: float = 0
         raise ValueError(family)
     w = edge_weights(len(e), weights, seed, lo, hi)
     return e, w, weights in ("unit", "int")
+
+
+def batch_instances(count: int, seed: int, n_lo: int = 8, n_hi: int = 20, prob: float = 0.3, lo: int = 1,
+                    hi: int = 5, p: int = 3):
+    """The batched workload: ``count`` graphs, each a fair coin between a random 3-regular
+    graph (n uniform over the even values in [n_lo, n_hi]) and G(n, prob) (n uniform in
+    [n_lo, n_hi]), integer weights uniform in {lo..hi}, and its own angles U(0, pi).
+
+    Returns a list of (n, family, edges, weights, gammas, betas); graph i draws its edges,
+    weights and angles from the streams of seed ``seed * 2^20 + i``.
+    """
+    st = Stream(seed, "batch")
+    evens = [n for n in range(max(n_lo, 4), n_hi + 1) if n % 2 == 0]
+    out = []
+    for i in range(count):
+        reg3 = st.next_below(2) == 0 and len(evens) > 0
+        n = evens[st.next_below(len(evens))] if reg3 else n_lo + st.next_below(n_hi - n_lo + 1)
+        gseed = ((seed << 20) + i) & MASK64
+        e = regular3_edges(n, gseed) if reg3 else gnp_edges(n, prob, gseed)
+        w = edge_weights(len(e), "int", gseed, lo, hi)
+        gam, bet = angles(p, gseed)
+        out.append((n, "reg3" if reg3 else "gnp", e, w, gam, bet))
+    return out

@@ -104,3 +104,69 @@ def test_calls_reject_bad_arguments_before_launch():
                                ct.c_void_p(1 << 22), ct.c_void_p(1 << 21), 1 << 30, None) == q.QAOA_ERR_INVALID_ARG
     assert q.lib.qaoa_sample(10, q.C128, ct.c_void_p(1 << 20), ct.byref(cost), -1, 0, None, None, None, 0, None) \
         == q.QAOA_ERR_INVALID_ARG
+
+
+# ---------------------------------------------------------------- batched gradients
+
+def _batch_ws(graphs, p=3, dtype=q.C128, tiles=None):
+    structs = (q.GraphT * max(len(graphs), 1))(*[g.as_struct() for g in graphs])
+    tp = None
+    if tiles is not None:
+        tiles = np.ascontiguousarray(np.asarray(tiles, dtype=np.int32))
+        tp = ct.c_void_p(tiles.ctypes.data)
+    out = ct.c_size_t()
+    rc = q.lib.qaoa_batch_workspace_size(dtype, p, len(graphs), structs, tp, ct.byref(out))
+    return rc, out.value
+
+
+def _ring(n, w=None, integer=True):
+    e = np.array([[u, (u + 1) % n] for u in range(n)])
+    return q.Graph(n, e, np.asarray(w if w is not None else np.ones(n)), integer)
+
+
+def test_batch_workspace_sizes():
+    rc, b1 = _batch_ws([_ring(10)])
+    assert rc == 0 and b1 > 0
+    rc, b2 = _batch_ws([_ring(10), _ring(16)])
+    assert rc == 0
+    # states, lambda and costs of the n = 16 graph: (16 + 16 + 4) bytes x 2^16 at least
+    assert b2 - b1 >= 36 * 2 ** 16
+    rc, b3 = _batch_ws([_ring(10), _ring(16)], dtype=q.C64)
+    assert rc == 0 and b3 < b2
+    rc, b0 = _batch_ws([])
+    assert rc == 0
+
+
+@pytest.mark.parametrize("case", ["float_weights", "too_big", "p_zero", "p_large", "bad_tile", "bad_graph"])
+def test_batch_rejections(case):
+    tiles = None
+    graphs, p, want = [_ring(8)], 3, q.QAOA_ERR_INVALID_ARG
+    if case == "float_weights":
+        graphs, want = [_ring(8, np.full(8, 0.5), integer=False)], q.QAOA_ERR_UNSUPPORTED
+    elif case == "too_big":
+        graphs, want = [_ring(q.BATCH_MAX_N + 1)], q.QAOA_ERR_UNSUPPORTED
+    elif case == "p_zero":
+        p = 0
+    elif case == "p_large":
+        p = q.BATCH_MAX_P + 1
+    elif case == "bad_tile":
+        tiles = np.full(q.MAX_N + 1, 2)
+    elif case == "bad_graph":
+        graphs = [q.Graph(4, np.array([[0, 0]]), None, True)]
+    rc, _ = _batch_ws(graphs, p=p, tiles=tiles)
+    assert rc == want
+
+
+def test_batch_gradient_checks_arguments_before_gpu_work():
+    g = _ring(8)
+    structs = (q.GraphT * 1)(g.as_struct())
+    ang = np.zeros(6)
+    dp = ang.ctypes.data_as(ct.POINTER(ct.c_double))
+    # missing angles, then a workspace that is too small: both refused on the host
+    assert q.lib.qaoa_batch_gradient(q.C128, 1, structs, None, 3, None, None, None, 0, None) == q.QAOA_ERR_INVALID_ARG
+    assert q.lib.qaoa_batch_gradient(q.C128, 1, structs, dp, 3, None, None, None, 0, None) == q.QAOA_ERR_WORKSPACE
+    ang[2] = float("nan")
+    assert q.lib.qaoa_batch_gradient(q.C128, 1, structs, dp, 3, None, None, None, 0, None) == q.QAOA_ERR_INVALID_ARG
+    size = ct.c_size_t()
+    assert q.lib.qaoa_batch_autotune_workspace_size(q.C128, 3, 12, 4, ct.byref(size)) == 0 and size.value > 0
+    assert q.lib.qaoa_batch_autotune_workspace_size(q.C128, 3, q.BATCH_MAX_N + 1, 4, ct.byref(size)) != 0

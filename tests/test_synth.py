@@ -44,3 +44,18 @@ def test_weights_and_angles():
     assert len(g) == len(b) == 6 and np.all((g >= 0) & (g < np.pi))
     psi = synth.random_state(7, 1)
     assert abs(np.linalg.norm(psi) - 1) < 1e-14
+
+
+def test_batch_instances_families_sizes_and_determinism():
+    a = synth.batch_instances(200, 4, n_lo=8, n_hi=20, p=3)
+    b = synth.batch_instances(200, 4, n_lo=8, n_hi=20, p=3)
+    fams = {"reg3": 0, "gnp": 0}
+    for (n, fam, e, w, gam, bet), y in zip(a, b):
+        assert np.array_equal(e, y[2]) and np.array_equal(w, y[3]) and np.array_equal(gam, y[4])
+        assert 8 <= n <= 20 and len(gam) == 3 and len(bet) == 3
+        assert np.all((w >= 1) & (w <= 5)) and np.all(w == np.floor(w))
+        assert np.all((0 <= e) & (e < n)) and np.all(e[:, 0] < e[:, 1])
+        if fam == "reg3":
+            assert n % 2 == 0 and np.all(np.bincount(e.ravel(), minlength=n) == 3)
+        fams[fam] += 1
+    assert 70 <= fams["reg3"] <= 130
