@@ -79,6 +79,36 @@ def test_pubo_literal_reading_differs():
     assert list(F) == [0, 1, 1, 0]
 
 
+def random_pubo_terms(n, nterms, seed, integer=True):
+    """Terms of degree 0..4 over n variables with weights in {-5..5} (or U(-1, 1))."""
+    u = synth.uniforms(seed, "weights", 6 * nterms).reshape(nterms, 6)
+    terms = []
+    for r in u:
+        deg = int(r[0] * 5)
+        vars_ = sorted({int(x * n) for x in r[1:1 + deg]})
+        wk = float(int(r[5] * 11) - 5) if integer else 2.0 * r[5] - 1.0
+        terms.append((wk, vars_))
+    return terms
+
+
+def test_pubo_closed_forms_higher_degree():
+    """Eq. 3 with terms of degree up to 4: a term of degree d is 1 on exactly 2^(n-d) of
+    the 2^n assignments, so sum_z f = sum_t w_t 2^(n - d_t); f(all ones) = sum_t w_t;
+    f(0) = the constant terms; and a single monomial is 1 exactly on the supersets of
+    its variable set."""
+    n = 9
+    for seed in range(4):
+        terms = random_pubo_terms(n, 25, seed)
+        F = qaoa.pubo_values(n, terms, integer=True)
+        assert F.sum() == sum(int(w) * 2 ** (n - len(t)) for w, t in terms)
+        assert F[(1 << n) - 1] == sum(int(w) for w, _ in terms)
+        assert F[0] == sum(int(w) for w, t in terms if not t)
+    F = qaoa.pubo_values(5, [(3.0, [1, 3, 4])], integer=True)
+    z = np.arange(32)
+    want = np.where(((z >> 1) & 1) & ((z >> 3) & 1) & ((z >> 4) & 1), 3, 0)
+    assert np.array_equal(F, want)
+
+
 # ------------------------------------------------------------------ states
 
 def small_instances():
