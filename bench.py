@@ -47,6 +47,8 @@ def parse():
                     help="integer weights {1..10} (int32 costs) or U(0,1) float64 weights")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
@@ -218,6 +220,74 @@ def run_reference(a):
     return 0
 
 
+# ------------------------------------------------------------------ batched vs plain
+
+BATCH_WORKLOAD = ("{g} graphs, n ~ U{{8..20}}, half random 3-regular / half G(n,0.3), integer weights {{1..5}}, "
+                  "p=3, own angles per graph: <C> + adjoint gradient of every graph")
+
+
+def measure_batched(q, dev, dtype: str, count: int, reps: int = 3):
+    """The batched workload: one persistent launch over all graphs against the plain path
+    (cost vector + gradient per graph, one graph at a time), both timed with CUDA events."""
+    import torch
+    import synth
+    p = 3
+    insts = synth.batch_instances(count, 1, p=p)
+    graphs = [q.Graph(n, e, w, True) for (n, f, e, w, g, b) in insts]
+    ang = np.stack([np.concatenate([g, b]) for (*_, g, b) in insts])
+    tiles, tune_ms = q.batch_autotune(dtype, p, 8, 20, graphs_per_n=152, device=dev)
+    q.batch_gradient(graphs, ang, dtype, tiles=tiles, device=dev)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = q.batch_gradient(graphs, ang, dtype, tiles=tiles, device=dev)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    batched_ms = statistics.median(ts)
+
+    def plain(sub):
+        res = []
+        for gph, (n, f, e, w, g, b) in sub:
+            cv = q.cost_vector(gph, "i32", device=dev)
+            psi, lam = q.new_state(n, dtype, dev), q.new_state(n, dtype, dev)
+            res.append(q.gradient(psi, lam, cv, g, b))
+        return res
+
+    pairs = list(zip(graphs, insts))
+    plain(pairs[:64])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    res = plain(pairs)
+    e1.record()
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    agree = float(np.max(np.abs(out.cpu().numpy() - torch.stack(res).cpu().numpy())))
+    return {"workload": BATCH_WORKLOAD.format(g=count), "state_dtype": dtype,
+            "graph_grads_per_s": count / (batched_ms / 1e3), "batched_ms": batched_ms, "plain_ms": plain_ms,
+            "speedup": plain_ms / batched_ms, "max_abs_diff_vs_plain": agree,
+            "tiles": {int(n): int(tiles[n]) for n in range(8, 21)}, "launches": "1 prep + 1 persistent per tile size",
+            "timing": "CUDA events, median of %d batched runs; plain: one run over all graphs" % reps}
+
+
+def measure_gradient(q, gradient_once, steps: int):
+    """Gradient evaluations per second at the main configuration (CUDA events)."""
+    import torch
+    gradient_once()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        gradient_once()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"evals_per_s": 1e3 / ms, "ms": ms}
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def run_ours(a):
@@ -260,6 +330,15 @@ def run_ours(a):
     def chk(rc, what):
         if rc != 0:
             raise q.QaoaError(rc, what)
+
+    def gradient_once():
+        desc = q.CostT()
+        gs = graph.as_struct()
+        chk(L.qaoa_cost_vector(ct.byref(gs), ct.c_void_p(C.data_ptr()), q.COST_I32 if integer else q.COST_F64,
+                               ct.byref(desc), sp), "cost")
+        chk(L.qaoa_gradient(a.n, dt_code, ct.c_void_p(psi.data_ptr()), ct.c_void_p(lam.data_ptr()), ct.byref(desc),
+                            gp, bp, a.p, ct.c_void_p(gout.data_ptr()), ct.c_void_p(ws.data_ptr()), ws_bytes, sp),
+            "gradient")
 
     def step_device():
         desc = q.CostT()
@@ -346,6 +425,10 @@ def run_ours(a):
     h2d = e.nbytes + (w.nbytes if w is not None else 0) + gam.nbytes + bet.nbytes
     d2h = 16 + shots * 16 + (2 * a.p + 2) * 8
 
+    # ---- secondary measurements (outside the timed step): gradient rate, batched vs plain
+    grad = measure_gradient(q, gradient_once, max(1, min(a.steps, 3)))
+    batched = None if a.no_batched else measure_batched(q, dev, "c128", a.batch_graphs)
+
     # ---- roofline of the dominant kernel (layer sweeps), measured live
     peak, peak_kind = measured_peak_hbm()
     sweep_ms, sweep_n, sweep_bytes = kms[0], kla[0], kby[0]
@@ -374,7 +457,11 @@ def run_ours(a):
             "e2e": {"value": e2e_value, "unit": "layers/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "clocks": clk,
+            "gradient": {"workload": f"adjoint gradient (cost vector + forward + adjoint pass), n={a.n}, p={a.p}",
+                         **grad},
         }
+        if batched is not None:
+            line["batched"] = batched
         if not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(a, e, w, integer, gam, bet)
         print(json.dumps(line), flush=True)

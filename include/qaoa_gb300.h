@@ -64,7 +64,8 @@ enum qaoa_op {
   QAOA_OP_EXPECTATION = 2,
   QAOA_OP_SAMPLE = 3,
   QAOA_OP_GRADIENT = 4,
-  QAOA_OP_OPTIMIZE = 5
+  QAOA_OP_OPTIMIZE = 5,
+  QAOA_OP_LBFGS = 6
 };
 
 /*
@@ -117,6 +118,27 @@ const char* qaoa_strerror(int status);
  * bounds on C(z) (sum of negative / positive weights) for integer graphs.
  */
 int qaoa_graph_check(const qaoa_graph_t* g, int64_t* cmin, int64_t* cmax);
+
+/*
+ * Cost vector of a general polynomial objective in 0-1 variables (Eq. 3):
+ *   C(z) = sum_t w_t prod_{i in T_t} z_i,
+ * term t given by the bit mask masks[t] of its variables T_t (bit i = variable
+ * i = qubit i; mask 0 is a constant term).  MaxCut is the special case with
+ * terms {u}: w, {v}: w, {u, v}: -2w per edge.  Host arrays masks[nterms],
+ * w[nterms]; nterms <= QAOA_MAX_PUBO_TERMS.  weight_kind QAOA_WEIGHT_INT
+ * (integral weights, sum |w| < 2^31): exact, int32 or float64 costs;
+ * QAOA_WEIGHT_F64: float64 costs from weights quantised to one common fixed
+ * point and summed exactly (one rounding per 2048 terms).  Fills *desc as
+ * qaoa_cost_vector does (integer bounds = sums of the negative / positive
+ * weights).  Errors: QAOA_ERR_INVALID_ARG for a variable outside [0, n), a
+ * non-finite or (INT) non-integral weight, or I32 costs with float weights.
+ * Every downstream call (layers, expectation, sampling, gradients) takes the
+ * result like a MaxCut cost vector.
+ */
+#define QAOA_MAX_PUBO_TERMS (1 << 24)
+int qaoa_cost_vector_pubo(int n, int64_t nterms, const uint32_t* masks, const double* w,
+                          int weight_kind, void* C_dev, int cost_dtype, qaoa_cost_t* desc,
+                          void* stream);
 
 /*
  * Bytes of device scratch the call `op` (enum qaoa_op) needs for n qubits,
@@ -260,6 +282,31 @@ int qaoa_optimize_adam(int n, int dtype, void* psi_dev, void* lambda_dev, const 
                        double* angles_dev, int p, int64_t steps, double lr, double beta1,
                        double beta2, double eps, double* history_dev, void* ws_dev,
                        size_t ws_bytes, void* stream);
+
+/*
+ * L-BFGS ascent on E = <C> over the angles, entirely on the device (the paper
+ * optimises the angles with L-BFGS on the adjoint gradient, Sec. V-B).  Each
+ * evaluation runs qaoa_gradient_dev at angles_dev and then one step of an
+ * L-BFGS state machine on the device: Armijo backtracking (c1 = 1e-4) with
+ * safeguarded quadratic interpolation; accepted steps store (s, y) when
+ * s.y > 0 (at most m <= QAOA_LBFGS_MAX_M pairs) and take the two-loop
+ * direction with H0 = s.y / y.y (the first step: -g / max(1, |g|)).  The run
+ * ends after max_evals evaluations, when |dE/dangles|_inf < gtol (converged)
+ * or when the step falls below 1e-12 (no progress).  As for Adam, the first
+ * evaluation runs directly and the rest replay a CUDA graph; the host reads a
+ * device flag every 16 evaluations to stop early.
+ * history_dev (optional): max_evals x (4p + 2) doubles, one row per evaluation
+ * (accepted or not) = [E, <psi|psi>, dE/dgamma, dE/dbeta, gamma, beta].
+ * info_dev (optional): 4 doubles [E at the final angles, accepted steps,
+ * evaluations, status 0 = evaluations used up, 1 = converged, 2 = no progress].
+ * On return angles_dev holds the best accepted angles.  Workspace:
+ * qaoa_workspace_size(..., QAOA_OP_LBFGS, p, ...).  Synchronises `stream`.
+ */
+#define QAOA_LBFGS_MAX_M 16
+int qaoa_optimize_lbfgs(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,
+                        double* angles_dev, int p, int64_t max_evals, int m, double gtol,
+                        double* history_dev, double* info_dev, void* ws_dev, size_t ws_bytes,
+                        void* stream);
 
 /* As qaoa_gradient, then synchronise and copy the 2p+2 doubles to out_host. */
 int qaoa_gradient_host(int n, int dtype, void* psi_dev, void* lambda_dev,

@@ -26,7 +26,8 @@ QAOA_OK, QAOA_ERR_INVALID_ARG, QAOA_ERR_UNSUPPORTED, QAOA_ERR_CUDA, QAOA_ERR_TIM
 C128, C64 = 0, 1
 COST_I32, COST_F64 = 0, 1
 WEIGHT_INT, WEIGHT_F64 = 0, 1
-OP_COST, OP_LAYERS, OP_EXPECTATION, OP_SAMPLE, OP_GRADIENT, OP_OPTIMIZE = range(6)
+OP_COST, OP_LAYERS, OP_EXPECTATION, OP_SAMPLE, OP_GRADIENT, OP_OPTIMIZE, OP_LBFGS = range(7)
+LBFGS_MAX_M = 16
 MAX_N, MAX_P, MAX_TABLE_SPAN = 32, 64, 16384
 BATCH_MAX_N, BATCH_MAX_P, BATCH_MAX_EDGES = 26, 12, 512
 
@@ -36,6 +37,7 @@ EXPORTS = [
     "qaoa_gradient", "qaoa_gradient_host", "qaoa_launch_count", "qaoa_launch_count_reset",
     "qaoa_timing_enable", "qaoa_timing_read", "qaoa_gradient_dev", "qaoa_optimize_adam", "qaoa_expectation_noalloc",
     "qaoa_batch_workspace_size", "qaoa_batch_gradient", "qaoa_batch_autotune_workspace_size", "qaoa_batch_autotune",
+    "qaoa_cost_vector_pubo", "qaoa_optimize_lbfgs",
 ]
 
 
@@ -76,6 +78,9 @@ def _load() -> ct.CDLL:
         "qaoa_gradient_dev": ([i32, i32, vp, vp, ct.POINTER(CostT), vp, i32, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_optimize_adam": ([i32, i32, vp, vp, ct.POINTER(CostT), vp, i32, i64, ct.c_double, ct.c_double,
                                 ct.c_double, ct.c_double, vp, vp, ct.c_size_t, vp], i32),
+        "qaoa_optimize_lbfgs": ([i32, i32, vp, vp, ct.POINTER(CostT), vp, i32, i64, i32, ct.c_double, vp, vp, vp,
+                                 ct.c_size_t, vp], i32),
+        "qaoa_cost_vector_pubo": ([i32, i64, vp, dp, i32, vp, i32, ct.POINTER(CostT), vp], i32),
         "qaoa_batch_workspace_size": ([i32, i32, i32, ct.POINTER(GraphT), vp, szp], i32),
         "qaoa_batch_gradient": ([i32, i32, ct.POINTER(GraphT), dp, i32, vp, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_batch_autotune_workspace_size": ([i32, i32, i32, i32, szp], i32),
@@ -225,6 +230,25 @@ def _angles(gammas, betas):
     if len(g) != len(b):
         raise ValueError("gammas and betas must have the same length")
     return g, b, g.ctypes.data_as(ct.POINTER(ct.c_double)), b.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+def cost_vector_pubo(n: int, masks, weights, integer: bool = True, dtype: str = "i32", device="cuda",
+                     out=None) -> CostVector:
+    """General PUBO cost (Eq. 3) on the device: C(z) = sum_t w_t [z & masks[t] == masks[t]]."""
+    torch = _torch()
+    m = np.ascontiguousarray(np.asarray(masks, dtype=np.uint32).reshape(-1))
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(-1))
+    if len(m) != len(w):
+        raise ValueError("masks and weights must have the same length")
+    tdt = torch.int32 if dtype == "i32" else torch.float64
+    C = out if out is not None else torch.empty(1 << n, dtype=tdt, device=device)
+    _require_cuda(C)
+    desc = CostT()
+    _check(_lib.qaoa_cost_vector_pubo(n, len(m), ct.c_void_p(m.ctypes.data), w.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                      WEIGHT_INT if integer else WEIGHT_F64, ct.c_void_p(C.data_ptr()),
+                                      COST_I32 if tdt == torch.int32 else COST_F64, ct.byref(desc),
+                                      ct.c_void_p(_stream(C.device))), "cost_vector_pubo")
+    return CostVector(C, n, desc.cmin, desc.cmax)
 
 
 def new_state(n: int, dtype: str = "c128", device="cuda"):
@@ -419,6 +443,33 @@ def batch_autotune(dtype: str = "c128", p: int = 3, n_lo: int = 8, n_hi: int = 2
                                     ms.ctypes.data_as(ct.POINTER(ct.c_double)), ct.c_void_p(ws.data_ptr()),
                                     ws.numel(), ct.c_void_p(_stream(device))), "batch_autotune")
     return tiles, ms.reshape(MAX_N + 1, 2)
+
+
+def optimize_lbfgs(cost: CostVector, angles, max_evals: int = 200, m: int = 10, gtol: float = 1e-6,
+                   dtype: str = "c128"):
+    """L-BFGS ascent on <C>, on the device (graph replay; the host polls a stop flag every 16
+    evaluations).  angles: float64 CUDA tensor [gamma, beta], updated in place to the best
+    accepted point.  Returns (history (evals x (4p + 2)) device tensor, info dict)."""
+    torch = _torch()
+    _require_cuda(angles)
+    p = angles.numel() // 2
+    n = cost.n
+    dt = C128 if dtype == "c128" else C64
+    psi = new_state(n, dtype, angles.device)
+    lam = new_state(n, dtype, angles.device)
+    ws = _workspace(workspace_size(n, dt, OP_LBFGS, p, 0, cost.span), angles.device)
+    hist = torch.zeros((max(max_evals, 1), 4 * p + 2), dtype=torch.float64, device=angles.device)
+    info = torch.zeros(4, dtype=torch.float64, device=angles.device)
+    cs = cost.struct()
+    _check(_lib.qaoa_optimize_lbfgs(n, dt, ct.c_void_p(psi.data_ptr()), ct.c_void_p(lam.data_ptr()), ct.byref(cs),
+                                    ct.c_void_p(angles.data_ptr()), p, max_evals, m, gtol,
+                                    ct.c_void_p(hist.data_ptr()), ct.c_void_p(info.data_ptr()),
+                                    ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(_stream(angles.device))),
+           "optimize_lbfgs")
+    i = info.cpu().numpy()
+    res = {"E": float(i[0]), "iterations": int(i[1]), "evaluations": int(i[2]),
+           "status": ("evaluations used up", "converged", "no progress")[int(i[3])]}
+    return hist[:res["evaluations"]], res
 
 
 def launch_count() -> int:

@@ -132,6 +132,10 @@ static size_t fx_table_bytes(int dtype, int p) {
 static size_t adam_extra_bytes(int p) {
   return round256((4 * p + 1) * sizeof(double)) + round256((2 * p + 2) * sizeof(double));
 }
+// L-BFGS state (history of QAOA_LBFGS_MAX_M pairs) and the gradient output
+static size_t lbfgs_extra_bytes(int p) {
+  return round256(lbfgs_state_doubles(p, QAOA_LBFGS_MAX_M) * sizeof(double)) + round256((2 * p + 2) * sizeof(double));
+}
 static size_t layer_ws_bytes(int dtype, int p, int64_t span, int nout) {
   return kScalarBytes + kNormPartialBytes + kTrigBytes + partial_bytes(nout) + phase_table_bytes(dtype, p, span) +
          fx_table_bytes(dtype, p);
@@ -422,6 +426,57 @@ static bool angles_ok(const double* g, const double* b, int p) {
 
 using namespace qaoa;
 
+// Run `steps` iterations of a fixed launch sequence on the caller's stream: the first one
+// directly (it also settles every per-kernel setting), the rest by replaying a CUDA graph of
+// one iteration, with no host round trip inside.  When done_flag is set, the host reads that
+// device double every `poll` replays and stops once it is non-zero.  The legacy default
+// stream cannot be captured: then the graph runs on a private blocking stream, which is
+// ordered after (and before) work on the legacy stream.  Synchronises before returning.
+template <class F>
+static int replay_steps(cudaStream_t s, int64_t steps, F&& iteration, const double* done_flag, int poll) {
+  if (steps <= 0) return QAOA_OK;
+  int rc = iteration(s);
+  if (rc) return rc;
+  if (steps == 1) return cuda_status(cudaStreamSynchronize(s));
+  cudaStream_t cur = s;
+  bool own = false;
+  if (s == nullptr) {
+    if (cudaStreamCreate(&cur) != cudaSuccess) return QAOA_ERR_CUDA;
+    own = true;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int out = QAOA_OK;
+  if (cudaStreamBeginCapture(cur, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    out = QAOA_ERR_CUDA;
+  } else {
+    const int rc_cap = iteration(cur);
+    const cudaError_t ec = cudaStreamEndCapture(cur, &graph);
+    if (rc_cap != QAOA_OK || ec != cudaSuccess) out = rc_cap != QAOA_OK ? rc_cap : QAOA_ERR_CUDA;
+    else if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) out = QAOA_ERR_CUDA;
+  }
+  int64_t k = 1;
+  while (out == QAOA_OK && k < steps) {
+    const int64_t chunk = done_flag ? std::min<int64_t>(poll, steps - k) : steps - k;
+    for (int64_t j = 0; j < chunk && out == QAOA_OK; ++j)
+      if (cudaGraphLaunch(exec, cur) != cudaSuccess) out = QAOA_ERR_CUDA;
+    k += chunk;
+    if (done_flag && out == QAOA_OK && k < steps) {
+      double flag = 0.0;
+      if (cudaMemcpyAsync(&flag, done_flag, sizeof(double), cudaMemcpyDeviceToHost, cur) != cudaSuccess ||
+          cudaStreamSynchronize(cur) != cudaSuccess)
+        out = QAOA_ERR_CUDA;
+      else if (flag != 0.0)
+        break;
+    }
+  }
+  if (cudaStreamSynchronize(cur) != cudaSuccess && out == QAOA_OK) out = QAOA_ERR_CUDA;
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (own) cudaStreamDestroy(cur);
+  return out;
+}
+
 extern "C" {
 
 int qaoa_version(void) { return 100; }
@@ -476,6 +531,7 @@ int qaoa_workspace_size(int n, int dtype, int op, int p, int64_t shots, int64_t 
     case QAOA_OP_SAMPLE: b = round256(sample_ws_bytes(n, dtype)); break;
     case QAOA_OP_GRADIENT: b = layer_ws_bytes(dtype, p, cost_span, 2 * p + 2); break;
     case QAOA_OP_OPTIMIZE: b = layer_ws_bytes(dtype, p, cost_span, 2 * p + 2) + adam_extra_bytes(p); break;
+    case QAOA_OP_LBFGS: b = layer_ws_bytes(dtype, p, cost_span, 2 * p + 2) + lbfgs_extra_bytes(p); break;
     default: return QAOA_ERR_INVALID_ARG;
   }
   *bytes = b;
@@ -517,6 +573,62 @@ int qaoa_cost_vector(const qaoa_graph_t* g, void* C_dev, int cost_dtype, qaoa_co
     desc->dtype = cost_dtype;
     desc->cmin = a.integer ? cmin : 1;
     desc->cmax = a.integer ? cmax : 0;
+  }
+  return QAOA_OK;
+}
+
+int qaoa_cost_vector_pubo(int n, int64_t nterms, const uint32_t* masks, const double* w, int weight_kind,
+                          void* C_dev, int cost_dtype, qaoa_cost_t* desc, void* stream) {
+  if (n < 1 || n > QAOA_MAX_N || nterms < 0 || nterms > QAOA_MAX_PUBO_TERMS || C_dev == nullptr)
+    return QAOA_ERR_INVALID_ARG;
+  if (nterms > 0 && (masks == nullptr || w == nullptr)) return QAOA_ERR_INVALID_ARG;
+  if (weight_kind != QAOA_WEIGHT_INT && weight_kind != QAOA_WEIGHT_F64) return QAOA_ERR_INVALID_ARG;
+  if (cost_dtype != QAOA_COST_I32 && cost_dtype != QAOA_COST_F64) return QAOA_ERR_INVALID_ARG;
+  if (cost_dtype == QAOA_COST_I32 && weight_kind != QAOA_WEIGHT_INT) return QAOA_ERR_INVALID_ARG;
+  const bool integer = weight_kind == QAOA_WEIGHT_INT;
+  double sum_abs = 0.0;
+  int64_t neg = 0, pos = 0;
+  for (int64_t t = 0; t < nterms; ++t) {
+    if (n < 32 && (masks[t] >> n) != 0) return QAOA_ERR_INVALID_ARG;  // a variable outside [0, n)
+    if (!std::isfinite(w[t])) return QAOA_ERR_INVALID_ARG;
+    if (integer && (w[t] != std::floor(w[t]) || std::fabs(w[t]) >= 2147483648.0)) return QAOA_ERR_INVALID_ARG;
+    sum_abs += std::fabs(w[t]);
+    if (integer) (w[t] < 0 ? neg : pos) += (int64_t)w[t];
+  }
+  if (integer && sum_abs >= 2147483648.0) return QAOA_ERR_INVALID_ARG;
+  if (!integer && !(sum_abs < 1e300)) return QAOA_ERR_INVALID_ARG;
+  int fixed_shift = 0;
+  if (!integer) {
+    int e2 = 0;
+    std::frexp(sum_abs + 1.0, &e2);  // every partial sum stays below 2^62
+    fixed_shift = 62 - e2;
+  }
+  PuboArgs* a = new PuboArgs;
+  int64_t t = 0;
+  int rc = QAOA_OK;
+  do {
+    std::memset(a, 0, sizeof(PuboArgs));
+    a->n = n;
+    a->accumulate = t > 0;
+    a->cost_dtype = cost_dtype;
+    a->integer = integer;
+    a->fixed_shift = fixed_shift;
+    a->C = C_dev;
+    a->nterms = (int)std::min<int64_t>(kPuboChunk, nterms - t);
+    for (int k = 0; k < a->nterms; ++k) {
+      a->mask[k] = masks[t + k];
+      a->q[k] = integer ? (long long)w[t + k] : (long long)std::llrint(std::ldexp(w[t + k], fixed_shift));
+    }
+    rc = cuda_status(launch_pubo(*a, (cudaStream_t)stream));
+    t += a->nterms;
+  } while (rc == QAOA_OK && t < nterms);
+  delete a;
+  if (rc) return rc;
+  if (desc) {
+    desc->C_dev = C_dev;
+    desc->dtype = cost_dtype;
+    desc->cmin = integer ? neg : 1;
+    desc->cmax = integer ? pos : 0;
   }
   return QAOA_OK;
 }
@@ -716,47 +828,42 @@ int qaoa_optimize_adam(int n, int dtype, void* psi_dev, void* lambda_dev, const 
   double* gout = (double*)(extra + round256((4 * p + 1) * sizeof(double)));
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(state, 0, (4 * p + 1) * sizeof(double), s) != cudaSuccess) return QAOA_ERR_CUDA;
-  if (steps == 0) return QAOA_OK;
-  cudaStream_t cur = s;
-  auto iteration = [&]() {
+  return replay_steps(s, steps, [&](cudaStream_t cur) {
     int r = gradient_impl(n, dtype, psi_dev, lambda_dev, cost, nullptr, nullptr, angles_dev, p, gout, ws_dev, gbytes,
                           (void*)cur);
     if (r) return r;
     return cuda_status(launch_adam(angles_dev, gout, state, counter, p, lr, beta1, beta2, eps, history_dev, steps, cur));
-  };
-  // first step directly (it also settles every per-kernel setting), the rest from a CUDA
-  // graph of one step replayed on the stream: no host round trip inside the loop
-  rc = iteration();
+  }, nullptr, 0);
+}
+
+int qaoa_optimize_lbfgs(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,
+                        double* angles_dev, int p, int64_t max_evals, int m, double gtol, double* history_dev,
+                        double* info_dev, void* ws_dev, size_t ws_bytes, void* stream) {
+  if (angles_dev == nullptr || max_evals < 0 || m < 1 || m > QAOA_LBFGS_MAX_M || !(gtol >= 0.0) || p < 1 ||
+      p > QAOA_MAX_P || !valid_cost(cost))
+    return QAOA_ERR_INVALID_ARG;
+  size_t need = 0;
+  const int64_t span = (cost->dtype == QAOA_COST_I32 && cost->cmax >= cost->cmin) ? cost->cmax - cost->cmin + 1 : 0;
+  int rc = qaoa_workspace_size(n, dtype, QAOA_OP_LBFGS, p, 0, span, &need);
   if (rc) return rc;
-  if (steps == 1) return cuda_status(cudaStreamSynchronize(s));
-  // the legacy default stream cannot be captured: capture on a private blocking stream,
-  // which is ordered after (and before) work on the legacy stream
-  bool own = false;
-  if (s == nullptr) {
-    if (cudaStreamCreate(&cur) != cudaSuccess) return QAOA_ERR_CUDA;
-    own = true;
-  }
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  int out = QAOA_OK;
-  if (cudaStreamBeginCapture(cur, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-    out = QAOA_ERR_CUDA;
-  } else {
-    const int rc_cap = iteration();
-    const cudaError_t ec = cudaStreamEndCapture(cur, &graph);
-    if (rc_cap != QAOA_OK || ec != cudaSuccess) out = rc_cap != QAOA_OK ? rc_cap : QAOA_ERR_CUDA;
-    else if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) out = QAOA_ERR_CUDA;
-  }
-  if (out == QAOA_OK) {
-    cudaError_t e = cudaSuccess;
-    for (int64_t k = 1; k < steps && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, cur);
-    if (e != cudaSuccess) out = QAOA_ERR_CUDA;
-  }
-  if (cudaStreamSynchronize(cur) != cudaSuccess && out == QAOA_OK) out = QAOA_ERR_CUDA;
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
-  if (own) cudaStreamDestroy(cur);
-  return out;
+  if (ws_dev == nullptr || ws_bytes < need) return QAOA_ERR_WORKSPACE;
+  const size_t gbytes = need - lbfgs_extra_bytes(p);
+  char* extra = (char*)ws_dev + gbytes;
+  double* state = (double*)extra;
+  double* gout = (double*)(extra + round256(lbfgs_state_doubles(p, QAOA_LBFGS_MAX_M) * sizeof(double)));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(state, 0, lbfgs_state_doubles(p, QAOA_LBFGS_MAX_M) * sizeof(double), s) != cudaSuccess)
+    return QAOA_ERR_CUDA;
+  rc = replay_steps(s, max_evals, [&](cudaStream_t cur) {
+    int r = gradient_impl(n, dtype, psi_dev, lambda_dev, cost, nullptr, nullptr, angles_dev, p, gout, ws_dev, gbytes,
+                          (void*)cur);
+    if (r) return r;
+    return cuda_status(launch_lbfgs(angles_dev, gout, state, p, m, gtol, 1e-4, history_dev, max_evals, cur));
+  }, state + 7, 16);
+  if (rc) return rc;
+  rc = cuda_status(launch_lbfgs_finish(angles_dev, state, p, info_dev, s));
+  if (rc) return rc;
+  return cuda_status(cudaStreamSynchronize(s));
 }
 
 int qaoa_gradient_host(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,

@@ -122,6 +122,10 @@ cudaError_t launch_norm(const void* psi, int dtype, int n, double* partials, int
 cudaError_t launch_angle_prep(const double* ang, int p, double* trig, cudaStream_t s);
 cudaError_t launch_adam(double* ang, const double* g, double* state, long long* step, int p, double lr, double b1,
                         double b2, double eps, double* history, long long max_steps, cudaStream_t s);
+size_t lbfgs_state_doubles(int p, int m);
+cudaError_t launch_lbfgs(double* ang, const double* gout, double* st, int p, int m, double gtol, double c1,
+                         double* history, long long max_rows, cudaStream_t s);
+cudaError_t launch_lbfgs_finish(double* ang, const double* st, int p, double* info, cudaStream_t s);
 cudaError_t launch_expect(int dtype, const void* psi, const void* C, int cost_dtype, int n, double* partials,
                           int grid, cudaStream_t s);
 int sweep_tile_bits(int dtype, bool two);     // B of the kernel a sweep uses
@@ -140,6 +144,21 @@ struct CostArgs {
   int64_t wi[QAOA_MAX_N][QAOA_MAX_N];  // symmetric adjacency weights (integer or fixed point)
 };
 cudaError_t launch_cost(const CostArgs& a, cudaStream_t s);
+
+// general PUBO cost, one chunk of terms per launch (parameters stay below 32 KB)
+constexpr int kPuboChunk = 2048;
+struct PuboArgs {
+  int n;
+  int nterms;       // terms in this chunk
+  int accumulate;   // add to C (later chunks) instead of overwriting it
+  int cost_dtype;
+  int integer;      // integer weights (q = w) or fixed point (q = w 2^fixed_shift)
+  int fixed_shift;
+  void* C;
+  uint32_t mask[kPuboChunk];
+  long long q[kPuboChunk];
+};
+cudaError_t launch_pubo(const PuboArgs& a, cudaStream_t s);
 
 // sampling
 struct SampleArgs {

@@ -170,3 +170,28 @@ def test_batch_gradient_checks_arguments_before_gpu_work():
     size = ct.c_size_t()
     assert q.lib.qaoa_batch_autotune_workspace_size(q.C128, 3, 12, 4, ct.byref(size)) == 0 and size.value > 0
     assert q.lib.qaoa_batch_autotune_workspace_size(q.C128, 3, q.BATCH_MAX_N + 1, 4, ct.byref(size)) != 0
+
+
+# ---------------------------------------------------------------- general PUBO cost
+
+@pytest.mark.parametrize("case", ["var_outside", "nan", "non_integral", "i32_float", "no_masks", "n_zero"])
+def test_pubo_rejections(case):
+    n, masks, w, kind, cdt = 4, [0b0011, 0b1000], [1.0, -2.0], q.WEIGHT_INT, q.COST_I32
+    if case == "var_outside":
+        masks = [0b10000]
+    elif case == "nan":
+        w, kind, cdt = [float("nan"), 1.0], q.WEIGHT_F64, q.COST_F64
+    elif case == "non_integral":
+        w = [0.5, 1.0]
+    elif case == "i32_float":
+        kind = q.WEIGHT_F64
+    elif case == "n_zero":
+        n = 0
+    m = np.ascontiguousarray(np.asarray(masks, dtype=np.uint32))
+    wa = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    mp = None if case == "no_masks" else ct.c_void_p(m.ctypes.data)
+    desc = q.CostT()
+    # a placeholder device pointer: every case is refused on the host before any launch
+    rc = q.lib.qaoa_cost_vector_pubo(n, len(m), mp, wa.ctypes.data_as(ct.POINTER(ct.c_double)), kind,
+                                     ct.c_void_p(256), cdt, ct.byref(desc), None)
+    assert rc == q.QAOA_ERR_INVALID_ARG

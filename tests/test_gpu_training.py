@@ -137,3 +137,107 @@ def test_adam_200_steps_improves_cut_n20():
     assert abs(hist[-1, 1] - 1.0) < 1e-10
     # first step launched directly, the other 199 replay one captured graph
     assert q.launch_count() - launches0 < 200
+
+
+def lbfgs_reference(n, C, ang0, max_evals, m, gtol, c1=1e-4):
+    """The same L-BFGS rules on the CPU, driven by the oracle's adjoint gradient (minimising
+    f = -E): Armijo backtracking with the safeguarded quadratic step, two-loop direction
+    with H0 = s.y / y.y, restart on a non-descent direction.  Returns (rows, x_best, status)."""
+    p = len(ang0) // 2
+    pt = np.array(ang0, dtype=np.float64)
+    x = g = d = None
+    fk = alpha = gtd = 0.0
+    S, Y, rho = [], [], []
+    rows = []
+    for ev in range(max_evals):
+        E, dg, db, _ = qaoa.adjoint_gradient(n, C, pt[:p], pt[p:])
+        grad = np.concatenate([dg, db])
+        rows.append(np.concatenate([[E, 1.0], grad, pt]))
+        ft, gt = -E, -grad
+        if ev == 0 or ft <= fk + c1 * alpha * gtd:
+            if ev > 0:
+                s, yv = pt - x, gt - g
+                sy = s @ yv
+                if sy > 1e-12 * np.sqrt((s @ s) * (yv @ yv)) and sy > 0:
+                    S.append(s), Y.append(yv), rho.append(1.0 / sy)
+                    if len(S) > m:
+                        S.pop(0), Y.pop(0), rho.pop(0)
+            x, g, fk = pt.copy(), gt.copy(), ft
+            if np.max(np.abs(g)) < gtol:
+                return rows, x, "converged"
+            q = g.copy()
+            al = [0.0] * len(S)
+            for k in range(len(S) - 1, -1, -1):
+                al[k] = rho[k] * (S[k] @ q)
+                q -= al[k] * Y[k]
+            h0 = (1.0 / (rho[-1] * (Y[-1] @ Y[-1]))) if S else 1.0 / max(1.0, np.linalg.norm(g))
+            r = h0 * q
+            for k in range(len(S)):
+                b = rho[k] * (Y[k] @ r)
+                r += S[k] * (al[k] - b)
+            d = -r
+            gtd = g @ d
+            if not gtd < 0:
+                S, Y, rho = [], [], []
+                d = -g / max(1.0, np.linalg.norm(g))
+                gtd = g @ d
+            alpha = 1.0
+        else:
+            den = 2.0 * (ft - fk - gtd * alpha)
+            a = -gtd * alpha * alpha / den if den > 0 else 0.5 * alpha
+            alpha = min(max(a, 0.1 * alpha), 0.5 * alpha)
+            if alpha < 1e-12:
+                return rows, x, "no progress"
+        pt = x + alpha * d
+    return rows, x, "evaluations used up"
+
+
+def test_lbfgs_matches_oracle_driven_lbfgs():
+    n, p = 8, 2
+    g, e, w, integer = instance(n, 6, prob=0.5)
+    cv = q.cost_vector(g, "f64")
+    C = qaoa.cut_values(n, e, w, integer=False)
+    gam, bet = synth.angles(p, 5)
+    ang0 = np.concatenate([gam, bet])
+    ang = torch.tensor(ang0, device="cuda")
+    hist, info = q.optimize_lbfgs(cv, ang, max_evals=40, m=5, gtol=1e-7)
+    rows, xbest, status = lbfgs_reference(n, C, ang0, 40, 5, 1e-7)
+    rows = np.array(rows)
+    hist = hist.cpu().numpy()
+    s = scale_of(w)
+    k = min(len(rows), len(hist), 25)  # the first evaluations, before rounding can flip a decision
+    assert np.max(np.abs(hist[:k, 0] - rows[:k, 0])) <= 1e-9 * s
+    assert np.max(np.abs(hist[:k, 2 + 2 * p:] - rows[:k, 2 + 2 * p:])) <= 1e-8
+    if info["status"] == status == "converged":
+        assert np.max(np.abs(ang.cpu().numpy() - xbest)) <= 1e-6
+
+
+def test_lbfgs_converges_to_a_stationary_point():
+    n, p = 12, 3
+    g, e, w, integer = instance(n, 3, prob=0.4)
+    cv = q.cost_vector(g, "f64")
+    C = qaoa.cut_values(n, e, w, integer=False)
+    ang = torch.tensor(np.concatenate(synth.angles(p, 8)), device="cuda")
+    E0 = qaoa.adjoint_gradient(n, C, *np.split(ang.cpu().numpy(), 2))[0]
+    hist, info = q.optimize_lbfgs(cv, ang, max_evals=300, m=10, gtol=1e-6)
+    assert info["status"] == "converged", info
+    a = ang.cpu().numpy()
+    E, dg, db, _ = qaoa.adjoint_gradient(n, C, a[:p], a[p:])
+    assert E >= E0 and abs(E - info["E"]) <= 1e-10 * scale_of(w)
+    assert np.max(np.abs(np.concatenate([dg, db]))) <= 1e-5
+
+
+def test_lbfgs_200_evaluations_n24_p10():
+    """The adjoint-gradient workload's optimisation loop: G(24, 0.2), U(0,1), p = 10, up to 200
+    evaluations on the device; accepted values never decrease and E rises."""
+    n, p = 24, 10
+    g, e, w, integer = instance(n, 1, prob=0.2)
+    cv = q.cost_vector(g, "f64")
+    ang = torch.tensor(np.concatenate(q.linear_ramp(p)), device="cuda") * 0.4
+    launches0 = q.launch_count()
+    hist, info = q.optimize_lbfgs(cv, ang, max_evals=200, m=10, gtol=1e-7)
+    h = hist.cpu().numpy()
+    assert len(h) == info["evaluations"] >= 2
+    assert info["E"] > h[0, 0]
+    assert np.all(np.abs(h[:, 1] - 1.0) <= 1e-10)
+    assert q.launch_count() - launches0 < 60  # one direct evaluation, then graph replays
