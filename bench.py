@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--workload", default="layers", choices=["layers", "batched"],
+                    help="layers: the n-qubit step (default); batched: only the batched-gradient workload")
     a = ap.parse_args()
     if a.warmup < 3:
         a.warmup = 3
@@ -450,6 +452,7 @@ def run_ours(a):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "layer sweep", "launches": sweep_n,
+                         "algorithmic_bytes_per_launch": sweep_bytes / max(1, sweep_n),
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "kernels_ms": {"sweep": kms[0], "cost": kms[1], "sample": kms[2], "other": kms[3]},
             "kernels_launches": {"sweep": kla[0], "cost": kla[1], "sample": kla[2], "other": kla[3]},
@@ -470,10 +473,29 @@ def run_ours(a):
     return 0
 
 
+def run_batched(a):
+    """The batched workload alone: one JSON line, graph gradients per second."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_2407_13012_gb300 as q
+    dev = torch.device("cuda", local)
+    res = measure_batched(q, dev, a.dtype, a.batch_graphs, reps=a.steps)
+    if rank == 0:
+        print(json.dumps({"metric": "batched adjoint gradients (graph gradients/s)", "value": res["graph_grads_per_s"],
+                          "unit": "graph gradients/s", "n_gpus": 1, "steps": a.steps, "warmup": 1,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f64" if a.dtype == "c128" else "f32", "data": "synthetic",
+                          "config": {"workload": res["workload"]}, "batched": res}), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "batched":
+        return run_batched(a)
     return run_ours(a)
 
 

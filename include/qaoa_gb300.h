@@ -315,6 +315,29 @@ int qaoa_gradient_host(int n, int dtype, void* psi_dev, void* lambda_dev,
                        void* stream);
 
 /*
+ * Learned angle proposer: fused inference of a message-passing network that
+ * maps each graph to 2p starting angles [gamma_1..p | beta_1..p] for the
+ * optimisers above (the paper starts them from fixed schedules, Sec. II-A; the
+ * network and its training are this library's addition).  With A the weighted
+ * adjacency, d_v the degree and s_v = sum_u A_vu (float32 throughout):
+ *   h_v = relu([d_v / 4, s_v / 2] W_in + b_in);
+ *   QAOA_PROPOSER_LAYERS times: h_v = relu(h_v W_s + ((sum_u A_vu h_u) / max(1, d_v)) W_m + b);
+ *   angles = relu([mean_v h_v, max_v h_v] W_1 + b_1) W_2 + b_2.
+ * params_dev: qaoa_proposer_param_count(p) floats (device), row-major
+ * (in x out) matrices in the order W_in (2 x H), b_in, (W_s, W_m (H x H), b) per
+ * layer, W_1 (2H x H), b_1, W_2 (H x 2p), b_2, with H = QAOA_PROPOSER_HIDDEN.
+ * graphs: host, n <= 32, any weights (checked as by qaoa_graph_check).
+ * angles_dev: ngraphs x 2p doubles.  One CTA per graph, one launch; the graph
+ * arrays are copied to ws_dev (qaoa_propose_workspace_size bytes) on `stream`.
+ */
+#define QAOA_PROPOSER_HIDDEN 64
+#define QAOA_PROPOSER_LAYERS 3
+int64_t qaoa_proposer_param_count(int p);
+int qaoa_propose_workspace_size(int ngraphs, const qaoa_graph_t* graphs, size_t* bytes);
+int qaoa_propose_angles(int ngraphs, const qaoa_graph_t* graphs, int p, const float* params_dev,
+                        double* angles_dev, void* ws_dev, size_t ws_bytes, void* stream);
+
+/*
  * Launch accounting (for benchmarks): number of kernels this library has
  * launched in this process since the last reset.  Host-only.
  */
@@ -339,12 +362,14 @@ int qaoa_timing_read(double* ms, int64_t* launches, double* bytes, int64_t* drop
  * Batched adjoint gradients of many small graphs (the batched workload: thousands
  * of graphs of uneven n, each with its own angles).  Each graph gets exactly
  * what qaoa_gradient computes from |+>: [E, <psi|psi>, dE/dgamma_1..p,
- * dE/dbeta_1..p] (Eq. 1, Sec. IV-D), here for integer-weight graphs only.
+ * dE/dbeta_1..p] (Eq. 1, Sec. IV-D).  Integer weights give int32 costs and
+ * phase tables; if any graph has float weights, every graph gets float64 costs
+ * (weights summed in edge order) and directly computed phases.
  * All graphs run in one persistent launch per tile size: each CTA takes the
  * next graph (largest n first) and runs its whole plan, so there is one launch
  * for the batch instead of ~2p(k-1)+3 per graph.  The paper evaluates graphs
  * one at a time; batching is this library's addition.
- *  graphs      ngraphs host descriptors (QAOA_WEIGHT_INT, n <= QAOA_BATCH_MAX_N,
+ *  graphs      ngraphs host descriptors (n <= QAOA_BATCH_MAX_N,
  *              m <= QAOA_BATCH_MAX_EDGES); checked as by qaoa_graph_check.
  *  angles      host, ngraphs x 2p doubles: row i = [gamma_1..p | beta_1..p]
  *              of graph i.  1 <= p <= QAOA_BATCH_MAX_P.
@@ -355,7 +380,7 @@ int qaoa_timing_read(double* ms, int64_t* launches, double* bytes, int64_t* drop
  *  ws_dev      at least qaoa_batch_workspace_size() bytes (256-byte aligned);
  *              it holds every graph's cost vector, state and lambda buffers.
  * Errors: QAOA_ERR_INVALID_ARG (a bad graph, angle or pointer),
- * QAOA_ERR_UNSUPPORTED (float weights, or a graph past the limits),
+ * QAOA_ERR_UNSUPPORTED (a graph past the limits),
  * QAOA_ERR_WORKSPACE.  The graph and angle arrays are read before the call
  * returns; the copy of them to the workspace is enqueued on `stream`.
  */

@@ -37,7 +37,8 @@ EXPORTS = [
     "qaoa_gradient", "qaoa_gradient_host", "qaoa_launch_count", "qaoa_launch_count_reset",
     "qaoa_timing_enable", "qaoa_timing_read", "qaoa_gradient_dev", "qaoa_optimize_adam", "qaoa_expectation_noalloc",
     "qaoa_batch_workspace_size", "qaoa_batch_gradient", "qaoa_batch_autotune_workspace_size", "qaoa_batch_autotune",
-    "qaoa_cost_vector_pubo", "qaoa_optimize_lbfgs",
+    "qaoa_cost_vector_pubo", "qaoa_optimize_lbfgs", "qaoa_proposer_param_count", "qaoa_propose_workspace_size",
+    "qaoa_propose_angles",
 ]
 
 
@@ -80,6 +81,9 @@ def _load() -> ct.CDLL:
                                 ct.c_double, ct.c_double, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_optimize_lbfgs": ([i32, i32, vp, vp, ct.POINTER(CostT), vp, i32, i64, i32, ct.c_double, vp, vp, vp,
                                  ct.c_size_t, vp], i32),
+        "qaoa_proposer_param_count": ([i32], i64),
+        "qaoa_propose_workspace_size": ([i32, ct.POINTER(GraphT), szp], i32),
+        "qaoa_propose_angles": ([i32, ct.POINTER(GraphT), i32, vp, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_cost_vector_pubo": ([i32, i64, vp, dp, i32, vp, i32, ct.POINTER(CostT), vp], i32),
         "qaoa_batch_workspace_size": ([i32, i32, i32, ct.POINTER(GraphT), vp, szp], i32),
         "qaoa_batch_gradient": ([i32, i32, ct.POINTER(GraphT), dp, i32, vp, vp, vp, ct.c_size_t, vp], i32),
@@ -407,7 +411,7 @@ def _tiles_arg(tiles):
 
 
 def batch_gradient(graphs, angles, dtype: str = "c128", tiles=None, device="cuda"):
-    """Batched S7 for many small integer-weight graphs in one persistent launch.
+    """Batched S7 for many small graphs in one persistent launch.
 
     graphs: sequence of Graph; angles: (ngraphs, 2p) host array, row i = [gamma | beta] of
     graph i.  Returns a (ngraphs, 2p + 2) float64 device tensor, row i = [E, norm,
@@ -470,6 +474,30 @@ def optimize_lbfgs(cost: CostVector, angles, max_evals: int = 200, m: int = 10, 
     res = {"E": float(i[0]), "iterations": int(i[1]), "evaluations": int(i[2]),
            "status": ("evaluations used up", "converged", "no progress")[int(i[3])]}
     return hist[:res["evaluations"]], res
+
+
+def proposer_param_count(p: int) -> int:
+    return int(_lib.qaoa_proposer_param_count(p))
+
+
+def propose_angles(graphs, params, p: int, device="cuda"):
+    """Learned starting angles for each graph from the fused network kernel: a (ngraphs, 2p)
+    float64 device tensor, rows [gamma | beta].  params: float32 CUDA tensor of
+    proposer_param_count(p) values."""
+    torch = _torch()
+    _require_cuda(params)
+    if params.dtype != torch.float32 or params.numel() != proposer_param_count(p):
+        raise ValueError("params must be a float32 tensor of proposer_param_count(p) values")
+    ng = len(graphs)
+    structs = (GraphT * max(ng, 1))(*[g.as_struct() for g in graphs])
+    nbytes = ct.c_size_t()
+    _check(_lib.qaoa_propose_workspace_size(ng, structs, ct.byref(nbytes)), "propose_workspace_size")
+    ws = _workspace(nbytes.value, device)
+    out = torch.empty((max(ng, 1), 2 * p), dtype=torch.float64, device=device)
+    _check(_lib.qaoa_propose_angles(ng, structs, p, ct.c_void_p(params.data_ptr()), ct.c_void_p(out.data_ptr()),
+                                    ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(_stream(device))),
+           "propose_angles")
+    return out[:ng]
 
 
 def launch_count() -> int:

@@ -23,12 +23,14 @@ constexpr int kPrepThreads = 256;
 constexpr int kMaxBatchEdges = 512;
 
 // One launch prepares every graph: blocks [0, cost_blocks) build the cost vectors (2^12
-// entries per block, C(z) = sum over edges of w [z_u != z_v], Sec. III-B's MaxCut cost);
+// entries per block, C(z) = sum over edges of w [z_u != z_v], Sec. III-B's MaxCut cost,
+// int32 for integer weights, else float64 summed in edge order);
 // the next ngraphs blocks build each graph's per-layer terms and tables; the last block
 // (fixed point) builds the shared turn tables.
 __global__ void __launch_bounds__(kPrepThreads) batch_prep_kernel(const __grid_constant__ BatchArgs b,
                                                                    int64_t cost_blocks) {
-  __shared__ int3 e_s[kMaxBatchEdges];
+  __shared__ int2 e_s[kMaxBatchEdges];
+  __shared__ double w_s[kMaxBatchEdges];
   const int64_t blk = blockIdx.x;
   const int tid = threadIdx.x;
   const int p = b.p;
@@ -41,15 +43,25 @@ __global__ void __launch_bounds__(kPrepThreads) batch_prep_kernel(const __grid_c
       else hi = mid - 1;
     }
     const BatchGraph G = b.graphs[lo];
-    for (int k = tid; k < G.m; k += kPrepThreads)
-      e_s[k] = make_int3(b.edges[3 * (G.edge + k)], b.edges[3 * (G.edge + k) + 1], b.edges[3 * (G.edge + k) + 2]);
+    for (int k = tid; k < G.m; k += kPrepThreads) {
+      e_s[k] = make_int2(b.edges[2 * (G.edge + k)], b.edges[2 * (G.edge + k) + 1]);
+      w_s[k] = b.ew[G.edge + k];
+    }
     __syncthreads();
     const uint64_t z0 = (uint64_t)(blk - b.blk_off[lo]) << kBatchCostBits;
     const uint64_t zend = 1ull << G.n;
     for (uint64_t z = z0 + tid; z < z0 + (1ull << kBatchCostBits) && z < zend; z += kPrepThreads) {
-      int c = 0;
-      for (int k = 0; k < G.m; ++k) c += e_s[k].z * (int)(((z >> e_s[k].x) ^ (z >> e_s[k].y)) & 1ull);
-      b.C[G.cost + (int64_t)z] = c;
+      if (b.cost_f64) {  // float64 sum in edge order
+        double c = 0.0;
+        for (int k = 0; k < G.m; ++k)
+          if (((z >> e_s[k].x) ^ (z >> e_s[k].y)) & 1ull) c += w_s[k];
+        ((double*)b.C)[G.cost + (int64_t)z] = c;
+      } else {
+        int c = 0;
+        for (int k = 0; k < G.m; ++k)
+          if (((z >> e_s[k].x) ^ (z >> e_s[k].y)) & 1ull) c += (int)w_s[k];
+        ((int*)b.C)[G.cost + (int64_t)z] = c;
+      }
     }
     return;
   }
@@ -117,8 +129,8 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) batch_kernel(const __grid_co
         sa.kind = SWEEP_GENERIC;
         sa.psi = (char*)b.psi + G.state * vs;
         sa.lam = (char*)b.lam + G.state * vs;
-        sa.C = b.C + G.cost;
-        sa.cost_dtype = QAOA_COST_I32;
+        sa.C = (const char*)b.C + G.cost * (b.cost_f64 ? 8 : 4);
+        sa.cost_dtype = b.cost_f64 ? QAOA_COST_F64 : QAOA_COST_I32;
         sa.needs_cost = bs.needs_cost;
         sa.g = bs.g;
         sa.tile_bits = CF::B;
@@ -159,15 +171,16 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) batch_kernel(const __grid_co
 
 template <class CF, bool FX>
 cudaError_t launch_batch_cfg(const BatchArgs& b, int first, int count, int* queue, cudaStream_t s) {
-  const size_t smem = (sizeof(typename Sweeper<CF, FX, true>::V) << CF::B) + ((size_t)4 << CF::B);
+  const size_t smem = (sizeof(typename Sweeper<CF, FX, true>::V) << CF::B) + ((size_t)(b.cost_f64 ? 8 : 4) << CF::B);
+  const size_t smem_max = (sizeof(typename Sweeper<CF, FX, true>::V) << CF::B) + ((size_t)8 << CF::B);
   static bool attr = false;
   static int per_sm = 1, sms = 1;
   if (!attr) {
-    cudaFuncSetAttribute(batch_kernel<CF, FX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(batch_kernel<CF, FX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<CF, FX>, CF::NT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<CF, FX>, CF::NT, smem_max);
     if (per_sm < 1) per_sm = 1;
     attr = true;
   }

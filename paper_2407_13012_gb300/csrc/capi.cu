@@ -151,31 +151,39 @@ struct Ctx {
 
 static int cuda_status(cudaError_t e) { return e == cudaSuccess ? QAOA_OK : QAOA_ERR_CUDA; }
 
-// Whether a sweep matches one of the two lean kernel shapes: full tile with affine
-// layout-0 addresses, internal formats, and the op pattern MIX or MIX PHASE MIX (with
-// lambda: MIX+X, or MIX+X CTERM PHASE MIX+X).
+// Whether a sweep runs in a lean kernel: full tiles with affine layout-0 addresses
+// (t + c = B, c <= B - RB), groups of >= 3 qubits, the state loaded in the internal format
+// (complex64: also the caller's, which is the same) or created as |+>.  complex64 takes
+// the lean kernel for plain mixer sweeps only: its op-program and two-buffer forms measured
+// slower than the generic kernel on GB300 (register spills at 32 amplitudes per thread and
+// barrier stalls at 16 amplitudes and one block per SM).  A single mixer on
+// internal formats is the plain shape; any other program runs as an op program (its cost
+// tile by 16-byte copies, which need whole 16-byte chunks per row).
 static int lean_kind(const Sweep& s, const Group& g, int tile_bits, int dtype, bool cost_f64) {
-  // measured on GB300: the lean shapes help the fixed-point (complex128) kernels; the
-  // float32 generic kernel is already faster than its lean form
-  if (dtype != QAOA_C128) return SWEEP_GENERIC;
-  const int rb = dtype == QAOA_C128 ? (s.two ? 3 : 4) : (tile_bits == 13 ? 5 : 4);  // float32 lean: unused
+  const bool fx = dtype == QAOA_C128;
+  if (!fx && s.two) return SWEEP_GENERIC;
+  const int rb = fx ? (s.two ? 3 : 4) : 5;
   if (g.t + g.c != tile_bits || g.c > tile_bits - rb || g.t < 3) return SWEEP_GENERIC;
-  if (s.init || s.load_user || s.store_user || !s.store_psi) return SWEEP_GENERIC;
-  if (s.two && !(s.load_lam && s.store_lam)) return SWEEP_GENERIC;
+  if (fx && s.load_user) return SWEEP_GENERIC;
   const uint32_t want_mix = s.two ? (F_PSI | F_LAM | F_XTERM) : F_PSI;
-  auto is = [](uint32_t op, uint32_t kind, uint32_t flags) {
-    return (op & 0xff) == kind && ((op & 0xff00) & ~(uint32_t)F_SIGN) == flags;
-  };
   const std::vector<uint32_t>& o = s.ops;
-  if (o.size() == 1 && is(o[0], OP_MIX, want_mix)) return SWEEP_LEAN_MIX;
+  const bool plain_formats = !s.init && !s.load_user && !s.store_user && s.store_psi &&
+                             (!s.two || (s.load_lam && s.store_lam));
+  if (plain_formats && o.size() == 1 && (o[0] & 0xff) == OP_MIX && ((o[0] & 0xff00) & ~(uint32_t)F_SIGN) == want_mix)
+    return SWEEP_LEAN_MIX;
+  bool reads_c = false, lam_live = s.two && s.load_lam;
+  for (uint32_t op : o) {
+    const uint32_t kind = op & 0xff;
+    reads_c |= (kind == OP_PHASE || kind == OP_LAMBDA || kind == OP_RED_EXPECT || kind == OP_RED_CTERM);
+    // the two-buffer lean kernel applies every mixer and phase to both buffers, which is
+    // exact for an op on psi alone only while lambda is still zero
+    if (s.two && (kind == OP_MIX || kind == OP_PHASE) && !(op & F_LAM) && lam_live) return SWEEP_GENERIC;
+    if (kind == OP_LAMBDA) lam_live = true;
+  }
   const bool chunky = g.j0 == 0 || (1 << g.c) >= (cost_f64 ? 2 : 4);
-  if (!chunky) return SWEEP_GENERIC;
-  if (!s.two && o.size() == 3 && is(o[0], OP_MIX, F_PSI) && is(o[1], OP_PHASE, F_PSI) && is(o[2], OP_MIX, F_PSI))
-    return SWEEP_LEAN_MERGED;
-  if (s.two && o.size() == 4 && is(o[0], OP_MIX, want_mix) && is(o[1], OP_RED_CTERM, F_PSI | F_LAM) &&
-      is(o[2], OP_PHASE, F_PSI | F_LAM) && is(o[3], OP_MIX, want_mix))
-    return SWEEP_LEAN_MERGED;
-  return SWEEP_GENERIC;
+  if (reads_c && !chunky) return SWEEP_GENERIC;
+  if (!fx) return SWEEP_GENERIC;
+  return SWEEP_LEAN_OPS;
 }
 
 // Run a list of sweeps with one shared grid, then reduce the partials into out[0..nout).
@@ -885,11 +893,13 @@ namespace {
 struct BatchLayout {
   std::vector<BatchGraph> graphs;  // processing order: large-tile graphs, then small-tile, n descending
   std::vector<BatchPlan> plans;
-  std::vector<int> edges;
+  std::vector<int> edges;          // (u, v) pairs
+  std::vector<double> ew;          // edge weights
+  bool cost_f64 = false;           // some graph has float weights: float64 costs for all
   std::vector<int64_t> blk_off;
   std::vector<double> angles;      // processing order
   int n_large = 0;                 // graphs [0, n_large) use 2^12 tiles, the rest 2^10
-  size_t off_graphs = 0, off_plans = 0, off_blk = 0, off_edges = 0, off_angles = 0, head_bytes = 0;
+  size_t off_graphs = 0, off_plans = 0, off_blk = 0, off_edges = 0, off_ew = 0, off_angles = 0, head_bytes = 0;
   size_t off_queue = 0, off_trig = 0, off_psi = 0, off_lam = 0, off_C = 0, off_phase = 0, off_dtab = 0,
          off_turn = 0, total = 0;
 };
@@ -941,10 +951,11 @@ int batch_layout(int dtype, int p, int ngraphs, const qaoa_graph_t* gs, const do
   const size_t vs = fx ? 16 : 8;
   std::vector<int64_t> cmin(ngraphs), cmax(ngraphs);
   std::vector<int> tile(ngraphs);
+  bool any_float = false;
   for (int i = 0; i < ngraphs; ++i) {
     const qaoa_graph_t& g = gs[i];
     if (qaoa_graph_check(&g, &cmin[i], &cmax[i]) != QAOA_OK) return QAOA_ERR_INVALID_ARG;
-    if (g.weight_kind != QAOA_WEIGHT_INT) return QAOA_ERR_UNSUPPORTED;
+    if (g.weight_kind != QAOA_WEIGHT_INT) any_float = true;
     if (g.n > QAOA_BATCH_MAX_N || g.m > QAOA_BATCH_MAX_EDGES) return QAOA_ERR_UNSUPPORTED;
     tile[i] = tiles ? tiles[g.n] : default_tile(g.n);
     if (tile[i] != 0 && tile[i] != 1) return QAOA_ERR_INVALID_ARG;
@@ -963,6 +974,7 @@ int batch_layout(int dtype, int p, int ngraphs, const qaoa_graph_t* gs, const do
   for (int t = 0; t < 2; ++t)
     for (int n = 0; n <= QAOA_MAX_N; ++n) plan_of[t][n] = -1;
   L = BatchLayout();
+  L.cost_f64 = any_float;
   L.graphs.resize(ngraphs);
   L.blk_off.assign(ngraphs + 1, 0);
   L.angles.assign((size_t)ngraphs * 2 * p, 0.0);
@@ -982,13 +994,14 @@ int batch_layout(int dtype, int p, int ngraphs, const qaoa_graph_t* gs, const do
       L.plans.push_back(P);
     }
     G.plan = plan_of[tile[i]][g.n];
-    const int64_t cb = std::max(std::llabs(cmin[i]), std::llabs(cmax[i]));
-    int ls = 0;
-    while (ls < 40 && ((int64_t)1 << ls) < cb) ++ls;
+    double sum_abs = 0.0;
+    for (int64_t e = 0; e < g.m; ++e) sum_abs += std::fabs(g.w ? g.w[e] : 1.0);
+    int ls = 0;  // 2^lam_shift >= sum |w| >= max |C|
+    while (ls < 62 && std::ldexp(1.0, ls) < sum_abs) ++ls;
     G.lam_shift = ls;
     const int64_t span = cmax[i] - cmin[i] + 1;
-    G.cmin = (int)cmin[i];
-    G.span = (span >= 1 && span <= QAOA_MAX_TABLE_SPAN) ? (int)span : 0;
+    G.cmin = L.cost_f64 ? 0 : (int)cmin[i];
+    G.span = (!L.cost_f64 && span >= 1 && span <= QAOA_MAX_TABLE_SPAN) ? (int)span : 0;
     G.state = amps;
     G.cost = amps;
     amps += std::max<int64_t>((int64_t)1 << g.n, 64);  // 64-element (>= 256-byte) alignment
@@ -998,7 +1011,7 @@ int batch_layout(int dtype, int p, int ngraphs, const qaoa_graph_t* gs, const do
     for (int64_t e = 0; e < g.m; ++e) {
       L.edges.push_back(g.uv[2 * e]);
       L.edges.push_back(g.uv[2 * e + 1]);
-      L.edges.push_back(g.w ? (int)g.w[e] : 1);
+      L.ew.push_back(g.w ? g.w[e] : 1.0);
     }
     edge += g.m;
     L.blk_off[k + 1] = L.blk_off[k] + (((int64_t)1 << g.n) + (1 << kBatchCostBits) - 1) / (1 << kBatchCostBits);
@@ -1006,7 +1019,10 @@ int batch_layout(int dtype, int p, int ngraphs, const qaoa_graph_t* gs, const do
       for (int j = 0; j < 2 * p; ++j) L.angles[(size_t)k * 2 * p + j] = angles[(size_t)i * 2 * p + j];
     if (tile[i] == 1) L.n_large = k + 1;
   }
-  if (L.edges.empty()) L.edges.push_back(0);
+  if (L.edges.empty()) {
+    L.edges.assign(2, 0);
+    L.ew.assign(1, 0.0);
+  }
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
@@ -1017,13 +1033,14 @@ int batch_layout(int dtype, int p, int ngraphs, const qaoa_graph_t* gs, const do
   L.off_plans = take(sizeof(BatchPlan) * std::max<size_t>(L.plans.size(), 1));
   L.off_blk = take(sizeof(int64_t) * (ngraphs + 1));
   L.off_edges = take(sizeof(int) * L.edges.size());
+  L.off_ew = take(sizeof(double) * L.ew.size());
   L.off_angles = take(sizeof(double) * std::max<size_t>(L.angles.size(), 1));
   L.head_bytes = o;
   L.off_queue = take(256);
   L.off_trig = take(sizeof(double) * 3 * p * std::max(ngraphs, 1));
   L.off_psi = take(vs * std::max<int64_t>(amps, 1));
   L.off_lam = take(vs * std::max<int64_t>(amps, 1));
-  L.off_C = take(4 * std::max<int64_t>(amps, 1));
+  L.off_C = take((L.cost_f64 ? 8 : 4) * std::max<int64_t>(amps, 1));
   L.off_phase = take(vs * std::max<int64_t>(tab, 1));
   L.off_dtab = take(fx ? (size_t)16 * p * 196 * std::max(ngraphs, 1) : 0);
   L.off_turn = take(fx ? (size_t)16 * 3072 : 0);
@@ -1044,6 +1061,7 @@ int batch_run(int dtype, int p, const BatchLayout& L, double* out_dev, void* ws_
   std::memcpy(head.data() + L.off_plans, L.plans.data(), sizeof(BatchPlan) * L.plans.size());
   std::memcpy(head.data() + L.off_blk, L.blk_off.data(), sizeof(int64_t) * L.blk_off.size());
   std::memcpy(head.data() + L.off_edges, L.edges.data(), sizeof(int) * L.edges.size());
+  std::memcpy(head.data() + L.off_ew, L.ew.data(), sizeof(double) * L.ew.size());
   std::memcpy(head.data() + L.off_angles, L.angles.data(), sizeof(double) * L.angles.size());
   if (cudaMemcpyAsync(ws, head.data(), L.head_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return QAOA_ERR_CUDA;
   if (cudaMemsetAsync(ws + L.off_queue, 0, 256, s) != cudaSuccess) return QAOA_ERR_CUDA;
@@ -1055,11 +1073,13 @@ int batch_run(int dtype, int p, const BatchLayout& L, double* out_dev, void* ws_
   b.graphs = (const BatchGraph*)(ws + L.off_graphs);
   b.plans = (const BatchPlan*)(ws + L.off_plans);
   b.edges = (const int*)(ws + L.off_edges);
+  b.ew = (const double*)(ws + L.off_ew);
+  b.cost_f64 = L.cost_f64;
   b.blk_off = (const int64_t*)(ws + L.off_blk);
   b.angles = (const double*)(ws + L.off_angles);
   b.psi = ws + L.off_psi;
   b.lam = ws + L.off_lam;
-  b.C = (int*)(ws + L.off_C);
+  b.C = ws + L.off_C;
   b.phase = ws + L.off_phase;
   b.dtab = dtype == QAOA_C128 ? ws + L.off_dtab : nullptr;
   b.turn = dtype == QAOA_C128 ? ws + L.off_turn : nullptr;
@@ -1177,6 +1197,88 @@ int qaoa_batch_autotune(int dtype, int p, int n_lo, int n_hi, int graphs_per_n, 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return rc;
+}
+
+// ------------------------------------------------------------ learned angle proposer
+
+namespace {
+struct ProposeLayout {
+  std::vector<int> n, uv;
+  std::vector<int64_t> edge_off;
+  std::vector<double> w;
+  size_t off_n = 0, off_eo = 0, off_uv = 0, off_w = 0, total = 0;
+};
+
+int propose_layout(int ngraphs, const qaoa_graph_t* graphs, ProposeLayout& L) {
+  if (ngraphs < 0 || ngraphs > QAOA_BATCH_MAX_GRAPHS || (ngraphs > 0 && graphs == nullptr)) return QAOA_ERR_INVALID_ARG;
+  L = ProposeLayout();
+  L.edge_off.push_back(0);
+  for (int i = 0; i < ngraphs; ++i) {
+    const qaoa_graph_t& g = graphs[i];
+    if (qaoa_graph_check(&g, nullptr, nullptr) != QAOA_OK) return QAOA_ERR_INVALID_ARG;
+    L.n.push_back(g.n);
+    for (int64_t e = 0; e < g.m; ++e) {
+      L.uv.push_back(g.uv[2 * e]);
+      L.uv.push_back(g.uv[2 * e + 1]);
+      L.w.push_back(g.w ? g.w[e] : 1.0);
+    }
+    L.edge_off.push_back(L.edge_off.back() + g.m);
+  }
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += round256(std::max<size_t>(bytes, 1));
+    return at;
+  };
+  L.off_n = take(sizeof(int) * L.n.size());
+  L.off_eo = take(sizeof(int64_t) * L.edge_off.size());
+  L.off_uv = take(sizeof(int) * L.uv.size());
+  L.off_w = take(sizeof(double) * L.w.size());
+  L.total = o;
+  return QAOA_OK;
+}
+}  // namespace
+
+int64_t qaoa_proposer_param_count(int p) {
+  if (p < 1 || p > QAOA_MAX_P) return -1;
+  return proposer_param_count(p);
+}
+
+int qaoa_propose_workspace_size(int ngraphs, const qaoa_graph_t* graphs, size_t* bytes) {
+  if (bytes == nullptr) return QAOA_ERR_INVALID_ARG;
+  ProposeLayout L;
+  const int rc = propose_layout(ngraphs, graphs, L);
+  if (rc) return rc;
+  *bytes = L.total;
+  return QAOA_OK;
+}
+
+int qaoa_propose_angles(int ngraphs, const qaoa_graph_t* graphs, int p, const float* params_dev, double* angles_dev,
+                        void* ws_dev, size_t ws_bytes, void* stream) {
+  if (p < 1 || p > QAOA_MAX_P) return QAOA_ERR_INVALID_ARG;
+  ProposeLayout L;
+  int rc = propose_layout(ngraphs, graphs, L);
+  if (rc) return rc;
+  if (ngraphs == 0) return QAOA_OK;
+  if (params_dev == nullptr || angles_dev == nullptr) return QAOA_ERR_INVALID_ARG;
+  if (ws_dev == nullptr || ws_bytes < L.total) return QAOA_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<char> head(L.total, 0);
+  std::memcpy(head.data() + L.off_n, L.n.data(), sizeof(int) * L.n.size());
+  std::memcpy(head.data() + L.off_eo, L.edge_off.data(), sizeof(int64_t) * L.edge_off.size());
+  if (!L.uv.empty()) std::memcpy(head.data() + L.off_uv, L.uv.data(), sizeof(int) * L.uv.size());
+  if (!L.w.empty()) std::memcpy(head.data() + L.off_w, L.w.data(), sizeof(double) * L.w.size());
+  char* ws = (char*)ws_dev;
+  if (cudaMemcpyAsync(ws, head.data(), L.total, cudaMemcpyHostToDevice, s) != cudaSuccess) return QAOA_ERR_CUDA;
+  ProposeArgs a;
+  a.p = p;
+  a.n = (const int*)(ws + L.off_n);
+  a.edge_off = (const int64_t*)(ws + L.off_eo);
+  a.uv = (const int*)(ws + L.off_uv);
+  a.w = (const double*)(ws + L.off_w);
+  a.params = params_dev;
+  a.angles = angles_dev;
+  return cuda_status(launch_propose(a, ngraphs, s));
 }
 
 int64_t qaoa_launch_count(void) { return g_launches.load(); }

@@ -46,7 +46,7 @@ struct SweepGeom {
   int64_t tiles;  // number of tiles = 2^(n - t - c)
 };
 
-enum SweepKind : int { SWEEP_GENERIC = 0, SWEEP_LEAN_MIX = 1, SWEEP_LEAN_MERGED = 2 };
+enum SweepKind : int { SWEEP_GENERIC = 0, SWEEP_LEAN_MIX = 1, SWEEP_LEAN_OPS = 2 };
 
 struct SweepArgs {
   int kind;  // SweepKind: generic op program or one of the lean shapes
@@ -217,7 +217,7 @@ struct BatchGraph {
   int64_t state;   // element offset of psi and lambda in the state arenas
   int64_t cost;    // element offset of C in the cost arena
   int64_t table;   // entry offset of the p * span phase-table entries
-  int64_t edge;    // offset of the (u, v, w) triples in the edge array
+  int64_t edge;    // index of the graph's first edge in the edge arrays
 };
 
 struct BatchArgs {
@@ -226,12 +226,14 @@ struct BatchArgs {
   int dtype;
   const BatchGraph* graphs;
   const BatchPlan* plans;
-  const int* edges;          // (u, v, w) integer triples
+  const int* edges;          // (u, v) pairs
+  const double* ew;          // edge weights
+  int cost_f64;              // float64 costs (float weights in the batch) instead of int32
   const int64_t* blk_off;    // cost kernel: first block of each graph (ngraphs + 1)
   const double* angles;      // [gamma p | beta p] per graph, processing order
   void* psi;                 // state arenas (internal format)
   void* lam;
-  int* C;                    // cost arena (int32)
+  void* C;                   // cost arena (int32 or float64)
   void* phase;               // phase tables
   void* dtab;                // fixed point: p * 196 mixer diagonals per graph
   void* turn;                // fixed point: shared turn tables
@@ -245,5 +247,18 @@ cudaError_t launch_batch_prep(const BatchArgs& b, int64_t cost_blocks, cudaStrea
 // tile: 0 = small tiles (2^10 amplitudes), 1 = large tiles (2^12)
 cudaError_t launch_batch(const BatchArgs& b, int tile, int first, int count, int* queue, cudaStream_t s);
 int batch_tile_bits(int tile);
+
+// learned angle proposer (fused network inference, one CTA per graph)
+struct ProposeArgs {
+  int p;
+  const int* n;              // per graph
+  const int64_t* edge_off;   // ngraphs + 1
+  const int* uv;             // (u, v) pairs
+  const double* w;           // edge weights
+  const float* params;       // packed network parameters
+  double* angles;            // ngraphs x 2p
+};
+int64_t proposer_param_count(int p);
+cudaError_t launch_propose(const ProposeArgs& a, int ngraphs, cudaStream_t s);
 
 }  // namespace qaoa

@@ -9,11 +9,10 @@ namespace {
 
 // ------------------------------------------------------------------ lean sweeps
 //
-// Most of the time goes to two sweep shapes: a mixer sweep (one group mixer) and a merged
-// sweep (mixer, phase, mixer; with lambda the adjoint X-terms, the C-term and the inverse
-// phase in between).  They get kernels whose layout sequence is fixed at compile time, so
-// each instance holds only the code it runs.  Tiles are full, the state is in the internal
-// format and layout 0 addresses are affine; the host checks all of that before choosing
+// Sweeps on full tiles run in kernels whose layout sequence is fixed at compile time, so
+// each instance holds only the code it runs: a plain mixer sweep, and a sweep that runs its
+// op program (mixers, phases, lambda and reductions) with the same mixer code.  The host
+// checks the tile shape, the formats and the affine layout-0 addresses before choosing
 // them.
 
 template <class CF, bool FX, bool TWO>
@@ -131,9 +130,12 @@ struct Lean : Sweeper<CF, FX, TWO> {
     fx_back<L>(lam);
   }
 
-  // ---- float32: rounds K..L forwards (F32_FWD) or K..0 backwards
+  // ---- float32: RX(2 beta) butterflies round by round through layouts 0..L, then one
+  // exchange back to layout 0.  With X-terms (adjoint pass) each round's terms are taken
+  // on the exact state before its butterflies, so the per-qubit factors are applied at the
+  // end of every round; otherwise once at the end.
   template <int K>
-  __device__ __forceinline__ void f32_round(bool tanf, float tu, float m, bool lam, bool xt, float& xs, int& pending) {
+  __device__ __forceinline__ void f32_round(bool tanf, float tu, float m, bool xt, float& xs, int& pending) {
     if constexpr (!FX) {
       const unsigned msk = gmask<K>();
       if (xt) {
@@ -152,92 +154,90 @@ struct Lean : Sweeper<CF, FX, TWO> {
       pending += __popc(msk);
       if (tanf) {
         this->template bf_round<true>(this->v, msk, tu);
-        if constexpr (TWO) if (lam) this->template bf_round<true>(this->w, msk, tu);
+        if constexpr (TWO) this->template bf_round<true>(this->w, msk, tu);
       } else {
         this->template bf_round<false>(this->v, msk, tu);
-        if constexpr (TWO) if (lam) this->template bf_round<false>(this->w, msk, tu);
+        if constexpr (TWO) this->template bf_round<false>(this->w, msk, tu);
       }
       if (xt && pending) {
         const float2 f = B::round_factor(tanf, m, pending);
         this->scale_f32(this->v, f);
-        if constexpr (TWO) if (lam) this->scale_f32(this->w, f);
+        if constexpr (TWO) this->scale_f32(this->w, f);
         pending = 0;
       }
     }
   }
   template <int K, int L>
-  __device__ __forceinline__ void f32_fwd(bool tanf, float tu, float m, bool lam, bool xt, float& xs, int& pending) {
+  __device__ __forceinline__ void f32_fwd(bool tanf, float tu, float m, bool xt, float& xs, int& pending) {
     if constexpr (K > 0) exb<K - 1, K>();
-    f32_round<K>(tanf, tu, m, lam, xt, xs, pending);
-    if constexpr (K < L) f32_fwd<K + 1, L>(tanf, tu, m, lam, xt, xs, pending);
+    f32_round<K>(tanf, tu, m, xt, xs, pending);
+    if constexpr (K < L) f32_fwd<K + 1, L>(tanf, tu, m, xt, xs, pending);
   }
-  template <int K>
-  __device__ __forceinline__ void f32_back(bool tanf, float tu, float m, bool lam, bool xt, float& xs, int& pending) {
-    f32_round<K>(tanf, tu, m, lam, xt, xs, pending);
-    if constexpr (K > 0) {
-      exb<K, K - 1>();
-      f32_back<K - 1>(tanf, tu, m, lam, xt, xs, pending);
+  template <int L>
+  __device__ __forceinline__ void f32_mixer(int layer, bool inverse, int xacc) {
+    if constexpr (!FX) {
+      const double cbd = arg_cosb(this->a, layer);
+      const double sbd = inverse ? -arg_sinb(this->a, layer) : arg_sinb(this->a, layer);
+      const bool tanf = fabs(cbd) >= fabs(sbd);
+      const float tu = tanf ? (float)(sbd / cbd) : (float)(cbd / sbd);
+      const float m = tanf ? (float)cbd : (float)sbd;
+      const bool xt = TWO && xacc >= 0;
+      float xs = 0.f;
+      int pending = 0;
+      f32_fwd<0, L>(tanf, tu, m, xt, xs, pending);
+      if (pending) {
+        const float2 f = B::round_factor(tanf, m, pending);
+        this->scale_f32(this->v, f);
+        if constexpr (TWO) this->scale_f32(this->w, f);
+      }
+      if (xt) this->block_add(xacc, 2.0 * (double)xs, 0.0, false);
+      if constexpr (L > 0) exb<L, 0>();
     }
   }
-  // RX on the group from layout 0 to layout L (BACK = false) or from L to 0 (BACK = true)
-  template <int L, bool BACK>
-  __device__ __forceinline__ void f32_mixer(int layer, bool inverse, bool lam, int xacc) {
-    const double cbd = arg_cosb(this->a, layer), sbd = inverse ? -arg_sinb(this->a, layer) : arg_sinb(this->a, layer);
-    const bool tanf = fabs(cbd) >= fabs(sbd);
-    const float tu = tanf ? (float)(sbd / cbd) : (float)(cbd / sbd);
-    const float m = tanf ? (float)cbd : (float)sbd;
-    const bool xt = TWO && xacc >= 0;
-    float xs = 0.f;
-    int pending = 0;
-    if constexpr (BACK) f32_back<L>(tanf, tu, m, lam, xt, xs, pending);
-    else f32_fwd<0, L>(tanf, tu, m, lam, xt, xs, pending);
-    if (pending) {
-      const float2 f = B::round_factor(tanf, m, pending);
-      this->scale_f32(this->v, f);
-      if constexpr (TWO) if (lam) this->scale_f32(this->w, f);
-    }
-    if (xt) this->block_add(xacc, 2.0 * (double)xs, 0.0, false);
+  template <int L>
+  __device__ __forceinline__ void mixer(int layer, bool inverse, int xacc) {
+    if constexpr (FX) fx_mixer<L>(layer, inverse, TWO, xacc);
+    else f32_mixer<L>(layer, inverse, xacc);
   }
 
-  // ---- the two sweep shapes; L = last round with group qubits
-  template <int L, bool MERGED>
+  // ---- the sweep: one mixer (OPS = false), or the sweep's op program (OPS = true) with
+  // every mixer on the compile-time layout sequence and the elementwise ops in layout 0;
+  // L = last round with group qubits
+  template <int L, bool OPS>
   __device__ __forceinline__ void run() {
     const uint32_t* ops = this->a.ops;
-    const uint32_t o1 = ops[0];
-    const bool lam = TWO;
-    auto acc_of = [](uint32_t op) { return (op & F_XTERM) ? (int)((op >> 24) & 0xff) : -1; };
-    if constexpr (FX) {
-      if constexpr (MERGED) {
-        // both mixers act on the same group: one copy of the mixer code in a loop keeps the
-        // kernel within the instruction cache
-        const uint32_t oc = TWO ? ops[1] : 0u, op = ops[TWO ? 2 : 1], o2 = ops[TWO ? 3 : 2];
-#pragma unroll 1
-        for (int k = 0; k < 2; ++k) {
-          const uint32_t o = k ? o2 : o1;
-          fx_mixer<L>((o >> 16) & 0xff, o & F_SIGN, lam, acc_of(o));
-          if (k == 0) {
-            if constexpr (TWO) this->op_cterm((oc >> 24) & 0xff);
-            this->op_phase((op >> 16) & 0xff, op & F_SIGN, true, TWO);
-          }
-        }
-      } else {
-        fx_mixer<L>((o1 >> 16) & 0xff, o1 & F_SIGN, lam, acc_of(o1));
-      }
+    if constexpr (!OPS) {
+      const uint32_t o = ops[0];
+      mixer<L>((o >> 16) & 0xff, o & F_SIGN, (o & F_XTERM) ? (int)((o >> 24) & 0xff) : -1);
     } else {
-      f32_mixer<L, false>((o1 >> 16) & 0xff, o1 & F_SIGN, lam, acc_of(o1));
-      if constexpr (MERGED) {
-        const uint32_t oc = TWO ? ops[1] : 0u, op = ops[TWO ? 2 : 1], o2 = ops[TWO ? 3 : 2];
-        if constexpr (TWO) this->op_cterm((oc >> 24) & 0xff);
-        this->op_phase((op >> 16) & 0xff, op & F_SIGN, true, TWO);
-        f32_mixer<L, true>((o2 >> 16) & 0xff, o2 & F_SIGN, lam, acc_of(o2));
-      } else {
-        if constexpr (L > 0) exb<L, 0>();
+      // one copy of the mixer code for every mixer of the program keeps the kernel within
+      // the instruction cache.  Two-buffer kernels apply mixers and phases to both buffers:
+      // an op on psi alone only occurs while lambda is still zero (the host checks that).
+#pragma unroll 1
+      for (int k = 0; k < this->a.nops; ++k) {
+        const uint32_t op = ops[k];
+        const uint32_t kind = op & 0xff;
+        const int layer = (op >> 16) & 0xff, acc = (int)((op >> 24) & 0xff);
+        const bool inv = op & F_SIGN;
+        if (kind == OP_MIX) {
+          mixer<L>(layer, inv, (op & F_XTERM) ? acc : -1);
+        } else if (kind == OP_PHASE) {
+          this->op_phase(layer, inv, true, TWO);
+        } else if (kind == OP_LAMBDA) {
+          if constexpr (TWO) this->op_lambda();
+        } else if (kind == OP_RED_EXPECT) {
+          this->op_expect(acc);
+        } else if (kind == OP_RED_CTERM) {
+          if constexpr (TWO) this->op_cterm(acc);
+        }
       }
     }
   }
 };
 
-template <class CF, bool FX, bool TWO, bool MERGED, int LAST>
+// Lean sweeps: full tiles, affine layout-0 addresses, state loaded in the internal format
+// or created as |+>, stored in the internal or the caller's format (complex64: the same).
+template <class CF, bool FX, bool TWO, bool OPS, int LAST>
 __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_constant__ SweepArgs a) {
   using S = Lean<CF, FX, TWO>;
   using V = typename S::V;
@@ -245,7 +245,8 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* X = (V*)smem_raw;
   void* Cs = smem_raw + (sizeof(V) << CF::B);
-  V* Tsm = (V*)((unsigned char*)Cs + (MERGED ? ((a.cost_dtype == QAOA_COST_F64 ? 8 : 4) << CF::B) : 0));
+  const bool cost = OPS && a.needs_cost;
+  V* Tsm = (V*)((unsigned char*)Cs + (cost ? ((a.cost_dtype == QAOA_COST_F64 ? 8 : 4) << CF::B) : 0));
   __shared__ double blk[kMaxAcc];
   __shared__ double red[2 * (CF::NT / 32)];
   __shared__ longlong2 dsm[16];
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
   V (&v)[R] = s.v;
   V (&w)[R] = s.w;
   s.Ds = dsm;
-  if (MERGED && a.smem_table_layer >= 0) {
+  if (OPS && a.smem_table_layer >= 0) {
     const V* src = (const V*)a.phase_table + (long long)a.smem_table_layer * a.span;
     for (int k = threadIdx.x; k < a.span; k += CF::NT) Tsm[k] = __ldg(src + k);
     s.Ts = Tsm;
@@ -274,12 +275,15 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
   const bool cf64 = a.cost_dtype == QAOA_COST_F64;
   const uint32_t tb0 = CF::idx(0, tid, 0);
   const uint64_t zs = 1ull << (CF::lo(0) - g.c + g.j0);
+  const bool init = OPS && a.load_fmt == 2;
+  const bool ld_lam = TWO && (!OPS || a.load_lam), st_lam = TWO && (!OPS || a.store_lam);
+  const int st_fmt = OPS ? a.store_fmt : 0;
   __syncthreads();
   for (int64_t tile = blockIdx.x; tile < g.tiles; tile += gridDim.x) {
     const uint64_t base = tile_base(g, tile);
     s.base = base;
     s.cur = 0;
-    if constexpr (MERGED) {  // cost tile, 16-byte asynchronous copies
+    if (cost) {  // cost tile, 16-byte asynchronous copies
       __syncthreads();
       const int per = cf64 ? 2 : 4;
       const uint32_t nch = (1u << CF::B) / per;
@@ -293,20 +297,27 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const uint64_t z = z0 + (uint64_t)r * zs;
-      v[r] = __ldg((const V*)a.psi + z);
-      if constexpr (TWO) w[r] = __ldg((const V*)a.lam + z);
+      if constexpr (FX) v[r] = init ? make_longlong2(a.init_fx, 0) : __ldg((const V*)a.psi + z);
+      else v[r] = init ? make_float2(a.init_f32, 0.f) : __ldg((const V*)a.psi + z);
+      if constexpr (TWO) w[r] = ld_lam ? __ldg((const V*)a.lam + z) : V{};
     }
-    if constexpr (MERGED) {
+    if (cost) {
       cp_async_wait_all();
       __syncthreads();
     }
-    s.template run<LAST, MERGED>();
+    s.template run<LAST, OPS>();
     const uint64_t z1 = local_to_z(g, base, tb0);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const uint64_t z = z1 + (uint64_t)r * zs;
-      ((V*)a.psi)[z] = v[r];
-      if constexpr (TWO) ((V*)a.lam)[z] = w[r];
+      if constexpr (FX) {
+        if (st_fmt == 0) ((V*)a.psi)[z] = v[r];
+        else if (st_fmt == 1)
+          ((double2*)a.psi)[z] = make_double2(fx_to_double(v[r].x, a.fx_shift), fx_to_double(v[r].y, a.fx_shift));
+      } else {
+        if (st_fmt >= 0) ((V*)a.psi)[z] = v[r];
+      }
+      if (st_lam) ((V*)a.lam)[z] = w[r];
     }
   }
   __syncthreads();
@@ -520,23 +531,23 @@ int blocks_per_sm(int cost_bytes) {
   return cached[slot];
 }
 
-template <class CF, bool FX, bool TWO, bool MERGED, int LAST>
+template <class CF, bool FX, bool TWO, bool OPS, int LAST>
 void lean_launch_l(const SweepArgs& a, size_t sm, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(lean_kernel<CF, FX, TWO, MERGED, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(lean_kernel<CF, FX, TWO, OPS, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem_bytes<CF, FX, TWO>(8, kSmemTable));
     attr = true;
   }
-  lean_kernel<CF, FX, TWO, MERGED, LAST><<<a.grid, CF::NT, sm, s>>>(a);
+  lean_kernel<CF, FX, TWO, OPS, LAST><<<a.grid, CF::NT, sm, s>>>(a);
 }
-template <class CF, bool FX, bool TWO, bool MERGED>
+template <class CF, bool FX, bool TWO, bool OPS>
 void lean_launch(const SweepArgs& a, int last, size_t sm, cudaStream_t s) {
   switch (last) {
-    case 0: lean_launch_l<CF, FX, TWO, MERGED, 0>(a, sm, s); break;
-    case 1: lean_launch_l<CF, FX, TWO, MERGED, 1>(a, sm, s); break;
-    case 2: lean_launch_l<CF, FX, TWO, MERGED, 2>(a, sm, s); break;
-    default: lean_launch_l<CF, FX, TWO, MERGED, (CF::NR > 3 ? 3 : 2)>(a, sm, s); break;
+    case 0: lean_launch_l<CF, FX, TWO, OPS, 0>(a, sm, s); break;
+    case 1: lean_launch_l<CF, FX, TWO, OPS, 1>(a, sm, s); break;
+    case 2: lean_launch_l<CF, FX, TWO, OPS, 2>(a, sm, s); break;
+    default: lean_launch_l<CF, FX, TWO, OPS, (CF::NR > 3 ? 3 : 2)>(a, sm, s); break;
   }
 }
 
@@ -546,17 +557,15 @@ void launch_t(const SweepArgs& a, cudaStream_t s) {
   const int cb = a.needs_cost ? (a.cost_dtype == QAOA_COST_F64 ? 8 : 4) : 0;
   const int te = a.smem_table_layer >= 0 ? (int)a.span : 0;
   const size_t sm = smem_bytes<CF, FX, TWO>(cb, te);
-  if (FX && (a.kind == SWEEP_LEAN_MIX || a.kind == SWEEP_LEAN_MERGED)) {
+  if (a.kind == SWEEP_LEAN_MIX || a.kind == SWEEP_LEAN_OPS) {
     // last round holding group qubits selects the instance
     int last = 0;
     for (int k = 0; k < CF::NR; ++k) {
       const int lo = std::max(0, CF::B - CF::RB * (k + 1)), hi = k == 0 ? CF::B : std::max(0, CF::B - CF::RB * k);
       if (hi > a.g.c && lo < a.g.c + a.g.t) last = k;
     }
-    if constexpr (FX) {
-      if (a.kind == SWEEP_LEAN_MERGED) lean_launch<CF, FX, TWO, true>(a, last, sm, s);
-      else lean_launch<CF, FX, TWO, false>(a, last, sm, s);
-    }
+    if (a.kind == SWEEP_LEAN_OPS) lean_launch<CF, FX, TWO, true>(a, last, sm, s);
+    else lean_launch<CF, FX, TWO, false>(a, last, sm, s);
     return;
   }
   sweep_kernel<CF, FX, TWO><<<a.grid, CF::NT, sm, s>>>(a);
@@ -625,8 +634,7 @@ int sweep_grid(int dtype, bool two, int tile_bits, int cost_bytes, int64_t tiles
   } else if (two) {
     per_sm = blocks_per_sm<CfgF3, false, true>(cost_bytes);
   } else {
-    per_sm = tile_bits == 12 ? blocks_per_sm<CfgF2, false, false>(cost_bytes)
-                             : blocks_per_sm<CfgF1, false, false>(cost_bytes);
+    per_sm = blocks_per_sm<CfgF1, false, false>(cost_bytes);
   }
   const int64_t cap = (int64_t)num_sms() * per_sm;
   return (int)(tiles < cap ? tiles : cap);
@@ -639,7 +647,6 @@ cudaError_t launch_sweep(int dtype, bool two, const SweepArgs& a, cudaStream_t s
     else launch_t<CfgX1, true, false>(a, s);
   } else {
     if (two) launch_t<CfgF3, false, true>(a, s);
-    else if (a.tile_bits == 12) launch_t<CfgF2, false, false>(a, s);
     else launch_t<CfgF1, false, false>(a, s);
   }
   note_launch(0, s, false, a.algo_bytes);

@@ -66,8 +66,6 @@ struct Cfg {
 
 // complex64 single buffer: 8192-amplitude tiles, 32 per thread, 256 threads
 using CfgF1 = Cfg<13, 5, 5, 4, 2>;
-// complex64 two buffers (gradient): 4096-amplitude tiles, 16 per thread per buffer
-using CfgF2 = Cfg<12, 4, 4, 4, 2>;
 // complex64 two buffers (gradient) with 8192-amplitude tiles: 32 amplitudes per thread per
 // buffer, one block per SM; at n = 32 this keeps >= 3 carried low bits (64-byte rows)
 using CfgF3 = Cfg<13, 5, 5, 4, 1>;

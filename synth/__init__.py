@@ -206,3 +206,17 @@ def batch_instances(count: int, seed: int, n_lo: int = 8, n_hi: int = 20, prob: 
         gam, bet = angles(p, gseed)
         out.append((n, "reg3" if reg3 else "gnp", e, w, gam, bet))
     return out
+
+
+def proposer_instances(count: int, seed: int, n_lo: int = 12, n_hi: int = 18, prob: float = 0.3):
+    """Graphs for the learned angle proposer: G(n, prob) with n uniform in [n_lo, n_hi] and
+    U(0,1) weights.  Returns a list of (n, edges, weights); graph i draws its edges and
+    weights from the streams of seed ``seed * 2^20 + i``."""
+    st = Stream(seed, "batch")
+    out = []
+    for i in range(count):
+        n = n_lo + st.next_below(n_hi - n_lo + 1)
+        gseed = ((seed << 20) + i) & MASK64
+        e = gnp_edges(n, prob, gseed)
+        out.append((n, e, edge_weights(len(e), "u01", gseed)))
+    return out

@@ -135,15 +135,16 @@ def test_batch_workspace_sizes():
     assert rc == 0 and b3 < b2
     rc, b0 = _batch_ws([])
     assert rc == 0
+    # a float-weight graph makes every cost float64: 4 more bytes per amplitude
+    rc, bf = _batch_ws([_ring(10), _ring(16, np.full(16, 0.5), integer=False)])
+    assert rc == 0 and bf - b2 >= 4 * 2 ** 16
 
 
-@pytest.mark.parametrize("case", ["float_weights", "too_big", "p_zero", "p_large", "bad_tile", "bad_graph"])
+@pytest.mark.parametrize("case", ["too_big", "p_zero", "p_large", "bad_tile", "bad_graph"])
 def test_batch_rejections(case):
     tiles = None
     graphs, p, want = [_ring(8)], 3, q.QAOA_ERR_INVALID_ARG
-    if case == "float_weights":
-        graphs, want = [_ring(8, np.full(8, 0.5), integer=False)], q.QAOA_ERR_UNSUPPORTED
-    elif case == "too_big":
+    if case == "too_big":
         graphs, want = [_ring(q.BATCH_MAX_N + 1)], q.QAOA_ERR_UNSUPPORTED
     elif case == "p_zero":
         p = 0

@@ -20,9 +20,9 @@ def scale_of(w):
     return max(1.0, float(np.sum(np.abs(w))))
 
 
-def check_rows(out, insts, dtype, p):
+def check_rows(out, insts, dtype, p, integer=True):
     for row, (n, fam, e, w, gam, bet) in zip(out, insts):
-        C = qaoa.cut_values(n, e, w, integer=True)
+        C = qaoa.cut_values(n, e, w, integer=integer)
         E, dg, db, _ = qaoa.adjoint_gradient(n, C, gam, bet)
         s = scale_of(w)
         tol = 1e-10 * s if dtype == "c128" else 1e-4 * s
@@ -33,8 +33,8 @@ def check_rows(out, insts, dtype, p):
         assert np.max(np.abs(row[2 + p:] - db)) <= tol, ctx
 
 
-def run(insts, dtype, tiles=None):
-    graphs = [q.Graph(n, e, w, True) for (n, fam, e, w, gam, bet) in insts]
+def run(insts, dtype, tiles=None, integer=True):
+    graphs = [q.Graph(n, e, w, integer) for (n, fam, e, w, gam, bet) in insts]
     ang = np.stack([np.concatenate([gam, bet]) for (*_, gam, bet) in insts])
     return q.batch_gradient(graphs, ang, dtype, tiles=tiles).cpu().numpy()
 
@@ -112,3 +112,14 @@ def test_batch_autotune():
     assert np.all(ms[8:15] > 0)
     insts = synth.batch_instances(20, 3, n_lo=8, n_hi=14, p=3)
     check_rows(run(insts, "c128", tiles), insts, "c128", 3)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_batch_float_weights_vs_oracle(dtype):
+    """U(0,1) weights (float64 costs, directly computed phases), n = 4..18, p = 4."""
+    p = 4
+    insts = []
+    for i, x in enumerate(synth.batch_instances(30, 8, n_lo=4, n_hi=18, p=p)):
+        n, fam, e, w, gam, bet = x
+        insts.append((n, fam, e, synth.edge_weights(len(e), "u01", 1000 + i), gam, bet))
+    check_rows(run(insts, dtype, integer=False), insts, dtype, p, integer=False)

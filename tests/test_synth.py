@@ -1,5 +1,6 @@
 """Seeded synthetic inputs: SplitMix64 reference values, determinism, graph families."""
 import numpy as np
+import pytest
 
 import synth
 
@@ -59,3 +60,16 @@ def test_batch_instances_families_sizes_and_determinism():
             assert n % 2 == 0 and np.all(np.bincount(e.ravel(), minlength=n) == 3)
         fams[fam] += 1
     assert 70 <= fams["reg3"] <= 130
+
+
+def test_proposer_param_layout_round_trip():
+    torch = pytest.importorskip("torch")
+    from paper_2407_13012_gb300 import proposer
+    import paper_2407_13012_gb300 as q
+    for p in (1, 4):
+        net = proposer.make_net(p)
+        vec = proposer.pack(net)
+        H = proposer.HIDDEN
+        assert len(vec) == 3 * H + 3 * (2 * H * H + H) + 2 * H * H + H + 2 * p * H + 2 * p
+        assert len(vec) == q.proposer_param_count(p)
+        assert np.array_equal(proposer.pack(proposer.unpack(vec, p)), vec)
