@@ -32,6 +32,17 @@ sys.path.insert(0, str(ROOT))
 METRIC = "QAOA layer sweeps/s & HBM GB/s at n=28-32; grad evals/s; batched vs plain"
 
 
+def emit(line: dict, a) -> None:
+    """Print the result line; with --jsonl also append it, with host and time, to a log."""
+    text = json.dumps(line)
+    print(text, flush=True)
+    if getattr(a, "jsonl", None):
+        rec = dict(line)
+        rec["host"] = {"cores": os.cpu_count(), "time": time.strftime("%Y-%m-%dT%H:%M:%S")}
+        with open(a.jsonl, "a") as f:
+            f.write(json.dumps(rec) + "\n")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -49,6 +60,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--jsonl", default=None, help="also append the JSON line to this file (a run log)")
     ap.add_argument("--workload", default="layers", choices=["layers", "batched"],
                     help="layers: the n-qubit step (default); batched: only the batched-gradient workload")
     a = ap.parse_args()
@@ -151,8 +163,24 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def traffic_record(kernel_hash: str):
-    """Per-launch DRAM bytes of the sweep kernel from the committed ncu summary, if current."""
+SWEEP_SOURCES = ("sweep.cu", "sweeper.cuh", "fixedpoint.cuh", "internal.h", "capi.cu")
+
+
+def sweep_source_hash() -> str:
+    """Hash of the sources that define and plan the layer-sweep kernels (the traffic record
+    is valid while they are unchanged)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in SWEEP_SOURCES:
+        f = ROOT / "paper_2407_13012_gb300" / "csrc" / name
+        h.update(name.encode())
+        h.update(f.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(kernel_hash: str, key: str):
+    """Per-launch DRAM bytes of the sweep kernels for workload `key` from the committed ncu
+    summary, if it was taken on the current sweep sources."""
     p = ROOT / "profiles" / "sweep_traffic.json"
     try:
         d = json.loads(p.read_text())
@@ -160,7 +188,7 @@ def traffic_record(kernel_hash: str):
         return None
     if d.get("source_hash") != kernel_hash:
         return None
-    return d
+    return d.get("workloads", {}).get(key)
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
@@ -218,7 +246,7 @@ def run_reference(a):
                              "sample": f"numpy oracle layer over a 2^{k}-amplitude slice of the n={a.n} state, "
                                        f"scaled x{scale:.1f} per layer, 3p layers per step"},
             "e2e": {"value": value, "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    emit(line, a)
     return 0
 
 
@@ -301,7 +329,6 @@ def run_ours(a):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2407_13012_gb300 as q
-    from paper_2407_13012_gb300 import _build
 
     e, w, integer, gam, bet = make_instance(a)
     graph = q.Graph(a.n, e, w, integer)
@@ -435,7 +462,7 @@ def run_ours(a):
     peak, peak_kind = measured_peak_hbm()
     sweep_ms, sweep_n, sweep_bytes = kms[0], kla[0], kby[0]
     achieved = (sweep_bytes / (sweep_ms / 1e3)) / 1e9 if sweep_ms > 0 else 0.0
-    tr = traffic_record(_build.source_hash())
+    tr = traffic_record(sweep_source_hash(), f"{a.dtype}_n{a.n}")
     traffic = None
     if tr is not None:
         traffic = tr.get("bytes_per_launch")
@@ -467,7 +494,7 @@ def run_ours(a):
             line["batched"] = batched
         if not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(a, e, w, integer, gam, bet)
-        print(json.dumps(line), flush=True)
+        emit(line, a)
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -482,11 +509,11 @@ def run_batched(a):
     dev = torch.device("cuda", local)
     res = measure_batched(q, dev, a.dtype, a.batch_graphs, reps=a.steps)
     if rank == 0:
-        print(json.dumps({"metric": "batched adjoint gradients (graph gradients/s)", "value": res["graph_grads_per_s"],
-                          "unit": "graph gradients/s", "n_gpus": 1, "steps": a.steps, "warmup": 1,
-                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                          "dtype": "f64" if a.dtype == "c128" else "f32", "data": "synthetic",
-                          "config": {"workload": res["workload"]}, "batched": res}), flush=True)
+        emit({"metric": "batched adjoint gradients (graph gradients/s)", "value": res["graph_grads_per_s"],
+              "unit": "graph gradients/s", "n_gpus": 1, "steps": a.steps, "warmup": 1,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+              "dtype": "f64" if a.dtype == "c128" else "f32", "data": "synthetic",
+              "config": {"workload": res["workload"]}, "batched": res}, a)
     return 0
 
 

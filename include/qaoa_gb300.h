@@ -280,8 +280,8 @@ int qaoa_gradient_dev(int n, int dtype, void* psi_dev, void* lambda_dev, const q
  */
 int qaoa_optimize_adam(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,
                        double* angles_dev, int p, int64_t steps, double lr, double beta1,
-                       double beta2, double eps, double* history_dev, void* ws_dev,
-                       size_t ws_bytes, void* stream);
+                       double beta2, double eps, double* history_dev, double* state_dev, int resume,
+                       void* ws_dev, size_t ws_bytes, void* stream);
 
 /*
  * L-BFGS ascent on E = <C> over the angles, entirely on the device (the paper
@@ -305,8 +305,22 @@ int qaoa_optimize_adam(int n, int dtype, void* psi_dev, void* lambda_dev, const 
 #define QAOA_LBFGS_MAX_M 16
 int qaoa_optimize_lbfgs(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,
                         double* angles_dev, int p, int64_t max_evals, int m, double gtol,
-                        double* history_dev, double* info_dev, void* ws_dev, size_t ws_bytes,
-                        void* stream);
+                        double* history_dev, double* info_dev, double* state_dev, int resume,
+                        void* ws_dev, size_t ws_bytes, void* stream);
+
+/*
+ * Checkpoint / resume of the optimisers.  state_dev (optional, device,
+ * qaoa_optimizer_state_size() bytes, caller-owned) holds the optimiser's whole
+ * state: Adam's moments and step count, or the L-BFGS machine (point, gradient,
+ * direction, step, pair history, counters).  With state_dev == NULL the state
+ * lives in the workspace and every call starts afresh (resume must be 0).  With
+ * resume = 1 the call continues from state_dev: saved angles plus saved state
+ * give exactly the trajectory of one uninterrupted run (history rows of the
+ * call are numbered from its own first step).  The state is a few KB; copying
+ * it and the angles to host memory is the checkpoint.
+ */
+enum qaoa_optimizer { QAOA_OPTIMIZER_ADAM = 0, QAOA_OPTIMIZER_LBFGS = 1 };
+int qaoa_optimizer_state_size(int kind, int p, size_t* bytes);
 
 /* As qaoa_gradient, then synchronise and copy the 2p+2 doubles to out_host. */
 int qaoa_gradient_host(int n, int dtype, void* psi_dev, void* lambda_dev,

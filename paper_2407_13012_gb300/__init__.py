@@ -78,9 +78,10 @@ def _load() -> ct.CDLL:
         "qaoa_gradient_host": ([i32, i32, vp, vp, ct.POINTER(CostT), dp, dp, i32, vp, dp, vp, ct.c_size_t, vp], i32),
         "qaoa_gradient_dev": ([i32, i32, vp, vp, ct.POINTER(CostT), vp, i32, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_optimize_adam": ([i32, i32, vp, vp, ct.POINTER(CostT), vp, i32, i64, ct.c_double, ct.c_double,
-                                ct.c_double, ct.c_double, vp, vp, ct.c_size_t, vp], i32),
+                                ct.c_double, ct.c_double, vp, vp, i32, vp, ct.c_size_t, vp], i32),
+        "qaoa_optimizer_state_size": ([i32, i32, szp], i32),
         "qaoa_optimize_lbfgs": ([i32, i32, vp, vp, ct.POINTER(CostT), vp, i32, i64, i32, ct.c_double, vp, vp, vp,
-                                 ct.c_size_t, vp], i32),
+                                 i32, vp, ct.c_size_t, vp], i32),
         "qaoa_proposer_param_count": ([i32], i64),
         "qaoa_propose_workspace_size": ([i32, ct.POINTER(GraphT), szp], i32),
         "qaoa_propose_angles": ([i32, ct.POINTER(GraphT), i32, vp, vp, vp, ct.c_size_t, vp], i32),
@@ -378,10 +379,24 @@ class QAOAExpectation:
         return self._fn.apply(angles)
 
 
+OPTIMIZER_ADAM, OPTIMIZER_LBFGS = 0, 1
+
+
+def optimizer_state(kind: str, p: int, device="cuda"):
+    """A zeroed device buffer for an optimiser's state ("adam" or "lbfgs"), for checkpoints:
+    pass it as `state`, copy it (and the angles) to save, pass it back with resume=True."""
+    torch = _torch()
+    nbytes = ct.c_size_t()
+    _check(_lib.qaoa_optimizer_state_size(OPTIMIZER_ADAM if kind == "adam" else OPTIMIZER_LBFGS, p,
+                                          ct.byref(nbytes)), "optimizer_state_size")
+    return torch.zeros(nbytes.value // 8, dtype=torch.float64, device=device)
+
+
 def optimize_adam(cost: CostVector, angles, steps: int, lr: float = 0.01, betas=(0.9, 0.999), eps: float = 1e-8,
-                  dtype: str = "c128", history: bool = True):
+                  dtype: str = "c128", history: bool = True, state=None, resume: bool = False):
     """Adam ascent on <C> for `steps` steps, entirely on the device (one CUDA graph per
-    step replayed).  angles: float64 CUDA tensor [gamma, beta] updated in place.
+    step replayed).  angles: float64 CUDA tensor [gamma, beta] updated in place.  state /
+    resume: see optimizer_state.
     Returns the history tensor (steps x (4p + 2)): [E, norm, dE/dgamma, dE/dbeta, gamma, beta]."""
     torch = _torch()
     _require_cuda(angles)
@@ -396,6 +411,7 @@ def optimize_adam(cost: CostVector, angles, steps: int, lr: float = 0.01, betas=
     _check(_lib.qaoa_optimize_adam(n, dt, ct.c_void_p(psi.data_ptr()), ct.c_void_p(lam.data_ptr()), ct.byref(cs),
                                    ct.c_void_p(angles.data_ptr()), p, steps, lr, betas[0], betas[1], eps,
                                    ct.c_void_p(hist.data_ptr() if hist is not None else 0),
+                                   ct.c_void_p(state.data_ptr() if state is not None else 0), int(resume),
                                    ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(_stream(angles.device))),
            "optimize_adam")
     return hist[:steps] if hist is not None else None
@@ -450,10 +466,11 @@ def batch_autotune(dtype: str = "c128", p: int = 3, n_lo: int = 8, n_hi: int = 2
 
 
 def optimize_lbfgs(cost: CostVector, angles, max_evals: int = 200, m: int = 10, gtol: float = 1e-6,
-                   dtype: str = "c128"):
+                   dtype: str = "c128", state=None, resume: bool = False):
     """L-BFGS ascent on <C>, on the device (graph replay; the host polls a stop flag every 16
     evaluations).  angles: float64 CUDA tensor [gamma, beta], updated in place to the best
-    accepted point.  Returns (history (evals x (4p + 2)) device tensor, info dict)."""
+    accepted point.  state / resume: see optimizer_state.  Returns (history of this call's
+    evaluations (rows x (4p + 2)) device tensor, info dict with running totals)."""
     torch = _torch()
     _require_cuda(angles)
     p = angles.numel() // 2
@@ -465,15 +482,17 @@ def optimize_lbfgs(cost: CostVector, angles, max_evals: int = 200, m: int = 10, 
     hist = torch.zeros((max(max_evals, 1), 4 * p + 2), dtype=torch.float64, device=angles.device)
     info = torch.zeros(4, dtype=torch.float64, device=angles.device)
     cs = cost.struct()
+    before = int(state[3].item()) if (resume and state is not None) else 0
     _check(_lib.qaoa_optimize_lbfgs(n, dt, ct.c_void_p(psi.data_ptr()), ct.c_void_p(lam.data_ptr()), ct.byref(cs),
                                     ct.c_void_p(angles.data_ptr()), p, max_evals, m, gtol,
                                     ct.c_void_p(hist.data_ptr()), ct.c_void_p(info.data_ptr()),
+                                    ct.c_void_p(state.data_ptr() if state is not None else 0), int(resume),
                                     ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(_stream(angles.device))),
            "optimize_lbfgs")
     i = info.cpu().numpy()
     res = {"E": float(i[0]), "iterations": int(i[1]), "evaluations": int(i[2]),
            "status": ("evaluations used up", "converged", "no progress")[int(i[3])]}
-    return hist[:res["evaluations"]], res
+    return hist[:res["evaluations"] - before], res
 
 
 def proposer_param_count(p: int) -> int:

@@ -153,10 +153,9 @@ static int cuda_status(cudaError_t e) { return e == cudaSuccess ? QAOA_OK : QAOA
 
 // Whether a sweep runs in a lean kernel: full tiles with affine layout-0 addresses
 // (t + c = B, c <= B - RB), groups of >= 3 qubits, the state loaded in the internal format
-// (complex64: also the caller's, which is the same) or created as |+>.  complex64 takes
-// the lean kernel for plain mixer sweeps only: its op-program and two-buffer forms measured
-// slower than the generic kernel on GB300 (register spills at 32 amplitudes per thread and
-// barrier stalls at 16 amplitudes and one block per SM).  A single mixer on
+// (complex64: also the caller's, which is the same) or created as |+>.  complex64 adjoint
+// (two-buffer) sweeps stay generic: their lean form spills at 32 amplitudes per thread per
+// buffer and measured slower on GB300.  A single mixer on
 // internal formats is the plain shape; any other program runs as an op program (its cost
 // tile by 16-byte copies, which need whole 16-byte chunks per row).
 static int lean_kind(const Sweep& s, const Group& g, int tile_bits, int dtype, bool cost_f64) {
@@ -182,7 +181,6 @@ static int lean_kind(const Sweep& s, const Group& g, int tile_bits, int dtype, b
   }
   const bool chunky = g.j0 == 0 || (1 << g.c) >= (cost_f64 ? 2 : 4);
   if (reads_c && !chunky) return SWEEP_GENERIC;
-  if (!fx) return SWEEP_GENERIC;
   return SWEEP_LEAN_OPS;
 }
 
@@ -818,11 +816,21 @@ int qaoa_gradient_dev(int n, int dtype, void* psi_dev, void* lambda_dev, const q
 }
 
 
+int qaoa_optimizer_state_size(int kind, int p, size_t* bytes) {
+  if (bytes == nullptr || p < 1 || p > QAOA_MAX_P) return QAOA_ERR_INVALID_ARG;
+  if (kind == QAOA_OPTIMIZER_ADAM) *bytes = (4 * (size_t)p + 1) * sizeof(double);
+  else if (kind == QAOA_OPTIMIZER_LBFGS) *bytes = lbfgs_state_doubles(p, QAOA_LBFGS_MAX_M) * sizeof(double);
+  else return QAOA_ERR_INVALID_ARG;
+  return QAOA_OK;
+}
+
 int qaoa_optimize_adam(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,
                        double* angles_dev, int p, int64_t steps, double lr, double beta1, double beta2, double eps,
-                       double* history_dev, void* ws_dev, size_t ws_bytes, void* stream) {
+                       double* history_dev, double* state_dev, int resume, void* ws_dev, size_t ws_bytes,
+                       void* stream) {
   if (angles_dev == nullptr || steps < 0 || !(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) ||
-      !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0) || p < 1 || p > QAOA_MAX_P || !valid_cost(cost))
+      !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0) || p < 1 || p > QAOA_MAX_P || !valid_cost(cost) ||
+      (resume != 0 && resume != 1) || (resume && state_dev == nullptr))
     return QAOA_ERR_INVALID_ARG;
   size_t need = 0;
   const int64_t span = (cost->dtype == QAOA_COST_I32 && cost->cmax >= cost->cmin) ? cost->cmax - cost->cmin + 1 : 0;
@@ -831,24 +839,33 @@ int qaoa_optimize_adam(int n, int dtype, void* psi_dev, void* lambda_dev, const 
   if (ws_dev == nullptr || ws_bytes < need) return QAOA_ERR_WORKSPACE;
   const size_t gbytes = need - adam_extra_bytes(p);
   char* extra = (char*)ws_dev + gbytes;
-  double* state = (double*)extra;
+  double* state = state_dev ? state_dev : (double*)extra;
   long long* counter = (long long*)(state + 4 * p);
   double* gout = (double*)(extra + round256((4 * p + 1) * sizeof(double)));
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemsetAsync(state, 0, (4 * p + 1) * sizeof(double), s) != cudaSuccess) return QAOA_ERR_CUDA;
+  long long row0 = 0;
+  if (resume) {  // history rows count from this call's first step
+    if (cudaMemcpyAsync(&row0, counter, sizeof(row0), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return QAOA_ERR_CUDA;
+  } else if (cudaMemsetAsync(state, 0, (4 * p + 1) * sizeof(double), s) != cudaSuccess) {
+    return QAOA_ERR_CUDA;
+  }
   return replay_steps(s, steps, [&](cudaStream_t cur) {
     int r = gradient_impl(n, dtype, psi_dev, lambda_dev, cost, nullptr, nullptr, angles_dev, p, gout, ws_dev, gbytes,
                           (void*)cur);
     if (r) return r;
-    return cuda_status(launch_adam(angles_dev, gout, state, counter, p, lr, beta1, beta2, eps, history_dev, steps, cur));
+    return cuda_status(
+        launch_adam(angles_dev, gout, state, counter, p, lr, beta1, beta2, eps, history_dev, row0, steps, cur));
   }, nullptr, 0);
 }
 
 int qaoa_optimize_lbfgs(int n, int dtype, void* psi_dev, void* lambda_dev, const qaoa_cost_t* cost,
                         double* angles_dev, int p, int64_t max_evals, int m, double gtol, double* history_dev,
-                        double* info_dev, void* ws_dev, size_t ws_bytes, void* stream) {
+                        double* info_dev, double* state_dev, int resume, void* ws_dev, size_t ws_bytes,
+                        void* stream) {
   if (angles_dev == nullptr || max_evals < 0 || m < 1 || m > QAOA_LBFGS_MAX_M || !(gtol >= 0.0) || p < 1 ||
-      p > QAOA_MAX_P || !valid_cost(cost))
+      p > QAOA_MAX_P || !valid_cost(cost) || (resume != 0 && resume != 1) || (resume && state_dev == nullptr))
     return QAOA_ERR_INVALID_ARG;
   size_t need = 0;
   const int64_t span = (cost->dtype == QAOA_COST_I32 && cost->cmax >= cost->cmin) ? cost->cmax - cost->cmin + 1 : 0;
@@ -857,16 +874,28 @@ int qaoa_optimize_lbfgs(int n, int dtype, void* psi_dev, void* lambda_dev, const
   if (ws_dev == nullptr || ws_bytes < need) return QAOA_ERR_WORKSPACE;
   const size_t gbytes = need - lbfgs_extra_bytes(p);
   char* extra = (char*)ws_dev + gbytes;
-  double* state = (double*)extra;
-  double* gout = (double*)(extra + round256(lbfgs_state_doubles(p, QAOA_LBFGS_MAX_M) * sizeof(double)));
+  const size_t nstate = lbfgs_state_doubles(p, QAOA_LBFGS_MAX_M);
+  double* state = state_dev ? state_dev : (double*)extra;
+  double* gout = (double*)(extra + round256(nstate * sizeof(double)));
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemsetAsync(state, 0, lbfgs_state_doubles(p, QAOA_LBFGS_MAX_M) * sizeof(double), s) != cudaSuccess)
+  long long row0 = 0;
+  if (resume) {
+    double scal[16];
+    if (cudaMemcpyAsync(scal, state, sizeof(scal), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return QAOA_ERR_CUDA;
+    row0 = (long long)scal[3];                // evaluations so far
+    if (scal[7] != 0.0) max_evals = 0;        // already finished: report only
+    rc = cuda_status(launch_lbfgs_resume(angles_dev, state, p, s));
+    if (rc) return rc;
+  } else if (cudaMemsetAsync(state, 0, nstate * sizeof(double), s) != cudaSuccess) {
     return QAOA_ERR_CUDA;
+  }
   rc = replay_steps(s, max_evals, [&](cudaStream_t cur) {
     int r = gradient_impl(n, dtype, psi_dev, lambda_dev, cost, nullptr, nullptr, angles_dev, p, gout, ws_dev, gbytes,
                           (void*)cur);
     if (r) return r;
-    return cuda_status(launch_lbfgs(angles_dev, gout, state, p, m, gtol, 1e-4, history_dev, max_evals, cur));
+    return cuda_status(launch_lbfgs(angles_dev, gout, state, p, m, gtol, 1e-4, history_dev, row0, max_evals, cur));
   }, state + 7, 16);
   if (rc) return rc;
   rc = cuda_status(launch_lbfgs_finish(angles_dev, state, p, info_dev, s));

@@ -121,10 +121,11 @@ cudaError_t launch_cost_bound(const void* C, int f64, int n, unsigned long long*
 cudaError_t launch_norm(const void* psi, int dtype, int n, double* partials, int* nblocks, cudaStream_t s);
 cudaError_t launch_angle_prep(const double* ang, int p, double* trig, cudaStream_t s);
 cudaError_t launch_adam(double* ang, const double* g, double* state, long long* step, int p, double lr, double b1,
-                        double b2, double eps, double* history, long long max_steps, cudaStream_t s);
+                        double b2, double eps, double* history, long long row0, long long max_rows, cudaStream_t s);
 size_t lbfgs_state_doubles(int p, int m);
 cudaError_t launch_lbfgs(double* ang, const double* gout, double* st, int p, int m, double gtol, double c1,
-                         double* history, long long max_rows, cudaStream_t s);
+                         double* history, long long row0, long long max_rows, cudaStream_t s);
+cudaError_t launch_lbfgs_resume(double* ang, const double* st, int p, cudaStream_t s);
 cudaError_t launch_lbfgs_finish(double* ang, const double* st, int p, double* info, cudaStream_t s);
 cudaError_t launch_expect(int dtype, const void* psi, const void* C, int cost_dtype, int n, double* partials,
                           int grid, cudaStream_t s);

@@ -50,7 +50,7 @@ __device__ double block_max(double v, double* red) {
 __global__ void __launch_bounds__(kLbThreads) lbfgs_kernel(double* __restrict__ ang, const double* __restrict__ gout,
                                                            double* __restrict__ st, int p, int m, double gtol,
                                                            double c1, double* __restrict__ history,
-                                                           long long max_rows) {
+                                                           long long row0, long long max_rows) {
   __shared__ double red[kLbThreads];
   __shared__ double al[QAOA_LBFGS_MAX_M];
   const int i = threadIdx.x, np2 = 2 * p;
@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(kLbThreads) lbfgs_kernel(double* __restrict__ 
   const long long ev = (long long)scal[SC_EVALS];
   int count = (int)scal[SC_COUNT], head = (int)scal[SC_HEAD];
   const int done = (int)scal[SC_DONE];
-  if (history != nullptr && ev < max_rows && done == 0) {
-    double* h = history + ev * (2 * np2 + 2);
+  if (history != nullptr && ev >= row0 && ev - row0 < max_rows && done == 0) {
+    double* h = history + (ev - row0) * (2 * np2 + 2);
     for (int k = i; k < np2 + 2; k += kLbThreads) h[k] = gout[k];
     if (on) h[np2 + 2 + i] = ang[i];
   }
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kLbThreads) lbfgs_kernel(double* __restrict__ 
     if (a < 1e-12) new_done = 2;
   }
   __syncthreads();
-  if (on) ang[i] = new_done ? x[i] : x[i] + new_alpha * d[i];
+  if (on) ang[i] = new_done ? x[i] : fma(new_alpha, d[i], x[i]);  // the resume kernel rounds the same way
   if (i == 0) {
     scal[SC_F] = new_f;
     scal[SC_ALPHA] = new_alpha;
@@ -167,6 +167,15 @@ __global__ void __launch_bounds__(kLbThreads) lbfgs_kernel(double* __restrict__ 
     scal[SC_COUNT] = count;
     scal[SC_HEAD] = head;
     scal[SC_DONE] = new_done;
+  }
+}
+
+// resuming: the evaluation point goes back to the trial the state machine expects next
+__global__ void lbfgs_resume_kernel(double* __restrict__ ang, const double* __restrict__ st, int p) {
+  const int i = threadIdx.x;
+  if (i < 2 * p && st[SC_EVALS] > 0 && st[SC_DONE] == 0) {
+    const double* x = st + 16;
+    ang[i] = fma(st[SC_ALPHA], x[4 * p + i], x[i]);  // d follows x and g
   }
 }
 
@@ -190,9 +199,16 @@ __global__ void lbfgs_finish_kernel(double* __restrict__ ang, const double* __re
 size_t lbfgs_state_doubles(int p, int m) { return 16 + 3 * (size_t)(2 * p) + 2 * (size_t)m * 2 * p + m; }
 
 cudaError_t launch_lbfgs(double* ang, const double* gout, double* st, int p, int m, double gtol, double c1,
-                         double* history, long long max_rows, cudaStream_t s) {
+                         double* history, long long row0, long long max_rows, cudaStream_t s) {
   note_launch(3, s, true);
-  lbfgs_kernel<<<1, kLbThreads, 0, s>>>(ang, gout, st, p, m, gtol, c1, history, max_rows);
+  lbfgs_kernel<<<1, kLbThreads, 0, s>>>(ang, gout, st, p, m, gtol, c1, history, row0, max_rows);
+  note_launch(3, s, false);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lbfgs_resume(double* ang, const double* st, int p, cudaStream_t s) {
+  note_launch(3, s, true);
+  lbfgs_resume_kernel<<<1, kLbThreads, 0, s>>>(ang, st, p);
   note_launch(3, s, false);
   return cudaGetLastError();
 }

@@ -430,12 +430,12 @@ __global__ void angle_prep_kernel(const double* __restrict__ ang, int p, double*
 // history[step * (4p + 2)] when history is non-null.
 __global__ void adam_kernel(double* __restrict__ ang, const double* __restrict__ g, double* __restrict__ state,
                             long long* __restrict__ step, int p, double lr, double b1, double b2, double eps,
-                            double* __restrict__ history, long long max_steps) {
+                            double* __restrict__ history, long long row0, long long max_rows) {
   const int i = threadIdx.x;
   const long long t = *step;  // completed steps before this one
   const int np2 = 2 * p;
-  if (history != nullptr && t < max_steps) {
-    double* h = history + t * (2 * np2 + 2);
+  if (history != nullptr && t >= row0 && t - row0 < max_rows) {
+    double* h = history + (t - row0) * (2 * np2 + 2);
     for (int k = i; k < np2 + 2; k += blockDim.x) h[k] = g[k];
     for (int k = i; k < np2; k += blockDim.x) h[np2 + 2 + k] = ang[k];
   }
@@ -702,9 +702,9 @@ cudaError_t launch_angle_prep(const double* ang, int p, double* trig, cudaStream
 }
 
 cudaError_t launch_adam(double* ang, const double* g, double* state, long long* step, int p, double lr, double b1,
-                        double b2, double eps, double* history, long long max_steps, cudaStream_t s) {
+                        double b2, double eps, double* history, long long row0, long long max_rows, cudaStream_t s) {
   note_launch(3, s, true);
-  adam_kernel<<<1, 128, 0, s>>>(ang, g, state, step, p, lr, b1, b2, eps, history, max_steps);
+  adam_kernel<<<1, 128, 0, s>>>(ang, g, state, step, p, lr, b1, b2, eps, history, row0, max_rows);
   note_launch(3, s, false);
   return cudaGetLastError();
 }

@@ -241,3 +241,40 @@ def test_lbfgs_200_evaluations_n24_p10():
     assert info["E"] > h[0, 0]
     assert np.all(np.abs(h[:, 1] - 1.0) <= 1e-10)
     assert q.launch_count() - launches0 < 60  # one direct evaluation, then graph replays
+
+
+def test_adam_checkpoint_resume_is_exact():
+    """12 steps, a checkpoint (angles + optimiser state to host and back), 8 more steps: the
+    same trajectory, bit for bit, as 20 uninterrupted steps."""
+    n, p = 10, 3
+    g, e, w, integer = instance(n, 12, prob=0.5)
+    cv = q.cost_vector(g, "f64")
+    ang0 = np.concatenate(synth.angles(p, 14))
+    a = torch.tensor(ang0, device="cuda")
+    full = q.optimize_adam(cv, a, 20, lr=0.03).cpu().numpy()
+    b = torch.tensor(ang0, device="cuda")
+    st = q.optimizer_state("adam", p)
+    h1 = q.optimize_adam(cv, b, 12, lr=0.03, state=st).cpu().numpy()
+    saved_ang, saved_st = b.cpu().numpy(), st.cpu().numpy()
+    b2, st2 = torch.tensor(saved_ang, device="cuda"), torch.tensor(saved_st, device="cuda")
+    h2 = q.optimize_adam(cv, b2, 8, lr=0.03, state=st2, resume=True).cpu().numpy()
+    assert np.array_equal(np.concatenate([h1, h2]), full)
+    assert np.array_equal(b2.cpu().numpy(), a.cpu().numpy())
+
+
+def test_lbfgs_checkpoint_resume_is_exact():
+    n, p = 10, 3
+    g, e, w, integer = instance(n, 13, prob=0.5)
+    cv = q.cost_vector(g, "f64")
+    ang0 = np.concatenate(synth.angles(p, 15))
+    a = torch.tensor(ang0, device="cuda")
+    full, info_full = q.optimize_lbfgs(cv, a, max_evals=30, m=6, gtol=1e-13)
+    b = torch.tensor(ang0, device="cuda")
+    st = q.optimizer_state("lbfgs", p)
+    h1, _ = q.optimize_lbfgs(cv, b, max_evals=14, m=6, gtol=1e-13, state=st)
+    saved_ang, saved_st = b.cpu().numpy(), st.cpu().numpy()
+    b2, st2 = torch.tensor(saved_ang, device="cuda"), torch.tensor(saved_st, device="cuda")
+    h2, info2 = q.optimize_lbfgs(cv, b2, max_evals=16, m=6, gtol=1e-13, state=st2, resume=True)
+    assert np.array_equal(np.concatenate([h1.cpu().numpy(), h2.cpu().numpy()]), full.cpu().numpy())
+    assert np.array_equal(b2.cpu().numpy(), a.cpu().numpy())
+    assert info2 == info_full
