@@ -153,14 +153,11 @@ static int cuda_status(cudaError_t e) { return e == cudaSuccess ? QAOA_OK : QAOA
 
 // Whether a sweep runs in a lean kernel: full tiles with affine layout-0 addresses
 // (t + c = B, c <= B - RB), groups of >= 3 qubits, the state loaded in the internal format
-// (complex64: also the caller's, which is the same) or created as |+>.  complex64 adjoint
-// (two-buffer) sweeps stay generic: their lean form spills at 32 amplitudes per thread per
-// buffer and measured slower on GB300.  A single mixer on
+// (complex64: also the caller's, which is the same) or created as |+>.  A single mixer on
 // internal formats is the plain shape; any other program runs as an op program (its cost
 // tile by 16-byte copies, which need whole 16-byte chunks per row).
 static int lean_kind(const Sweep& s, const Group& g, int tile_bits, int dtype, bool cost_f64) {
   const bool fx = dtype == QAOA_C128;
-  if (!fx && s.two) return SWEEP_GENERIC;
   const int rb = fx ? (s.two ? 3 : 4) : 5;
   if (g.t + g.c != tile_bits || g.c > tile_bits - rb || g.t < 3) return SWEEP_GENERIC;
   if (fx && s.load_user) return SWEEP_GENERIC;

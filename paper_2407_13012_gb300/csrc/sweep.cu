@@ -130,15 +130,19 @@ struct Lean : Sweeper<CF, FX, TWO> {
     fx_back<L>(lam);
   }
 
-  // ---- float32: RX(2 beta) butterflies round by round through layouts 0..L, then one
-  // exchange back to layout 0.  With X-terms (adjoint pass) each round's terms are taken
-  // on the exact state before its butterflies, so the per-qubit factors are applied at the
-  // end of every round; otherwise once at the end.
+  // ---- float32: RX(2 beta) = m (I - i u X) per qubit in tangent or cotangent form, as
+  // unit-free butterflies round by round through layouts 0..L; the factors m (or -i m) of
+  // all t qubits are applied once at the end, then one exchange returns to layout 0.
+  // X-terms (adjoint pass): psi and lambda carry the same factor c of the qubits already
+  // done, so Im conj(lambda) X_j psi of the unscaled buffers is |c|^2 = m^(2 done) times the
+  // true value; X_j commutes with every RX_i, so each round's terms may be taken just before
+  // its butterflies.
   template <int K>
-  __device__ __forceinline__ void f32_round(bool tanf, float tu, float m, bool xt, float& xs, int& pending) {
+  __device__ __forceinline__ void f32_round(bool tanf, float tu, float m2, bool xt, float& xs, float& w2) {
     if constexpr (!FX) {
       const unsigned msk = gmask<K>();
       if (xt) {
+        float part = 0.f;
 #pragma unroll
         for (int rb = 0; rb < CF::RB; ++rb) {
           if (!((msk >> rb) & 1u)) continue;
@@ -146,12 +150,13 @@ struct Lean : Sweeper<CF, FX, TWO> {
           for (int r = 0; r < R; ++r) {
             if (r & (1 << rb)) continue;
             const int q = r | (1 << rb);
-            xs += this->w[r].x * this->v[q].y - this->w[r].y * this->v[q].x + this->w[q].x * this->v[r].y -
-                  this->w[q].y * this->v[r].x;
+            part += this->w[r].x * this->v[q].y - this->w[r].y * this->v[q].x + this->w[q].x * this->v[r].y -
+                    this->w[q].y * this->v[r].x;
           }
         }
+        xs = fmaf(part, w2, xs);
+        for (unsigned b = msk; b; b &= b - 1) w2 *= m2;
       }
-      pending += __popc(msk);
       if (tanf) {
         this->template bf_round<true>(this->v, msk, tu);
         if constexpr (TWO) this->template bf_round<true>(this->w, msk, tu);
@@ -159,19 +164,13 @@ struct Lean : Sweeper<CF, FX, TWO> {
         this->template bf_round<false>(this->v, msk, tu);
         if constexpr (TWO) this->template bf_round<false>(this->w, msk, tu);
       }
-      if (xt && pending) {
-        const float2 f = B::round_factor(tanf, m, pending);
-        this->scale_f32(this->v, f);
-        if constexpr (TWO) this->scale_f32(this->w, f);
-        pending = 0;
-      }
     }
   }
   template <int K, int L>
-  __device__ __forceinline__ void f32_fwd(bool tanf, float tu, float m, bool xt, float& xs, int& pending) {
+  __device__ __forceinline__ void f32_fwd(bool tanf, float tu, float m2, bool xt, float& xs, float& w2) {
     if constexpr (K > 0) exb<K - 1, K>();
-    f32_round<K>(tanf, tu, m, xt, xs, pending);
-    if constexpr (K < L) f32_fwd<K + 1, L>(tanf, tu, m, xt, xs, pending);
+    f32_round<K>(tanf, tu, m2, xt, xs, w2);
+    if constexpr (K < L) f32_fwd<K + 1, L>(tanf, tu, m2, xt, xs, w2);
   }
   template <int L>
   __device__ __forceinline__ void f32_mixer(int layer, bool inverse, int xacc) {
@@ -182,14 +181,11 @@ struct Lean : Sweeper<CF, FX, TWO> {
       const float tu = tanf ? (float)(sbd / cbd) : (float)(cbd / sbd);
       const float m = tanf ? (float)cbd : (float)sbd;
       const bool xt = TWO && xacc >= 0;
-      float xs = 0.f;
-      int pending = 0;
-      f32_fwd<0, L>(tanf, tu, m, xt, xs, pending);
-      if (pending) {
-        const float2 f = B::round_factor(tanf, m, pending);
-        this->scale_f32(this->v, f);
-        if constexpr (TWO) this->scale_f32(this->w, f);
-      }
+      float xs = 0.f, w2 = 1.f;
+      f32_fwd<0, L>(tanf, tu, m * m, xt, xs, w2);
+      const float2 f = B::round_factor(tanf, m, this->a.g.t);
+      this->scale_f32(this->v, f);
+      if constexpr (TWO) this->scale_f32(this->w, f);
       if (xt) this->block_add(xacc, 2.0 * (double)xs, 0.0, false);
       if constexpr (L > 0) exb<L, 0>();
     }
