@@ -49,7 +49,7 @@ extern "C" {
 enum qaoa_status {
   QAOA_OK = 0,
   QAOA_ERR_INVALID_ARG = 1, /* bad pointer, size, graph or angle */
-  QAOA_ERR_UNSUPPORTED = 2, /* valid but outside this build's limits */
+  QAOA_ERR_UNSUPPORTED = 2, /* valid but outside the library's limits */
   QAOA_ERR_CUDA = 3,        /* CUDA launch / runtime error */
   QAOA_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
   QAOA_ERR_WORKSPACE = 5    /* ws_bytes smaller than qaoa_workspace_size() */

@@ -5,19 +5,15 @@
 // One CTA owns one graph at a time: it runs the graph's whole sweep plan over the graph's
 // own state buffers, tile after tile, with CTA barriers between sweeps, and writes the
 // graph's outputs from its block accumulators, so no launch boundary or cross-CTA reduction
-// separates the sweeps.  Graphs come off a work counter largest first, which balances the
+// separates the sweeps.  complex128 sweeps on full 2^12 tiles use the lean tile code
+// (compile-time layout sequences; forward sweeps on psi alone), the rest the generic
+// program (for complex64 the lean form spilled and measured slower).  Graphs come off a work counter largest first, which balances the
 // CTAs (longest-processing-time order).  Small graphs (n <= 10) run on 2^10-amplitude tiles,
 // larger ones on 2^12; the host may pick per qubit count from measured times.
-#include "sweeper.cuh"
+#include "batch_kernel.cuh"
 
 namespace qaoa {
 namespace {
-
-// complex128 (fixed point) and complex64 tiles for two buffers
-using CfgXB = Cfg<12, 3, 3, 3, 1>;
-using CfgXS = Cfg<10, 3, 3, 3, 2>;
-using CfgFB = Cfg<12, 4, 4, 4, 2>;
-using CfgFS = Cfg<10, 3, 3, 4, 2>;
 
 constexpr int kPrepThreads = 256;
 constexpr int kMaxBatchEdges = 512;
@@ -95,103 +91,13 @@ __global__ void __launch_bounds__(kPrepThreads) batch_prep_kernel(const __grid_c
 
 // The persistent kernel: graphs [first, first + count) of the processing order, taken from
 // *queue one at a time by each CTA.
-template <class CF, bool FX>
-__global__ void __launch_bounds__(CF::NT, CF::MINB) batch_kernel(const __grid_constant__ BatchArgs b, int first,
-                                                                int count, int* queue) {
-  using S = Sweeper<CF, FX, true>;
-  using V = typename S::V;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* X = (V*)smem_raw;
-  void* Cs = smem_raw + (sizeof(V) << CF::B);
-  __shared__ SweepArgs sa;
-  __shared__ double blk[kMaxAcc];
-  __shared__ double red[2 * (CF::NT / 32)];
-  __shared__ longlong2 dsm[16];
-  __shared__ int cur;
-  const int tid = threadIdx.x;
-  const int p = b.p;
-  const int nout = 2 * p + 2;
-  for (;;) {
-    __syncthreads();  // the previous graph is finished with cur, blk and sa
-    if (tid == 0) cur = atomicAdd(queue, 1);
-    for (int r = tid; r < nout; r += CF::NT) blk[r] = 0.0;
-    __syncthreads();
-    const int gi = cur;
-    if (gi >= count) break;
-    const int64_t gidx = first + gi;
-    const BatchGraph G = b.graphs[gidx];
-    const BatchPlan& P = b.plans[G.plan];
-    const size_t vs = sizeof(V);
-    for (int si = 0; si < P.nsweeps; ++si) {
-      const BatchSweep& bs = P.sw[si];
-      __syncthreads();  // the previous sweep's stores and its use of sa are complete
-      if (tid == 0) {
-        sa.kind = SWEEP_GENERIC;
-        sa.psi = (char*)b.psi + G.state * vs;
-        sa.lam = (char*)b.lam + G.state * vs;
-        sa.C = (const char*)b.C + G.cost * (b.cost_f64 ? 8 : 4);
-        sa.cost_dtype = b.cost_f64 ? QAOA_COST_F64 : QAOA_COST_I32;
-        sa.needs_cost = bs.needs_cost;
-        sa.g = bs.g;
-        sa.tile_bits = CF::B;
-        sa.load_fmt = bs.load_fmt;
-        sa.store_fmt = bs.store_fmt;
-        sa.load_lam = bs.load_lam;
-        sa.store_lam = bs.store_lam;
-        sa.init_fx = P.init_fx;
-        sa.init_f32 = P.init_f32;
-        sa.fx_shift = P.fx_shift;
-        sa.norm2_dev = nullptr;
-        sa.cmax_dev = nullptr;
-        sa.nops = bs.nops;
-        sa.dev_trig = b.trig + gidx * 3 * p;
-        sa.np = p;
-        sa.phase_table = G.span > 0 ? (const char*)b.phase + G.table * vs : nullptr;
-        sa.cmin = G.cmin;
-        sa.span = G.span;
-        sa.smem_table_layer = -1;
-        sa.d_table = FX ? (const char*)b.dtab + gidx * p * 196 * sizeof(longlong2) : nullptr;
-        sa.turn_table = b.turn;
-        sa.nred = 0;
-        sa.partials = nullptr;
-        sa.grid = 0;
-      }
-      for (int k = tid; k < bs.nops; k += CF::NT) sa.ops[k] = bs.ops[k];
-      __syncthreads();
-      S s(sa, X, Cs, blk, red);
-      s.Ds = dsm;
-      s.evalid = 1u << (bs.g.t + bs.g.c);
-      if constexpr (FX) s.lam_shift = G.lam_shift;
-      for (int64_t tile = 0; tile < bs.g.tiles; ++tile) sweep_tile<CF, FX, true, true>(s, sa, tile, Cs);
-    }
-    __syncthreads();  // block_add results are in blk
-    for (int r = tid; r < nout; r += CF::NT) b.out[(int64_t)G.out * nout + r] = blk[r];
-  }
-}
-
-template <class CF, bool FX>
-cudaError_t launch_batch_cfg(const BatchArgs& b, int first, int count, int* queue, cudaStream_t s) {
-  const size_t smem = (sizeof(typename Sweeper<CF, FX, true>::V) << CF::B) + ((size_t)(b.cost_f64 ? 8 : 4) << CF::B);
-  const size_t smem_max = (sizeof(typename Sweeper<CF, FX, true>::V) << CF::B) + ((size_t)8 << CF::B);
-  static bool attr = false;
-  static int per_sm = 1, sms = 1;
-  if (!attr) {
-    cudaFuncSetAttribute(batch_kernel<CF, FX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<CF, FX>, CF::NT, smem_max);
-    if (per_sm < 1) per_sm = 1;
-    attr = true;
-  }
-  const int grid = std::max(1, std::min(count, sms * per_sm));
-  batch_kernel<CF, FX><<<grid, CF::NT, smem, s>>>(b, first, count, queue);
-  return cudaGetLastError();
-}
-
 }  // namespace
 
 int batch_tile_bits(int tile) { return tile == 0 ? CfgXS::B : CfgXB::B; }
+int batch_register_bits(int dtype, int tile) {
+  if (tile == 0) return dtype == QAOA_C128 ? CfgXS::RB : CfgFS::RB;
+  return dtype == QAOA_C128 ? CfgXB::RB : CfgFB::RB;
+}
 
 cudaError_t launch_batch_prep(const BatchArgs& b, int64_t cost_blocks, cudaStream_t s) {
   const int64_t blocks = cost_blocks + b.ngraphs + 1;
@@ -206,11 +112,11 @@ cudaError_t launch_batch(const BatchArgs& b, int tile, int first, int count, int
   note_launch(0, s, true);
   cudaError_t e;
   if (b.dtype == QAOA_C128)
-    e = tile == 0 ? launch_batch_cfg<CfgXS, true>(b, first, count, queue, s)
-                  : launch_batch_cfg<CfgXB, true>(b, first, count, queue, s);
+    e = tile == 0 ? launch_batch_cfg<CfgXS, true, false>(b, first, count, queue, s)
+                  : launch_batch_c128_large(b, first, count, queue, s);
   else
-    e = tile == 0 ? launch_batch_cfg<CfgFS, false>(b, first, count, queue, s)
-                  : launch_batch_cfg<CfgFB, false>(b, first, count, queue, s);
+    e = tile == 0 ? launch_batch_cfg<CfgFS, false, false>(b, first, count, queue, s)
+                  : launch_batch_cfg<CfgFB, false, false>(b, first, count, queue, s);
   note_launch(0, s, false);
   return e;
 }

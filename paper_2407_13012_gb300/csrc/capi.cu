@@ -932,8 +932,36 @@ struct BatchLayout {
 
 int default_tile(int n) { return n <= 10 ? 0 : 1; }
 
+// last layout holding group qubits [c, c + t) on tiles of 2^B with RB register bits
+int last_layout(int B, int RB, int c, int t) {
+  const int nr = (B + RB - 1) / RB;
+  int last = 0;
+  for (int k = 0; k < nr; ++k) {
+    const int lo = std::max(0, B - RB * (k + 1)), hi = k == 0 ? B : std::max(0, B - RB * k);
+    if (hi > c && lo < c + t) last = k;
+  }
+  return last;
+}
+
+// Whether a batched sweep can run the lean tile code (complex128, 2^12 tiles): full tiles with
+// affine layout-0 addresses, groups of >= 3 qubits, whole 16-byte cost chunks per row, and
+// in two-buffer sweeps every op on psi alone before lambda exists (the lean code applies
+// mixers and phases to both buffers).
+int batch_lean_last(const Sweep& s, const Group& g, int B, int RB, bool fx, bool cost_f64) {
+  if (!fx || B != 12 || g.t + g.c != B || g.c > B - RB || g.t < 3) return -1;
+  bool reads_c = false, lam_live = s.two && s.load_lam;
+  for (uint32_t op : s.ops) {
+    const uint32_t kind = op & 0xff;
+    reads_c |= (kind == OP_PHASE || kind == OP_LAMBDA || kind == OP_RED_EXPECT || kind == OP_RED_CTERM);
+    if (s.two && (kind == OP_MIX || kind == OP_PHASE) && !(op & F_LAM) && lam_live) return -1;
+    if (kind == OP_LAMBDA) lam_live = true;
+  }
+  if (reads_c && !(g.j0 == 0 || (1 << g.c) >= (cost_f64 ? 2 : 4))) return -1;
+  return last_layout(B, RB, g.c, g.t);
+}
+
 // the gradient plan of n qubits on 2^B tiles, accumulators = output indices
-int batch_plan(int n, int B, int p, BatchPlan& P) {
+int batch_plan(int n, int B, int RB, bool fx, bool cost_f64, int p, BatchPlan& P) {
   std::memset(&P, 0, sizeof(P));
   const std::vector<Group> gs = plan_groups(n, B);
   std::vector<Sweep> sw;
@@ -958,6 +986,8 @@ int batch_plan(int n, int B, int p, BatchPlan& P) {
     b.store_fmt = (i == P.nsweeps - 1 || !s.store_psi) ? -1 : 0;
     b.load_lam = s.two && s.load_lam;
     b.store_lam = s.two && s.store_lam;
+    b.two = s.two;
+    b.lean_last = batch_lean_last(s, g, B, RB, fx, cost_f64);
     b.nops = (int)s.ops.size();
     for (int k = 0; k < b.nops; ++k) {
       b.ops[k] = s.ops[k];
@@ -1014,7 +1044,7 @@ int batch_layout(int dtype, int p, int ngraphs, const qaoa_graph_t* gs, const do
     G.out = i;
     if (plan_of[tile[i]][g.n] < 0) {
       BatchPlan P;
-      const int rc = batch_plan(g.n, batch_tile_bits(tile[i]), p, P);
+      const int rc = batch_plan(g.n, batch_tile_bits(tile[i]), batch_register_bits(dtype, tile[i]), fx, any_float, p, P);
       if (rc) return rc;
       plan_of[tile[i]][g.n] = (int)L.plans.size();
       L.plans.push_back(P);

@@ -196,6 +196,8 @@ constexpr int kBatchMaxSweeps = 32;  // sweeps per batched plan
 struct BatchSweep {
   SweepGeom g;
   int load_fmt, store_fmt, load_lam, store_lam, needs_cost, nops;
+  int two;        // the sweep carries lambda
+  int lean_last;  // >= 0: last layout with group qubits, for the lean tile code (2^12 tiles); -1: generic
   uint32_t ops[kBatchMaxOps];  // accumulator field = output index
 };
 
@@ -247,7 +249,9 @@ constexpr int kBatchCostBits = 12;  // cost-kernel entries per block: 2^12
 cudaError_t launch_batch_prep(const BatchArgs& b, int64_t cost_blocks, cudaStream_t s);
 // tile: 0 = small tiles (2^10 amplitudes), 1 = large tiles (2^12)
 cudaError_t launch_batch(const BatchArgs& b, int tile, int first, int count, int* queue, cudaStream_t s);
+cudaError_t launch_batch_c128_large(const BatchArgs& b, int first, int count, int* queue, cudaStream_t s);
 int batch_tile_bits(int tile);
+int batch_register_bits(int dtype, int tile);  // RB of the batched tile configuration
 
 // learned angle proposer (fused network inference, one CTA per graph)
 struct ProposeArgs {

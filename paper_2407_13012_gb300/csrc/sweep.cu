@@ -7,237 +7,12 @@ namespace qaoa {
 namespace {
 
 
-// ------------------------------------------------------------------ lean sweeps
-//
-// Sweeps on full tiles run in kernels whose layout sequence is fixed at compile time, so
-// each instance holds only the code it runs: a plain mixer sweep, and a sweep that runs its
-// op program (mixers, phases, lambda and reductions) with the same mixer code.  The host
-// checks the tile shape, the formats and the affine layout-0 addresses before choosing
-// them.
-
-template <class CF, bool FX, bool TWO>
-struct Lean : Sweeper<CF, FX, TWO> {
-  using B = Sweeper<CF, FX, TWO>;
-  using V = typename B::V;
-  static constexpr int R = CF::R, NR = CF::NR;
-  using B::B;
-
-  // group-qubit register bits of round K (relative to lo(K)), uniform
-  template <int K>
-  __device__ __forceinline__ unsigned gmask() const {
-    const int gl = this->a.g.c, gh = this->a.g.c + this->a.g.t;
-    unsigned m = 0;
-#pragma unroll
-    for (int rb = 0; rb < CF::RB; ++rb) {
-      const int b = CF::lo(K) + rb;
-      if (b < CF::newhi(K) && b >= gl && b < gh) m |= 1u << rb;
-    }
-    return m;
-  }
-  template <int F, int T>
-  __device__ __forceinline__ void exb() {
-    this->template ex<F, T>(this->v);
-    if constexpr (TWO) this->template ex<F, T>(this->w);
-    this->cur = T;
-  }
-  template <int K>
-  __device__ __forceinline__ uint32_t ix(int r) const { return CF::idx(K, this->tid, r); }
-
-  // ---- fixed point: W rounds, D multiply (and X-term) at layout L
-  __device__ __forceinline__ void wht_mask(V (&u)[R], unsigned m) {
-    if constexpr (FX) {
-      if (m & 1u) this->template wht_bit<0>(u);
-      if constexpr (CF::RB > 1) if (m & 2u) this->template wht_bit<(CF::RB > 1 ? 1 : 0)>(u);
-      if constexpr (CF::RB > 2) if (m & 4u) this->template wht_bit<(CF::RB > 2 ? 2 : 0)>(u);
-      if constexpr (CF::RB > 3) if (m & 8u) this->template wht_bit<(CF::RB > 3 ? 3 : 0)>(u);
-      if constexpr (CF::RB > 4) if (m & 16u) this->template wht_bit<(CF::RB > 4 ? 4 : 0)>(u);
-    }
-  }
-  template <int K>
-  __device__ __forceinline__ void wht_k(bool lam) {
-    const unsigned m = gmask<K>();
-    wht_mask(this->v, m);
-    if constexpr (TWO) if (lam) wht_mask(this->w, m);
-  }
-  template <int K, int L>
-  __device__ __forceinline__ void fx_fwd(bool lam) {
-    if constexpr (K > 0) exb<K - 1, K>();
-    wht_k<K>(lam);
-    if constexpr (K < L) fx_fwd<K + 1, L>(lam);
-  }
-  template <int K>
-  __device__ __forceinline__ void fx_back(bool lam) {
-    wht_k<K>(lam);
-    if constexpr (K > 0) {
-      exb<K, K - 1>();
-      fx_back<K - 1>(lam);
-    }
-  }
-  template <int L, bool BIG>
-  __device__ __forceinline__ void dmul_l(V (&u)[R], int gl, int t) {
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const longlong2 e = this->Ds[__popc((ix<L>(r) >> gl) & ((1u << t) - 1))];
-      fx::C64 o;
-      if constexpr (BIG) {
-        const fx::Limbs xr = fx::split(u[r].x), xi = fx::split(u[r].y), nxi = fx::split(-u[r].y);
-        const fx::Limbs er = fx::split(e.x), ei = fx::split(e.y);
-        o.x = fx::dot2_q62(xr, er, nxi, ei, t);
-        o.y = fx::dot2_q62(xr, ei, xi, er, t);
-      } else {
-        o = fx::cmul_q62(u[r].x, u[r].y, e.x, e.y, t);
-      }
-      u[r] = make_longlong2(o.x, o.y);
-    }
-  }
-  // W D W from layout 0 back to layout 0; D at layout L (the last round with group qubits)
-  template <int L>
-  __device__ __forceinline__ void fx_mixer(int layer, bool inverse, bool lam, int xacc) {
-    const int gl = this->a.g.c, t = this->a.g.t;
-    __syncthreads();
-    if (this->tid <= (uint32_t)t) {
-      longlong2 e = __ldg((const longlong2*)this->a.d_table + ((long long)layer * 14 + t) * 14 + this->tid);
-      if (inverse) e.y = -e.y;
-      this->Ds[this->tid] = e;
-    }
-    fx_fwd<0, L>(lam);
-    __syncthreads();
-    if constexpr (TWO) {
-      if (xacc >= 0) {
-        i128 xs = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int pc = __popc((ix<L>(r) >> gl) & ((1u << t) - 1));
-          const i128 pr = (i128)this->w[r].x * this->v[r].y - (i128)this->w[r].y * this->v[r].x;
-          xs += (pr >> 32) * (t - 2 * pc);
-        }
-        this->block_add(xacc, 2.0 * i128_to_double(xs, 2 * this->a.fx_shift + t - 32 - this->lam_shift), 0.0, false);
-      }
-    }
-    // lean sweeps run only on groups of >= 3 qubits, so the shift form of the multiply
-    // applies; the two-buffer kernels keep the branch (it schedules better there)
-    if constexpr (TWO) {
-      if (t >= 3) {
-        dmul_l<L, true>(this->v, gl, t);
-        if (lam) dmul_l<L, true>(this->w, gl, t);
-      } else {
-        dmul_l<L, false>(this->v, gl, t);
-        if (lam) dmul_l<L, false>(this->w, gl, t);
-      }
-    } else {
-      dmul_l<L, true>(this->v, gl, t);
-    }
-    fx_back<L>(lam);
-  }
-
-  // ---- float32: RX(2 beta) = m (I - i u X) per qubit in tangent or cotangent form, as
-  // unit-free butterflies round by round through layouts 0..L; the factors m (or -i m) of
-  // all t qubits are applied once at the end, then one exchange returns to layout 0.
-  // X-terms (adjoint pass): psi and lambda carry the same factor c of the qubits already
-  // done, so Im conj(lambda) X_j psi of the unscaled buffers is |c|^2 = m^(2 done) times the
-  // true value; X_j commutes with every RX_i, so each round's terms may be taken just before
-  // its butterflies.
-  template <int K>
-  __device__ __forceinline__ void f32_round(bool tanf, float tu, float m2, bool xt, float& xs, float& w2) {
-    if constexpr (!FX) {
-      const unsigned msk = gmask<K>();
-      if (xt) {
-        float part = 0.f;
-#pragma unroll
-        for (int rb = 0; rb < CF::RB; ++rb) {
-          if (!((msk >> rb) & 1u)) continue;
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            if (r & (1 << rb)) continue;
-            const int q = r | (1 << rb);
-            part += this->w[r].x * this->v[q].y - this->w[r].y * this->v[q].x + this->w[q].x * this->v[r].y -
-                    this->w[q].y * this->v[r].x;
-          }
-        }
-        xs = fmaf(part, w2, xs);
-        for (unsigned b = msk; b; b &= b - 1) w2 *= m2;
-      }
-      if (tanf) {
-        this->template bf_round<true>(this->v, msk, tu);
-        if constexpr (TWO) this->template bf_round<true>(this->w, msk, tu);
-      } else {
-        this->template bf_round<false>(this->v, msk, tu);
-        if constexpr (TWO) this->template bf_round<false>(this->w, msk, tu);
-      }
-    }
-  }
-  template <int K, int L>
-  __device__ __forceinline__ void f32_fwd(bool tanf, float tu, float m2, bool xt, float& xs, float& w2) {
-    if constexpr (K > 0) exb<K - 1, K>();
-    f32_round<K>(tanf, tu, m2, xt, xs, w2);
-    if constexpr (K < L) f32_fwd<K + 1, L>(tanf, tu, m2, xt, xs, w2);
-  }
-  template <int L>
-  __device__ __forceinline__ void f32_mixer(int layer, bool inverse, int xacc) {
-    if constexpr (!FX) {
-      const double cbd = arg_cosb(this->a, layer);
-      const double sbd = inverse ? -arg_sinb(this->a, layer) : arg_sinb(this->a, layer);
-      const bool tanf = fabs(cbd) >= fabs(sbd);
-      const float tu = tanf ? (float)(sbd / cbd) : (float)(cbd / sbd);
-      const float m = tanf ? (float)cbd : (float)sbd;
-      const bool xt = TWO && xacc >= 0;
-      float xs = 0.f, w2 = 1.f;
-      f32_fwd<0, L>(tanf, tu, m * m, xt, xs, w2);
-      const float2 f = B::round_factor(tanf, m, this->a.g.t);
-      this->scale_f32(this->v, f);
-      if constexpr (TWO) this->scale_f32(this->w, f);
-      if (xt) this->block_add(xacc, 2.0 * (double)xs, 0.0, false);
-      if constexpr (L > 0) exb<L, 0>();
-    }
-  }
-  template <int L>
-  __device__ __forceinline__ void mixer(int layer, bool inverse, int xacc) {
-    if constexpr (FX) fx_mixer<L>(layer, inverse, TWO, xacc);
-    else f32_mixer<L>(layer, inverse, xacc);
-  }
-
-  // ---- the sweep: one mixer (OPS = false), or the sweep's op program (OPS = true) with
-  // every mixer on the compile-time layout sequence and the elementwise ops in layout 0;
-  // L = last round with group qubits
-  template <int L, bool OPS>
-  __device__ __forceinline__ void run() {
-    const uint32_t* ops = this->a.ops;
-    if constexpr (!OPS) {
-      const uint32_t o = ops[0];
-      mixer<L>((o >> 16) & 0xff, o & F_SIGN, (o & F_XTERM) ? (int)((o >> 24) & 0xff) : -1);
-    } else {
-      // one copy of the mixer code for every mixer of the program keeps the kernel within
-      // the instruction cache.  Two-buffer kernels apply mixers and phases to both buffers:
-      // an op on psi alone only occurs while lambda is still zero (the host checks that).
-#pragma unroll 1
-      for (int k = 0; k < this->a.nops; ++k) {
-        const uint32_t op = ops[k];
-        const uint32_t kind = op & 0xff;
-        const int layer = (op >> 16) & 0xff, acc = (int)((op >> 24) & 0xff);
-        const bool inv = op & F_SIGN;
-        if (kind == OP_MIX) {
-          mixer<L>(layer, inv, (op & F_XTERM) ? acc : -1);
-        } else if (kind == OP_PHASE) {
-          this->op_phase(layer, inv, true, TWO);
-        } else if (kind == OP_LAMBDA) {
-          if constexpr (TWO) this->op_lambda();
-        } else if (kind == OP_RED_EXPECT) {
-          this->op_expect(acc);
-        } else if (kind == OP_RED_CTERM) {
-          if constexpr (TWO) this->op_cterm(acc);
-        }
-      }
-    }
-  }
-};
-
 // Lean sweeps: full tiles, affine layout-0 addresses, state loaded in the internal format
 // or created as |+>, stored in the internal or the caller's format (complex64: the same).
 template <class CF, bool FX, bool TWO, bool OPS, int LAST>
 __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_constant__ SweepArgs a) {
   using S = Lean<CF, FX, TWO>;
   using V = typename S::V;
-  constexpr int R = CF::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* X = (V*)smem_raw;
   void* Cs = smem_raw + (sizeof(V) << CF::B);
@@ -248,8 +23,6 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
   __shared__ longlong2 dsm[16];
   for (int r = threadIdx.x; r < kMaxAcc; r += CF::NT) blk[r] = 0.0;
   S s(a, X, Cs, blk, red);
-  V (&v)[R] = s.v;
-  V (&w)[R] = s.w;
   s.Ds = dsm;
   if (OPS && a.smem_table_layer >= 0) {
     const V* src = (const V*)a.phase_table + (long long)a.smem_table_layer * a.span;
@@ -257,7 +30,6 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
     s.Ts = Tsm;
     s.ts_layer = a.smem_table_layer;
   }
-  const SweepGeom& g = a.g;
   s.evalid = 1u << CF::B;
   if constexpr (FX && TWO) {
     if (a.cmax_dev != nullptr) {
@@ -267,55 +39,9 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
       s.lam_shift = k < 0 ? 0 : k;
     }
   }
-  const uint32_t tid = threadIdx.x;
-  const bool cf64 = a.cost_dtype == QAOA_COST_F64;
-  const uint32_t tb0 = CF::idx(0, tid, 0);
-  const uint64_t zs = 1ull << (CF::lo(0) - g.c + g.j0);
-  const bool init = OPS && a.load_fmt == 2;
-  const bool ld_lam = TWO && (!OPS || a.load_lam), st_lam = TWO && (!OPS || a.store_lam);
-  const int st_fmt = OPS ? a.store_fmt : 0;
   __syncthreads();
-  for (int64_t tile = blockIdx.x; tile < g.tiles; tile += gridDim.x) {
-    const uint64_t base = tile_base(g, tile);
-    s.base = base;
-    s.cur = 0;
-    if (cost) {  // cost tile, 16-byte asynchronous copies
-      __syncthreads();
-      const int per = cf64 ? 2 : 4;
-      const uint32_t nch = (1u << CF::B) / per;
-      for (uint32_t ch = tid; ch < nch; ch += CF::NT) {
-        const uint32_t i = ch * per;
-        const uint64_t z = local_to_z(g, base, i);
-        cp_async16((char*)Cs + (size_t)phys_cost(i, cf64) * (cf64 ? 8 : 4), (const char*)a.C + z * (cf64 ? 8 : 4));
-      }
-    }
-    const uint64_t z0 = local_to_z(g, base, tb0);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const uint64_t z = z0 + (uint64_t)r * zs;
-      if constexpr (FX) v[r] = init ? make_longlong2(a.init_fx, 0) : __ldg((const V*)a.psi + z);
-      else v[r] = init ? make_float2(a.init_f32, 0.f) : __ldg((const V*)a.psi + z);
-      if constexpr (TWO) w[r] = ld_lam ? __ldg((const V*)a.lam + z) : V{};
-    }
-    if (cost) {
-      cp_async_wait_all();
-      __syncthreads();
-    }
-    s.template run<LAST, OPS>();
-    const uint64_t z1 = local_to_z(g, base, tb0);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const uint64_t z = z1 + (uint64_t)r * zs;
-      if constexpr (FX) {
-        if (st_fmt == 0) ((V*)a.psi)[z] = v[r];
-        else if (st_fmt == 1)
-          ((double2*)a.psi)[z] = make_double2(fx_to_double(v[r].x, a.fx_shift), fx_to_double(v[r].y, a.fx_shift));
-      } else {
-        if (st_fmt >= 0) ((V*)a.psi)[z] = v[r];
-      }
-      if (st_lam) ((V*)a.lam)[z] = w[r];
-    }
-  }
+  for (int64_t tile = blockIdx.x; tile < a.g.tiles; tile += gridDim.x)
+    lean_tile<CF, FX, TWO, OPS, LAST, false>(s, a, tile, Cs);
   __syncthreads();
   for (int r = threadIdx.x; r < a.nred; r += CF::NT)
     a.partials[(int64_t)a.red_slot[r] * a.grid + blockIdx.x] = blk[r];
