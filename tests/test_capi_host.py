@@ -196,3 +196,21 @@ def test_pubo_rejections(case):
     rc = q.lib.qaoa_cost_vector_pubo(n, len(m), mp, wa.ctypes.data_as(ct.POINTER(ct.c_double)), kind,
                                      ct.c_void_p(256), cdt, ct.byref(desc), None)
     assert rc == q.QAOA_ERR_INVALID_ARG
+
+
+def test_optimizer_state_sizes_and_resume_checks():
+    size = ct.c_size_t()
+    assert q.lib.qaoa_optimizer_state_size(q.OPTIMIZER_ADAM, 4, ct.byref(size)) == 0
+    assert size.value == (4 * 4 + 1) * 8
+    assert q.lib.qaoa_optimizer_state_size(q.OPTIMIZER_LBFGS, 4, ct.byref(size)) == 0
+    m, np2 = q.LBFGS_MAX_M, 8
+    assert size.value == (16 + 3 * np2 + 2 * m * np2 + m) * 8
+    assert q.lib.qaoa_optimizer_state_size(7, 4, ct.byref(size)) == q.QAOA_ERR_INVALID_ARG
+    assert q.lib.qaoa_optimizer_state_size(q.OPTIMIZER_ADAM, 0, ct.byref(size)) == q.QAOA_ERR_INVALID_ARG
+    # resume without a state buffer is refused on the host
+    cost = q.CostT(256, q.COST_F64, 1, 0)
+    ang = ct.c_void_p(512)
+    assert q.lib.qaoa_optimize_adam(8, q.C128, None, None, ct.byref(cost), ang, 2, 5, 0.01, 0.9, 0.999, 1e-8,
+                                    None, None, 1, None, 0, None) == q.QAOA_ERR_INVALID_ARG
+    assert q.lib.qaoa_optimize_lbfgs(8, q.C128, None, None, ct.byref(cost), ang, 2, 5, 4, 1e-6, None, None,
+                                     None, 1, None, 0, None) == q.QAOA_ERR_INVALID_ARG
