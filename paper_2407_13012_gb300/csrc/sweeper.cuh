@@ -839,12 +839,41 @@ struct Lean : Sweeper<CF, FX, TWO> {
   __device__ __forceinline__ uint32_t ix(int r) const { return CF::idx(K, this->tid, r); }
 
   // ---- fixed point: W rounds, D multiply (and X-term) at layout L
+  // two Walsh-Hadamard rounds on register bits B0 and B1 at once: for each quadruple
+  // (x0, x1, x2, x3) = u[r], u[r | b0], u[r | b1], u[r | b0 | b1] the outputs are
+  // (x0 + x1) +- (x2 + x3) and (x0 - x1) +- (x2 - x3), written as three-input sums
+  template <int B0, int B1>
+  __device__ __forceinline__ void wht_bit2(V (&u)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (r & ((1 << B0) | (1 << B1))) continue;
+      const int q1 = r | (1 << B0), q2 = r | (1 << B1), q3 = q1 | q2;
+      const longlong2 x0 = u[r], x1 = u[q1], x2 = u[q2], x3 = u[q3];
+      const long long a0x = x0.x + x1.x, a0y = x0.y + x1.y, a1x = x0.x - x1.x, a1y = x0.y - x1.y;
+      u[r] = make_longlong2(a0x + x2.x + x3.x, a0y + x2.y + x3.y);
+      u[q2] = make_longlong2(a0x - x2.x - x3.x, a0y - x2.y - x3.y);
+      u[q1] = make_longlong2(a1x + x2.x - x3.x, a1y + x2.y - x3.y);
+      u[q3] = make_longlong2(a1x - x2.x + x3.x, a1y - x2.y + x3.y);
+    }
+  }
   __device__ __forceinline__ void wht_mask(V (&u)[R], unsigned m) {
     if constexpr (FX) {
-      if (m & 1u) this->template wht_bit<0>(u);
-      if constexpr (CF::RB > 1) if (m & 2u) this->template wht_bit<(CF::RB > 1 ? 1 : 0)>(u);
-      if constexpr (CF::RB > 2) if (m & 4u) this->template wht_bit<(CF::RB > 2 ? 2 : 0)>(u);
-      if constexpr (CF::RB > 3) if (m & 8u) this->template wht_bit<(CF::RB > 3 ? 3 : 0)>(u);
+      if (CF::RB > 1 && (m & 3u) == 3u) {
+        this->template wht_bit2<0, (CF::RB > 1 ? 1 : 0)>(u);
+      } else {
+        if (m & 1u) this->template wht_bit<0>(u);
+        if constexpr (CF::RB > 1) if (m & 2u) this->template wht_bit<(CF::RB > 1 ? 1 : 0)>(u);
+      }
+      if constexpr (CF::RB > 3) {
+        if ((m & 12u) == 12u) {
+          this->template wht_bit2<(CF::RB > 3 ? 2 : 0), (CF::RB > 3 ? 3 : 0)>(u);
+        } else {
+          if (m & 4u) this->template wht_bit<(CF::RB > 2 ? 2 : 0)>(u);
+          if (m & 8u) this->template wht_bit<(CF::RB > 3 ? 3 : 0)>(u);
+        }
+      } else if constexpr (CF::RB > 2) {
+        if (m & 4u) this->template wht_bit<(CF::RB > 2 ? 2 : 0)>(u);
+      }
       if constexpr (CF::RB > 4) if (m & 16u) this->template wht_bit<(CF::RB > 4 ? 4 : 0)>(u);
     }
   }
