@@ -502,8 +502,8 @@ struct Sweeper {
       if constexpr (BIG) {
         const fx::Limbs xr = fx::split(u[r].x), xi = fx::split(u[r].y), nxi = fx::split(-u[r].y);
         const fx::Limbs er = fx::split(e.x), ei = fx::split(e.y);
-        o.x = fx::dot2_q62(xr, er, nxi, ei, t);
-        o.y = fx::dot2_q62(xr, ei, xi, er, t);
+        o.x = fx::dot2_q62_hi(xr, er, nxi, ei, t);
+        o.y = fx::dot2_q62_hi(xr, ei, xi, er, t);
       } else {
         o = fx::cmul_q62(u[r].x, u[r].y, e.x, e.y, t);
       }
@@ -906,8 +906,8 @@ struct Lean : Sweeper<CF, FX, TWO> {
       if constexpr (BIG) {
         const fx::Limbs xr = fx::split(u[r].x), xi = fx::split(u[r].y), nxi = fx::split(-u[r].y);
         const fx::Limbs er = fx::split(e.x), ei = fx::split(e.y);
-        o.x = fx::dot2_q62(xr, er, nxi, ei, t);
-        o.y = fx::dot2_q62(xr, ei, xi, er, t);
+        o.x = fx::dot2_q62_hi(xr, er, nxi, ei, t);
+        o.y = fx::dot2_q62_hi(xr, ei, xi, er, t);
       } else {
         o = fx::cmul_q62(u[r].x, u[r].y, e.x, e.y, t);
       }

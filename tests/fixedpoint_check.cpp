@@ -40,6 +40,22 @@ int main() {
     printf("cmul exact rate too low: %lld / %lld\n", exact, total);
     ++fails;
   }
+  // the mixer-diagonal form without low-limb products: within one unit for e >= 3
+  for (int it = 0; it < 1000000; ++it) {
+    const int bits = 1 + (int)(rng() % 61);
+    const long long lim = (1ll << bits) - 1;
+    const long long xr = (long long)(rng() % (2 * (unsigned long long)lim + 1)) - lim;
+    const long long xi = (long long)(rng() % (2 * (unsigned long long)lim + 1)) - lim;
+    const double th = ang(rng);
+    const long long ur = q62(std::cos(th)), ui = q62(std::sin(th));
+    const int e = 3 + (int)(rng() % 11);
+    const C64 a = cmul_q62_hi(xr, xi, ur, ui, e);
+    const C64 b = cmul_q62_exact(xr, xi, ur, ui, e);
+    const long long dx = a.x - b.x, dy = a.y - b.y;
+    if (dx > 1 || dx < -1 || dy > 1 || dy < -1) {
+      if (fails++ < 10) printf("cmul_hi mismatch e=%d: %lld %lld vs %lld %lld\n", e, a.x, a.y, b.x, b.y);
+    }
+  }
   for (int it = 0; it < 1000000; ++it) {
     const long long x = (long long)(rng() >> (rng() % 63)) * ((rng() & 1) ? 1 : -1);
     const int s = (int)(rng() % 120);
