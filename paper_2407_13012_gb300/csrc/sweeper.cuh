@@ -329,7 +329,48 @@ struct Sweeper {
     }
   }
 
+  // the same factors on psi and lambda: looked up (or computed) once per amplitude
+  template <bool INV>
+  __device__ __forceinline__ void phase_apply2(int layer) {
+    const bool f64 = a.cost_dtype == QAOA_COST_F64;
+    unsigned miss = 0;
+    if (!f64 && a.phase_table != nullptr) {
+      const V* tab = layer == ts_layer ? Ts : (const V*)a.phase_table + (long long)layer * a.span;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const long long k = (long long)cost_i(Cs, idx(r)) - a.cmin;
+        if (k >= 0 && k < a.span) {
+          V e = tab[k];
+          if constexpr (INV) e.y = -e.y;
+          v[r] = vmul(v[r], e);
+          w[r] = vmul(w[r], e);
+        } else {
+          miss |= 1u << r;
+        }
+      }
+    } else {
+      miss = R == 32 ? 0xffffffffu : ((1u << R) - 1);
+    }
+    if (miss) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        if (!((miss >> r) & 1u)) continue;
+        V e = phase_direct(layer, cost_f(Cs, f64, idx(r)));
+        if constexpr (INV) e.y = -e.y;
+        v[r] = vmul(v[r], e);
+        w[r] = vmul(w[r], e);
+      }
+    }
+  }
+
   __device__ __forceinline__ void op_phase(int layer, bool inverse, bool on_psi, bool on_lam) {
+    if constexpr (TWO) {
+      if (on_psi && on_lam) {
+        if (inverse) phase_apply2<true>(layer);
+        else phase_apply2<false>(layer);
+        return;
+      }
+    }
     if (inverse) {
       if (on_psi) phase_apply<true>(v, layer);
       if (TWO && on_lam) phase_apply<true>(w, layer);
