@@ -200,6 +200,26 @@ def test_large_p1_against_closed_form(n, dtype):
     torch.cuda.empty_cache()
 
 
+def test_n31_complex128_p1_and_p2_invariants():
+    """The largest complex128 size (34 GB state): G(31, 0.1), U(0,1) weights.  p = 1 against
+    the closed form; p = 2 keeps the norm and, with beta_2 shifted by pi/2 (RX(pi) = -iX on
+    every qubit, which commutes with C's bit-flip symmetry), the same <C>."""
+    n = 31
+    g, e, w, integer = instance("gnp", n, 4, "u01", prob=0.1)
+    cv = q.cost_vector(g, "f64")
+    gam, bet = synth.angles(2, 6)
+    psi = q.new_state(n, "c128")
+    out = to_np(q.apply_layers(psi, cv, gam[:1], bet[:1], expect=True))
+    ref = closed_form.expectation_p1(n, e, w, gam[0], bet[0])
+    assert abs(out[0] - ref) <= 1e-10 * scale_of(w) and abs(out[1] - 1.0) <= 1e-12
+    a = to_np(q.apply_layers(psi, cv, gam, bet, expect=True))
+    b = to_np(q.apply_layers(psi, cv, gam, bet + np.array([0.0, np.pi / 2]), expect=True))
+    assert abs(a[1] - 1.0) <= 1e-12 and abs(b[1] - 1.0) <= 1e-12
+    assert abs(a[0] - b[0]) <= 1e-10 * scale_of(w)
+    del psi, cv
+    torch.cuda.empty_cache()
+
+
 # ------------------------------------------------------------------ S5-S6 sampling
 
 def upload(psi_ref, dtype):
