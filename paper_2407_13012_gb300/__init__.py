@@ -169,7 +169,9 @@ _ws_cache: dict = {}
 
 
 def _workspace(nbytes: int, device):
-    """A cached device scratch buffer of at least nbytes (torch-allocated)."""
+    """A cached device scratch buffer of at least nbytes (torch-allocated).  One buffer per
+    device serves every call of this binding on that device, so those calls must be ordered
+    on one stream (the current stream, which the binding uses throughout)."""
     torch = _torch()
     key = torch.device(device).index if torch.device(device).index is not None else torch.cuda.current_device()
     buf = _ws_cache.get(key)

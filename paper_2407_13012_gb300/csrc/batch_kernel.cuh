@@ -124,17 +124,17 @@ template <class CF, bool FX, bool LEAN>
 cudaError_t launch_batch_cfg(const BatchArgs& b, int first, int count, int* queue, cudaStream_t s) {
   const size_t smem = (sizeof(typename Sweeper<CF, FX, true>::V) << CF::B) + ((size_t)(b.cost_f64 ? 8 : 4) << CF::B);
   const size_t smem_max = (sizeof(typename Sweeper<CF, FX, true>::V) << CF::B) + ((size_t)8 << CF::B);
-  static bool attr = false;
+  static std::mutex mu;
+  static uint64_t done = 0;
   static int per_sm = 1, sms = 1;
-  if (!attr) {
+  once_per_device(mu, done, [&] {
     cudaFuncSetAttribute(batch_kernel<CF, FX, LEAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<CF, FX, LEAN>, CF::NT, smem_max);
     if (per_sm < 1) per_sm = 1;
-    attr = true;
-  }
+  });
   const int grid = std::max(1, std::min(count, sms * per_sm));
   batch_kernel<CF, FX, LEAN><<<grid, CF::NT, smem, s>>>(b, first, count, queue);
   return cudaGetLastError();

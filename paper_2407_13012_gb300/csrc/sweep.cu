@@ -237,13 +237,13 @@ size_t smem_bytes(int cost_bytes, int table_entries = 0) {
 template <class CF, bool FX, bool TWO>
 int blocks_per_sm(int cost_bytes) {
   static int cached[3] = {0, 0, 0};
-  static bool attr = false;
+  static std::mutex mu;
+  static uint64_t done = 0;
   const int slot = cost_bytes == 0 ? 0 : (cost_bytes == 4 ? 1 : 2);
-  if (!attr) {
+  once_per_device(mu, done, [] {
     cudaFuncSetAttribute(sweep_kernel<CF, FX, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem_bytes<CF, FX, TWO>(8, kSmemTable));
-    attr = true;
-  }
+  });
   if (!cached[slot]) {
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<CF, FX, TWO>, CF::NT,
@@ -255,12 +255,12 @@ int blocks_per_sm(int cost_bytes) {
 
 template <class CF, bool FX, bool TWO, bool OPS, int LAST>
 void lean_launch_l(const SweepArgs& a, size_t sm, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  static std::mutex mu;
+  static uint64_t done = 0;
+  once_per_device(mu, done, [] {
     cudaFuncSetAttribute(lean_kernel<CF, FX, TWO, OPS, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem_bytes<CF, FX, TWO>(8, kSmemTable));
-    attr = true;
-  }
+  });
   lean_kernel<CF, FX, TWO, OPS, LAST><<<a.grid, CF::NT, sm, s>>>(a);
 }
 template <class CF, bool FX, bool TWO, bool OPS>

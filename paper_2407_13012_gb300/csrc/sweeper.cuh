@@ -31,6 +31,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
+#include <mutex>
 #include <type_traits>
 
 #include "fixedpoint.cuh"
@@ -38,6 +40,20 @@
 namespace qaoa {
 namespace {
 
+
+// Kernel attributes (the dynamic shared-memory limit) belong to a device: setup() runs once
+// per device for each call site, under the site's lock, before that device's first launch.
+template <class F>
+inline void once_per_device(std::mutex& mu, uint64_t& done, F&& setup) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t bit = 1ull << (dev & 63);
+  std::lock_guard<std::mutex> lk(mu);
+  if (!(done & bit)) {
+    setup();
+    done |= bit;
+  }
+}
 
 // ------------------------------------------------------------------ tile layouts
 
