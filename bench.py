@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--p", type=int, default=6)
     ap.add_argument("--shots", type=int, default=1_000_000)
     ap.add_argument("--family", default="reg3", choices=["reg3", "gnp"])
+    ap.add_argument("--prob", type=float, default=0.1, help="edge probability of G(n, p) (--family gnp)")
     ap.add_argument("--weights", default="int", choices=["int", "u01"],
                     help="integer weights {1..10} (int32 costs) or U(0,1) float64 weights")
     ap.add_argument("--seed", type=int, default=0)
@@ -70,7 +71,7 @@ def parse():
 
 
 def workload_name(a):
-    fam = "random 3-regular" if a.family == "reg3" else "G(n,0.1)"
+    fam = "random 3-regular" if a.family == "reg3" else f"G(n,{a.prob:g})"
     w = "U(0,1) fp64 weights" if a.weights == "u01" else "integer weights {1..10}"
     return (f"MaxCut QAOA n={a.n} {fam}, {w}, p={a.p}, {a.dtype} statevector: cost vector + "
             f"{a.p} layers with <C> + {a.shots} samples + adjoint gradient (2p layers)")
@@ -79,7 +80,7 @@ def workload_name(a):
 def make_instance(a):
     import synth
     fam = "gnp" if (a.family == "reg3" and a.n % 2) else a.family  # 3-regular needs even n
-    e, w, integer = synth.graph(fam, a.n, a.seed, weights=a.weights, prob=0.1)
+    e, w, integer = synth.graph(fam, a.n, a.seed, weights=a.weights, prob=a.prob)
     gam, bet = synth.angles(a.p, a.seed)
     return e, w, integer, gam, bet
 
