@@ -550,7 +550,7 @@ int qaoa_cost_vector(const qaoa_graph_t* g, void* C_dev, int cost_dtype, qaoa_co
   CostArgs a;
   std::memset(&a, 0, sizeof(a));
   a.n = g->n;
-  a.lo_bits = std::min(g->n, 10);
+  a.lo_bits = std::min(g->n, 12);
   a.cost_dtype = cost_dtype;
   a.integer = g->weight_kind == QAOA_WEIGHT_INT;
   a.C = C_dev;

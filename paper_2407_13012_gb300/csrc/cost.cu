@@ -9,7 +9,7 @@
 //   K(h)   = sum over high-high edges of w [h_u != h_v] + sum over low-high edges of w h_v,
 //   a_u(h) = sum over high neighbours v of u of w_uv (1 - 2 h_v).
 // A block builds A once in shared memory, then walks its high parts h; per element
-// the work is one table read plus at most L adds.  Integer weights accumulate
+// the work is four shared-memory reads and three adds (details at the kernel).  Integer weights accumulate
 // exactly in int64 (stored as int32 or float64).  Float weights are quantised once to
 // a common fixed point (int64, value * 2^shift), summed exactly, and rounded once to
 // float64 at the store.
@@ -21,48 +21,67 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxLowBits = 12;
 
+// A block stages the weights in shared memory, builds the low-low table A and the sums
+// b_v = sum_{u < L} w_uv of every high vertex once, then per high part h: a_u(h) for the L
+// low vertices, K(h) by one warp (a lane per high vertex), and sum_u x_u a_u(h) as two
+// 64-entry tables over the low six and the next six low bits; an element is then four
+// shared-memory reads and three adds, and the block writes 2^L consecutive costs.
 __global__ void __launch_bounds__(kThreads) cost_kernel(const __grid_constant__ CostArgs a) {
   __shared__ long long A[1 << kMaxLowBits];
+  __shared__ long long W[QAOA_MAX_N][QAOA_MAX_N];
+  __shared__ long long bsum[QAOA_MAX_N];
   __shared__ long long au[kMaxLowBits];
+  __shared__ long long S0[64], S1[64];
   __shared__ long long Kh;
-  const int L = a.lo_bits;
+  const int n = a.n, L = a.lo_bits, tid = threadIdx.x;
   const uint32_t X = 1u << L;
-  // low-low table
-  for (uint32_t x = threadIdx.x; x < X; x += kThreads) {
+  for (int i = tid; i < n * n; i += kThreads) W[i / n][i % n] = a.wi[i / n][i % n];
+  __syncthreads();
+  for (uint32_t x = tid; x < X; x += kThreads) {  // low-low table
     long long s = 0;
     for (int u = 0; u < L; ++u)
       for (int v = u + 1; v < L; ++v)
-        if (((x >> u) ^ (x >> v)) & 1) s += a.wi[u][v];
+        if (((x >> u) ^ (x >> v)) & 1) s += W[u][v];
     A[x] = s;
   }
-  const int64_t H = 1ll << (a.n - L);
+  for (int v = L + tid; v < n; v += kThreads) {
+    long long s = 0;
+    for (int u = 0; u < L; ++u) s += W[u][v];
+    bsum[v] = s;
+  }
+  const int64_t H = 1ll << (n - L);
   for (int64_t h = blockIdx.x; h < H; h += gridDim.x) {
-    __syncthreads();
-    if (threadIdx.x < (unsigned)L) {
-      const int u = threadIdx.x;
+    __syncthreads();  // the previous h is done with au, S0, S1 and Kh
+    if (tid < L) {
       long long s = 0;
-      for (int v = L; v < a.n; ++v) {
-        const long long w = a.wi[u][v];
-        s += ((h >> (v - L)) & 1) ? -w : w;
-      }
-      au[u] = s;
-    } else if (threadIdx.x == (unsigned)L) {
+      for (int v = L; v < n; ++v) s += ((h >> (v - L)) & 1) ? -W[tid][v] : W[tid][v];
+      au[tid] = s;
+    } else if (tid >= 32 && tid < 64) {  // K(h): lane k handles high vertex L + k (n - L <= 32)
+      const int u = L + (tid - 32);
       long long s = 0;
-      for (int u = L; u < a.n; ++u) {
+      if (u < n) {
         const int hu = (h >> (u - L)) & 1;
-        for (int v = u + 1; v < a.n; ++v)
-          if (hu ^ ((h >> (v - L)) & 1)) s += a.wi[u][v];
-        if (hu)
-          for (int v = 0; v < L; ++v) s += a.wi[v][u];
+        if (hu) s = bsum[u];
+        for (int v = u + 1; v < n; ++v)
+          if (hu ^ ((h >> (v - L)) & 1)) s += W[u][v];
       }
-      Kh = s;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (tid == 32) Kh = s;
+    }
+    __syncthreads();
+    if (tid < 128) {  // sum_u x_u a_u(h) over bits [0, 6) and [6, 12)
+      const int idx = tid & 63, b0 = (tid >> 6) * 6;
+      long long s = 0;
+      for (int k = 0; k < 6; ++k)
+        if (b0 + k < L && ((idx >> k) & 1)) s += au[b0 + k];
+      if (tid < 64) S0[idx] = s;
+      else S1[idx] = s;
     }
     __syncthreads();
     const uint64_t zbase = (uint64_t)h << L;
-    for (uint32_t x = threadIdx.x; x < X; x += kThreads) {
-      long long c = A[x] + Kh;
-      for (int u = 0; u < L; ++u)
-        if ((x >> u) & 1) c += au[u];
+    const long long kh = Kh;
+    for (uint32_t x = tid; x < X; x += kThreads) {
+      const long long c = A[x] + kh + S0[x & 63] + S1[x >> 6];
       const uint64_t z = zbase | x;
       if (a.cost_dtype == QAOA_COST_I32) {
         ((int*)a.C)[z] = (int)c;
@@ -74,7 +93,6 @@ __global__ void __launch_bounds__(kThreads) cost_kernel(const __grid_constant__ 
     }
   }
 }
-
 
 // General PUBO cost (Eq. 3): C(z) = sum_t w_t [z AND mask_t == mask_t] over one chunk of
 // terms held in the kernel parameters.  A block owns 2^L consecutive z (fixed high part h)
