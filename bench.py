@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=30)
+    ap.add_argument("--n", type=int, default=None, help="qubits (default 30; 32 for --workload xy)")
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
     ap.add_argument("--p", type=int, default=6)
     ap.add_argument("--shots", type=int, default=1_000_000)
@@ -62,9 +62,13 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--jsonl", default=None, help="also append the JSON line to this file (a run log)")
-    ap.add_argument("--workload", default="layers", choices=["layers", "batched"],
-                    help="layers: the n-qubit step (default); batched: only the batched-gradient workload")
+    ap.add_argument("--workload", default="layers", choices=["layers", "batched", "xy"],
+                    help="layers: the n-qubit step (default); batched: only the batched-gradient workload; "
+                         "xy: QAOA on the Hamming-weight-k subspace with the ring XY mixer (balanced cut)")
+    ap.add_argument("--k", type=int, default=None, help="Hamming weight of the xy workload (default n/2)")
     a = ap.parse_args()
+    if a.n is None:
+        a.n = 32 if a.workload == "xy" else 30
     if a.warmup < 3:
         a.warmup = 3
     return a
@@ -518,8 +522,93 @@ def run_batched(a):
     return 0
 
 
+def xy_cpu_baseline(n_small: int = 20, reps: int = 2):
+    """The oracle (full 2^n vectors, as it stands) on one layer at n = 20, k = 10, timed on
+    the host; returns seconds per layer and the amplitudes it carries."""
+    from oracle import qaoa as oq
+    from oracle import xy as ox
+    import synth
+    e, w, _ = synth.graph("reg3", n_small, 0, weights="int")
+    C = oq.cut_values(n_small, e, w)
+    psi = ox.dicke_state(n_small, n_small // 2)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        ox.xy_state(n_small, n_small // 2, C, [0.3], [0.4], psi0=psi)
+    return (time.perf_counter() - t0) / reps, 1 << n_small
+
+
+def run_xy(a):
+    """QAOA on F_k = {z : popcount(z) = k} with the ring XY mixer: one JSON line, layers/s."""
+    import torch
+    from math import comb
+    import synth
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_2407_13012_gb300 as q
+    n = a.n
+    k = a.k if a.k is not None else n // 2
+    fam = "gnp" if (a.family == "reg3" and n % 2) else a.family
+    e, w, integer = synth.graph(fam, n, a.seed, weights=a.weights, prob=a.prob)
+    g = q.Graph(n, e, w, integer)
+    cv = q.xy_cost_vector(g, k, "i32" if integer else "f64")
+    gam, bet = synth.angles(a.p, a.seed)
+    psi = q.xy_new_state(n, k, a.dtype)
+    D = comb(n, k)
+
+    def step():
+        return q.xy_apply_layers(psi, n, k, cv, gam, bet, init=True, expect=True)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    q.timing_enable(True)
+    q.timing_read()
+    q.launch_count_reset()
+    clocks = Clocks(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(a.steps):
+        out = step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    clk = clocks.stop()
+    kms, kla, kby, _ = q.timing_read()
+    q.timing_enable(False)
+    launches = q.launch_count()
+    E, nrm = out.cpu().numpy().tolist()
+    peak, src = measured_peak_hbm()
+    achieved = kby[0] / (kms[0] * 1e-3) / 1e9 if kms[0] > 0 else None
+    line = {"metric": "xy-mixer QAOA layers per second (Hamming-weight subspace)", "value": a.p * 1e3 / ms,
+            "unit": "layers/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if a.dtype == "c128" else "f32", "data": "synthetic",
+            "config": {"workload": f"balanced-cut QAOA on F_k: n={n} {'random 3-regular' if fam == 'reg3' else fam}, "
+                                   f"k={k} ({D} amplitudes), p={a.p}, ring XY mixer, {a.dtype} subspace state; "
+                                   f"step = Dicke start + p layers + <C>", "n": n, "k": k, "p": a.p,
+                       "state_dtype": a.dtype, "l2": "state larger than L2, no flush"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "kernel": "phase + pair-gate passes", "launches": kla[0],
+                         "peak_source": f"{src} hbm_gbs"},
+            "gpu_launches": launches, "result": {"E": E, "norm": nrm}, "clocks": clk}
+    if not a.no_cpu_baseline:
+        sec, amps = xy_cpu_baseline()
+        scale = D / amps * (n / 20)
+        line["cpu_baseline"] = {"value": 1.0 / (sec * scale), "unit": "layers/s", "cores": 1, "kind": "oracle",
+                                "sample": f"oracle (full 2^20 vectors) on one n=20, k=10 layer, {sec:.2f} s, scaled "
+                                          f"by amplitudes and pair gates (x{scale:.0f}) to one layer of this workload"}
+    if rank == 0:
+        emit(line, a)
+    return 0
+
+
 def main():
     a = parse()
+    if a.workload == "xy" and a.impl != "reference":
+        return run_xy(a)
     if a.impl == "reference":
         return run_reference(a)
     if a.workload == "batched":

@@ -422,6 +422,67 @@ int qaoa_batch_autotune_workspace_size(int dtype, int p, int n_hi, int graphs_pe
 int qaoa_batch_autotune(int dtype, int p, int n_lo, int n_hi, int graphs_per_n, int32_t* tiles_out,
                         double* ms_out, void* ws_dev, size_t ws_bytes, void* stream);
 
+/*
+ * Constraint-preserving QAOA on a Hamming-weight subspace.  The paper names
+ * constraint-preserving mixers that shrink the simulated search space as future
+ * work (Sec. VI) without fixing one; this library takes the ring XY mixer of the
+ * quantum alternating operator ansatz (Hadfield et al., Algorithms 12(2):34, 2019)
+ * for the constraint popcount(z) = k (for MaxCut with k = n/2: graph bisection).
+ *  - Feasible set F_k = {z in [0, 2^n) : popcount(z) = k}, binom(n, k) states.
+ *    A subspace state holds binom(n, k) amplitudes (QAOA_C128 / QAOA_C64,
+ *    interleaved as above) in RANK ORDER: the states of F_k by increasing z
+ *    (rank(z) = sum_i binom(c_i, i) over the set bits c_1 < ... < c_k).
+ *  - Layer l (Eq. 1 with the mixer replaced): psi_z *= exp(-i gamma_l C(z)), then
+ *    the pair gates exp(-i beta_l (X_a X_b + Y_a Y_b) / 2) on the ring pairs
+ *    (j, j+1 mod n) in parity order: even j < n-1, then odd j < n-1, then the
+ *    closing pair (n-1, 0) (n = 2: the single pair (0, 1); n = 1: none).
+ *  - init = 1 starts from the uniform superposition over F_k (Dicke state).
+ *  - Arithmetic: complex128 states in float64, complex64 states in float32
+ *    (phases from float64 angles reduced mod 2 pi).
+ * Limits: 1 <= n <= QAOA_XY_MAX_N, 0 <= k <= n, m <= QAOA_XY_MAX_EDGES; the
+ * caller sizes every buffer with qaoa_xy_dim().  Graphs are validated as in
+ * qaoa_graph_check() except for these limits.
+ */
+#define QAOA_XY_MAX_N 40
+#define QAOA_XY_MAX_EDGES 1024
+
+/* *dim = binom(n, k), the number of amplitudes and cost entries.  Host-only. */
+int qaoa_xy_dim(int n, int k, int64_t* dim);
+
+/*
+ * Bytes of device scratch for qaoa_xy_apply_layers (depth p, integer cost span
+ * cmax - cmin + 1 of the descriptor, 0 when there is no phase table) and, with
+ * p = 0 and span 0, for qaoa_xy_expectation.  Host-only.
+ */
+int qaoa_xy_workspace_size(int n, int k, int dtype, int p, int64_t cost_span, size_t* bytes);
+
+/*
+ * Cost of every feasible state (Sec. IV-A restricted to F_k): C_dev[r] = C(z_r)
+ * for the state z_r of rank r, binom(n, k) entries of cost_dtype.  Integer
+ * weights: exact (int32 or float64).  Float weights: float64, quantised to one
+ * common fixed point and summed exactly as qaoa_cost_vector does.  desc as in
+ * qaoa_cost_vector (bounds are those of the whole cut, valid on F_k).  No
+ * workspace.  Errors: QAOA_ERR_INVALID_ARG (bad graph, k, pointer or dtype).
+ */
+int qaoa_xy_cost_vector(const qaoa_graph_t* g, int k, void* C_dev, int cost_dtype, qaoa_cost_t* desc,
+                        void* stream);
+
+/*
+ * p layers in place on a subspace state (see above); gamma/beta are host arrays
+ * of p doubles.  expect_dev: optional device double[2] receiving [<C>, <psi|psi>]
+ * of the final state (float64, fixed reduction order).  cost: a descriptor from
+ * qaoa_xy_cost_vector for the same (n, k).  Errors: QAOA_ERR_INVALID_ARG (sizes,
+ * pointers, non-finite angles, a workspace not 256-byte aligned),
+ * QAOA_ERR_WORKSPACE (ws_bytes below qaoa_xy_workspace_size), QAOA_ERR_CUDA.
+ */
+int qaoa_xy_apply_layers(int n, int k, int dtype, void* psi_dev, const qaoa_cost_t* cost, const double* gamma,
+                         const double* beta, int p, int init, double* expect_dev, void* ws_dev, size_t ws_bytes,
+                         void* stream);
+
+/* [<C>, <psi|psi>] of a subspace state into out_dev (device double[2]). */
+int qaoa_xy_expectation(int n, int k, int dtype, const void* psi_dev, const qaoa_cost_t* cost, double* out_dev,
+                        void* ws_dev, size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,6 +46,21 @@ def feasible_states(n: int, k: int) -> np.ndarray:
     return z[pop == k]
 
 
+def state_of_rank(n: int, k: int, r: int) -> int:
+    """The state of F_k with rank r, one at a time (for sizes too large to enumerate):
+    in the combinatorial number system r = sum_i binom(c_i, i), the top set bit c_k is the
+    largest c with binom(c, k) <= r, and the rest is the state of rank r - binom(c_k, k)
+    among k - 1 bits below it."""
+    z, c = 0, n - 1
+    for i in range(k, 0, -1):
+        while comb(c, i) > r:
+            c -= 1
+        z |= 1 << c
+        r -= comb(c, i)
+        c -= 1
+    return z
+
+
 def subspace_dim(n: int, k: int) -> int:
     return comb(n, k) if 0 <= k <= n else 0
 

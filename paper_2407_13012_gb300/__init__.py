@@ -38,7 +38,8 @@ EXPORTS = [
     "qaoa_timing_enable", "qaoa_timing_read", "qaoa_gradient_dev", "qaoa_optimize_adam", "qaoa_expectation_noalloc",
     "qaoa_batch_workspace_size", "qaoa_batch_gradient", "qaoa_batch_autotune_workspace_size", "qaoa_batch_autotune",
     "qaoa_cost_vector_pubo", "qaoa_optimize_lbfgs", "qaoa_proposer_param_count", "qaoa_propose_workspace_size",
-    "qaoa_propose_angles",
+    "qaoa_propose_angles", "qaoa_xy_dim", "qaoa_xy_workspace_size", "qaoa_xy_cost_vector", "qaoa_xy_apply_layers",
+    "qaoa_xy_expectation",
 ]
 
 
@@ -90,6 +91,11 @@ def _load() -> ct.CDLL:
         "qaoa_batch_gradient": ([i32, i32, ct.POINTER(GraphT), dp, i32, vp, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_batch_autotune_workspace_size": ([i32, i32, i32, i32, szp], i32),
         "qaoa_batch_autotune": ([i32, i32, i32, i32, i32, vp, dp, vp, ct.c_size_t, vp], i32),
+        "qaoa_xy_dim": ([i32, i32, ct.POINTER(ct.c_int64)], i32),
+        "qaoa_xy_workspace_size": ([i32, i32, i32, i32, i64, szp], i32),
+        "qaoa_xy_cost_vector": ([ct.POINTER(GraphT), i32, vp, i32, ct.POINTER(CostT), vp], i32),
+        "qaoa_xy_apply_layers": ([i32, i32, i32, vp, ct.POINTER(CostT), dp, dp, i32, i32, vp, vp, ct.c_size_t, vp], i32),
+        "qaoa_xy_expectation": ([i32, i32, i32, vp, ct.POINTER(CostT), vp, vp, ct.c_size_t, vp], i32),
         "qaoa_launch_count": ([], i64),
         "qaoa_launch_count_reset": ([], None),
         "qaoa_timing_enable": ([i32], i32),
@@ -519,6 +525,71 @@ def propose_angles(graphs, params, p: int, device="cuda"):
                                     ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(_stream(device))),
            "propose_angles")
     return out[:ng]
+
+
+# ------------------------------------------- Hamming-weight subspace, ring XY mixer
+
+
+def xy_dim(n: int, k: int) -> int:
+    """binom(n, k): amplitudes of a state on F_k = {z : popcount(z) = k}."""
+    d = ct.c_int64()
+    _check(_lib.qaoa_xy_dim(n, k, ct.byref(d)), "xy_dim")
+    return d.value
+
+
+def xy_cost_vector(graph: Graph, k: int, dtype: str = "i32", device="cuda", out=None) -> CostVector:
+    """C(z) of every z in F_k, in rank order (increasing z), on the device."""
+    torch = _torch()
+    tdt = torch.int32 if dtype == "i32" else torch.float64
+    C = out if out is not None else torch.empty(xy_dim(graph.n, k), dtype=tdt, device=device)
+    _require_cuda(C)
+    desc = CostT()
+    g = graph.as_struct()
+    _check(_lib.qaoa_xy_cost_vector(ct.byref(g), k, ct.c_void_p(C.data_ptr()), COST_I32 if tdt == torch.int32 else COST_F64,
+                                    ct.byref(desc), ct.c_void_p(_stream(C.device))), "xy_cost_vector")
+    return CostVector(C, graph.n, desc.cmin, desc.cmax)
+
+
+def xy_new_state(n: int, k: int, dtype: str = "c128", device="cuda"):
+    torch = _torch()
+    return torch.empty(xy_dim(n, k), dtype=torch.complex128 if dtype == "c128" else torch.complex64, device=device)
+
+
+def _xy_workspace(n: int, k: int, dt: int, p: int, span: int, device):
+    b = ct.c_size_t()
+    _check(_lib.qaoa_xy_workspace_size(n, k, dt, p, span, ct.byref(b)), "xy_workspace_size")
+    return _workspace(b.value, device)
+
+
+def xy_apply_layers(psi, n: int, k: int, cost: CostVector, gammas, betas, init: bool = True, expect: bool = False):
+    """p layers of phase + ring XY mixer in place on a subspace state; returns the device
+    tensor [<C>, norm] when expect=True."""
+    torch = _torch()
+    _require_cuda(psi)
+    g, b, gp, bp = _angles(gammas, betas)
+    dt = _dtype_code(psi)
+    ws = _xy_workspace(n, k, dt, len(g), cost.span, psi.device)
+    out = torch.empty(2, dtype=torch.float64, device=psi.device) if expect else None
+    cs = cost.struct()
+    _check(_lib.qaoa_xy_apply_layers(n, k, dt, ct.c_void_p(psi.data_ptr()), ct.byref(cs), gp, bp, len(g), int(init),
+                                     ct.c_void_p(out.data_ptr() if out is not None else 0),
+                                     ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(_stream(psi.device))),
+           "xy_apply_layers")
+    return out
+
+
+def xy_expectation(psi, n: int, k: int, cost: CostVector):
+    """Device tensor [<C>, <psi|psi>] of a subspace state."""
+    torch = _torch()
+    _require_cuda(psi)
+    dt = _dtype_code(psi)
+    ws = _xy_workspace(n, k, dt, 0, 0, psi.device)
+    out = torch.empty(2, dtype=torch.float64, device=psi.device)
+    cs = cost.struct()
+    _check(_lib.qaoa_xy_expectation(n, k, dt, ct.c_void_p(psi.data_ptr()), ct.byref(cs), ct.c_void_p(out.data_ptr()),
+                                    ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(_stream(psi.device))),
+           "xy_expectation")
+    return out
 
 
 def launch_count() -> int:

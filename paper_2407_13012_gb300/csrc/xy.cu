@@ -1,0 +1,540 @@
+// Constraint-preserving QAOA: the state lives on the feasible states only (the direction
+// the paper names for future work in Sec. VI — reduce the search space the simulator
+// carries for a constrained problem).  The constraint is a Hamming weight,
+//   F_k = {z in [0, 2^n) : popcount(z) = k}   (for MaxCut with k = n/2: graph bisection),
+// and the mixer is the ring XY mixer of the quantum alternating operator ansatz
+// (Hadfield et al., Algorithms 12(2):34, 2019), which keeps popcount(z):
+//   G_ab(beta) = exp(-i beta (X_a X_b + Y_a Y_b) / 2)
+// on the ring pairs (j, j+1 mod n), applied as parity sets: even j (j < n-1), then odd j
+// (j < n-1), then the closing pair (n-1, 0) alone when n is odd (with the odd set when n
+// is even); n = 2 has the single pair (0, 1).  The start state is the uniform
+// superposition over F_k (Dicke state), the cost unitary is Eq. 1's, restricted to F_k.
+//
+// Layout: binom(n, k) amplitudes in rank order, the rank of z being its position among
+// the states of F_k in increasing integer order (combinatorial number system:
+// rank(z) = sum_i binom(c_i, i) over the set bits c_1 < ... < c_k of z).  A thread walks a
+// chunk of consecutive ranks: it unranks the first (O(n)) and steps to the next state of
+// F_k with Gosper's rule (the next larger integer of equal popcount, O(1)).
+//
+// A pair gate on (a, b), a < b, pairs z (z_a = 1, z_b = 0) with z' = z ^ 2^a ^ 2^b, the
+// same state with that set bit moved from a up to b (z' > z); states with z_a = z_b are
+// unchanged.  The thread owning z updates both amplitudes, so a launch touches every
+// amplitude at most once.  For adjacent qubits (b = a + 1) the moved bit keeps its index
+// j + 1 among the set bits (j = set bits below a), so
+//   rank(z') - rank(z) = binom(a + 1, j + 1) - binom(a, j + 1) = binom(a, j);
+// the closing pair (0, n-1) ranks z' directly.
+#include "internal.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+namespace qaoa {
+namespace {
+
+constexpr int kXYThreads = 256;
+constexpr int kXYChunk = 16;       // consecutive ranks per thread
+constexpr int kXYRedBlocks = 1024;  // expectation partials (fixed grid: fixed reduction order)
+constexpr int kBN = QAOA_XY_MAX_N + 1;
+
+struct XYShape {
+  int n, k;
+  unsigned long long D;                 // binom(n, k)
+  unsigned long long binom[kBN][kBN];  // binom[c][i] = binom(c, i), 0 for i > c
+};
+
+struct XYCostArgs {
+  XYShape s;
+  int m;
+  int cost_dtype;
+  int integer;
+  int fixed_shift;
+  void* C;
+  unsigned char eu[QAOA_XY_MAX_EDGES], ev[QAOA_XY_MAX_EDGES];
+  long long ew[QAOA_XY_MAX_EDGES];  // integer or fixed-point weights
+};
+
+__device__ __forceinline__ void load_binom(unsigned long long (*B)[kBN], const XYShape& s) {
+  for (int i = threadIdx.x; i < kBN * kBN; i += blockDim.x) B[i / kBN][i % kBN] = s.binom[i / kBN][i % kBN];
+  __syncthreads();
+}
+
+// the state of F_k with rank r (r < binom(n, k)): the largest c with binom(c, i) <= r is
+// the i-th set bit, from i = k down to 1 (binom(i - 1, i) = 0 stops the search at c >= i - 1)
+__device__ __forceinline__ unsigned long long xy_unrank(unsigned long long r, int n, int k,
+                                                        const unsigned long long (*B)[kBN]) {
+  unsigned long long z = 0;
+  int c = n - 1;
+  for (int i = k; i >= 1; --i) {
+    while (B[c][i] > r) --c;
+    z |= 1ull << c;
+    r -= B[c][i];
+    --c;
+  }
+  return z;
+}
+
+__device__ __forceinline__ unsigned long long xy_rank(unsigned long long z, const unsigned long long (*B)[kBN]) {
+  unsigned long long r = 0;
+  for (int i = 1; z != 0; ++i) {
+    r += B[__ffsll((long long)z) - 1][i];
+    z &= z - 1;
+  }
+  return r;
+}
+
+// next larger integer with the same popcount (Gosper); z != 0
+__device__ __forceinline__ unsigned long long xy_next(unsigned long long z) {
+  const unsigned long long t = z | (z - 1);
+  return (t + 1) | (((~t & (t + 1)) - 1) >> __ffsll((long long)z));
+}
+
+template <typename T>
+struct Real;
+template <>
+struct Real<double2> {
+  using type = double;
+};
+template <>
+struct Real<float2> {
+  using type = float;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kXYThreads)
+    xy_gate_kernel(const __grid_constant__ XYShape s, T* __restrict__ psi, int qa, int qb,
+                   typename Real<T>::type cb, typename Real<T>::type sb) {
+  __shared__ unsigned long long B[kBN][kBN];
+  load_binom(B, s);
+  const unsigned long long D = s.D, nch = (D + kXYChunk - 1) / kXYChunk;
+  const unsigned long long ma = 1ull << qa, mb = 1ull << qb, below = ma - 1;
+  const bool adjacent = qb == qa + 1;
+  for (unsigned long long ch = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; ch < nch;
+       ch += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long r0 = ch * kXYChunk, r1 = r0 + kXYChunk < D ? r0 + kXYChunk : D;
+    unsigned long long z = xy_unrank(r0, s.n, s.k, B);
+    for (unsigned long long r = r0; r < r1; ++r) {
+      if ((z & ma) && !(z & mb)) {
+        const unsigned long long rp = adjacent ? r + B[qa][__popcll(z & below)] : xy_rank(z ^ ma ^ mb, B);
+        if (rp < D) {
+          const T x = psi[r], y = psi[rp];
+          T u, v;
+          u.x = cb * x.x + sb * y.y;  // cos(beta) x - i sin(beta) y
+          u.y = cb * x.y - sb * y.x;
+          v.x = cb * y.x + sb * x.y;  // cos(beta) y - i sin(beta) x
+          v.y = cb * y.y - sb * x.x;
+          psi[r] = u;
+          psi[rp] = v;
+        }
+      }
+      if (r + 1 < r1) z = xy_next(z);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kXYThreads) xy_cost_kernel(const __grid_constant__ XYCostArgs a) {
+  __shared__ unsigned long long B[kBN][kBN];
+  __shared__ unsigned char eu[QAOA_XY_MAX_EDGES], ev[QAOA_XY_MAX_EDGES];
+  __shared__ long long ew[QAOA_XY_MAX_EDGES];
+  for (int e = threadIdx.x; e < a.m; e += blockDim.x) {
+    eu[e] = a.eu[e];
+    ev[e] = a.ev[e];
+    ew[e] = a.ew[e];
+  }
+  load_binom(B, a.s);
+  const unsigned long long D = a.s.D, nch = (D + kXYChunk - 1) / kXYChunk;
+  for (unsigned long long ch = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; ch < nch;
+       ch += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long r0 = ch * kXYChunk, r1 = r0 + kXYChunk < D ? r0 + kXYChunk : D;
+    unsigned long long z = xy_unrank(r0, a.s.n, a.s.k, B);
+    for (unsigned long long r = r0; r < r1; ++r) {
+      long long c = 0;  // exact: integer weights, or one common fixed point
+      for (int e = 0; e < a.m; ++e)
+        if (((z >> eu[e]) ^ (z >> ev[e])) & 1) c += ew[e];
+      if (a.cost_dtype == QAOA_COST_I32) {
+        ((int*)a.C)[r] = (int)c;
+      } else if (a.integer) {
+        ((double*)a.C)[r] = (double)c;
+      } else {
+        ((double*)a.C)[r] = ldexp((double)c, -a.fixed_shift);
+      }
+      if (r + 1 < r1) z = xy_next(z);
+    }
+  }
+}
+
+template <typename T>
+__global__ void xy_init_kernel(T* __restrict__ psi, unsigned long long D, double amp) {
+  for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < D;
+       r += (unsigned long long)gridDim.x * blockDim.x) {
+    T v;
+    v.x = (typename Real<T>::type)amp;
+    v.y = 0;
+    psi[r] = v;
+  }
+}
+
+// exp(-i theta) in the state's precision; float states reduce theta mod 2 pi in float64 first
+__device__ __forceinline__ double2 phase_of(double theta, double2*) {
+  double sn, cs;
+  sincos(theta, &sn, &cs);
+  return make_double2(cs, -sn);
+}
+__device__ __forceinline__ float2 phase_of(double theta, float2*) {
+  const double two_pi = 6.283185307179586476925286766559;
+  const double red = theta - two_pi * rint(theta / two_pi);
+  float sn, cs;
+  sincosf((float)red, &sn, &cs);
+  return make_float2(cs, -sn);
+}
+
+template <typename T>
+__global__ void xy_phase_kernel(T* __restrict__ psi, const void* __restrict__ C, int cost_dtype, unsigned long long D,
+                                const T* __restrict__ tab, long long cmin, long long span, double gamma) {
+  for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < D;
+       r += (unsigned long long)gridDim.x * blockDim.x) {
+    T f;
+    if (cost_dtype == QAOA_COST_I32) {
+      const long long c = ((const int*)C)[r];
+      const long long i = c - cmin;
+      f = (tab != nullptr && i >= 0 && i < span) ? tab[i] : phase_of(gamma * (double)c, (T*)nullptr);
+    } else {
+      f = phase_of(gamma * ((const double*)C)[r], (T*)nullptr);
+    }
+    const T x = psi[r];
+    T y;
+    y.x = x.x * f.x - x.y * f.y;
+    y.y = x.x * f.y + x.y * f.x;
+    psi[r] = y;
+  }
+}
+
+// block partials of [sum C |psi|^2, sum |psi|^2] in float64, fixed order for a fixed grid
+template <typename T>
+__global__ void __launch_bounds__(kXYThreads)
+    xy_expect_kernel(const T* __restrict__ psi, const void* __restrict__ C, int cost_dtype, unsigned long long D,
+                     double* __restrict__ part) {
+  __shared__ double se[kXYThreads], sn[kXYThreads];
+  double e = 0.0, nn = 0.0;
+  for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < D;
+       r += (unsigned long long)gridDim.x * blockDim.x) {
+    const T x = psi[r];
+    const double pr = (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+    const double c = cost_dtype == QAOA_COST_I32 ? (double)((const int*)C)[r] : ((const double*)C)[r];
+    e += c * pr;
+    nn += pr;
+  }
+  se[threadIdx.x] = e;
+  sn[threadIdx.x] = nn;
+  __syncthreads();
+  for (int h = kXYThreads / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      se[threadIdx.x] += se[threadIdx.x + h];
+      sn[threadIdx.x] += sn[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = se[0];
+    part[2 * blockIdx.x + 1] = sn[0];
+  }
+}
+
+__global__ void __launch_bounds__(kXYThreads) xy_finish_kernel(const double* __restrict__ part, int nb,
+                                                               double* __restrict__ out) {
+  __shared__ double se[kXYThreads], sn[kXYThreads];
+  double e = 0.0, nn = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kXYThreads) {
+    e += part[2 * b];
+    nn += part[2 * b + 1];
+  }
+  se[threadIdx.x] = e;
+  sn[threadIdx.x] = nn;
+  __syncthreads();
+  for (int h = kXYThreads / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      se[threadIdx.x] += se[threadIdx.x + h];
+      sn[threadIdx.x] += sn[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = se[0];
+    out[1] = sn[0];
+  }
+}
+
+struct XYTableArgs {
+  double gam[QAOA_MAX_P];
+  int p;
+  long long cmin, span;
+  void* tab;
+};
+
+template <typename T>
+__global__ void xy_tables_kernel(const __grid_constant__ XYTableArgs a) {
+  const long long total = (long long)a.p * a.span;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int l = (int)(i / a.span);
+    ((T*)a.tab)[i] = phase_of(a.gam[l] * (double)(a.cmin + i % a.span), (T*)nullptr);
+  }
+}
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int sm_count() {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+unsigned grid_for(unsigned long long work, int sms) {
+  const unsigned long long cap = (unsigned long long)sms * 8;
+  const unsigned long long b = (work + kXYThreads - 1) / kXYThreads;
+  return (unsigned)(b < 1 ? 1 : (b < cap ? b : cap));
+}
+
+void fill_shape(XYShape& s, int n, int k) {
+  std::memset(&s, 0, sizeof(s));
+  s.n = n;
+  s.k = k;
+  for (int c = 0; c < kBN; ++c) {
+    s.binom[c][0] = 1;
+    for (int i = 1; i <= c; ++i) s.binom[c][i] = s.binom[c - 1][i - 1] + s.binom[c - 1][i];
+  }
+  s.D = s.binom[n][k];
+}
+
+bool shape_ok(int n, int k) { return n >= 1 && n <= QAOA_XY_MAX_N && k >= 0 && k <= n; }
+bool dtype_ok(int dtype) { return dtype == QAOA_C128 || dtype == QAOA_C64; }
+size_t elem_bytes(int dtype) { return dtype == QAOA_C128 ? 16 : 8; }
+size_t cost_bytes(int cost_dtype) { return cost_dtype == QAOA_COST_I32 ? 4 : 8; }
+int status_of(cudaError_t e) { return e == cudaSuccess ? QAOA_OK : QAOA_ERR_CUDA; }
+
+// phase-table span of an integer cost descriptor, 0 when the phases are computed directly
+long long table_span(const qaoa_cost_t* c) {
+  if (c == nullptr || c->dtype != QAOA_COST_I32 || c->cmax < c->cmin) return 0;
+  const long long span = c->cmax - c->cmin + 1;
+  return span <= QAOA_MAX_TABLE_SPAN ? span : 0;
+}
+
+size_t ws_bytes_for(int dtype, int p, long long span) {
+  size_t b = round256(2 * (size_t)kXYRedBlocks * sizeof(double));
+  if (span > 0 && p > 0) b += round256((size_t)p * span * elem_bytes(dtype));
+  return b;
+}
+
+// the ring pairs (a < b) in application order: even set, odd set, closing pair
+int ring_pairs(int n, int (*pr)[2]) {
+  int np = 0;
+  if (n < 2) return 0;
+  if (n == 2) {
+    pr[0][0] = 0;
+    pr[0][1] = 1;
+    return 1;
+  }
+  for (int j = 0; j < n - 1; j += 2, ++np) pr[np][0] = j, pr[np][1] = j + 1;
+  for (int j = 1; j < n - 1; j += 2, ++np) pr[np][0] = j, pr[np][1] = j + 1;
+  pr[np][0] = 0;
+  pr[np][1] = n - 1;
+  return np + 1;
+}
+
+int graph_check(const qaoa_graph_t* g, long long* neg, long long* pos, double* sum_abs) {
+  if (g == nullptr || g->n < 1 || g->n > QAOA_XY_MAX_N || g->m < 0 || g->m > QAOA_XY_MAX_EDGES)
+    return QAOA_ERR_INVALID_ARG;
+  if (g->m > 0 && g->uv == nullptr) return QAOA_ERR_INVALID_ARG;
+  if (g->weight_kind != QAOA_WEIGHT_INT && g->weight_kind != QAOA_WEIGHT_F64) return QAOA_ERR_INVALID_ARG;
+  bool seen[QAOA_XY_MAX_N][QAOA_XY_MAX_N] = {};
+  *neg = *pos = 0;
+  *sum_abs = 0.0;
+  for (int64_t e = 0; e < g->m; ++e) {
+    const int u = g->uv[2 * e], v = g->uv[2 * e + 1];
+    if (u < 0 || v < 0 || u >= g->n || v >= g->n || u == v) return QAOA_ERR_INVALID_ARG;
+    if (seen[u][v]) return QAOA_ERR_INVALID_ARG;
+    seen[u][v] = seen[v][u] = true;
+    const double w = g->w ? g->w[e] : 1.0;
+    if (!std::isfinite(w)) return QAOA_ERR_INVALID_ARG;
+    *sum_abs += std::fabs(w);
+    if (g->weight_kind == QAOA_WEIGHT_INT) {
+      if (w != std::floor(w) || std::fabs(w) >= 2147483648.0) return QAOA_ERR_INVALID_ARG;
+      if (w < 0) *neg += (long long)w; else *pos += (long long)w;
+    }
+  }
+  if (g->weight_kind == QAOA_WEIGHT_INT && *sum_abs >= 2147483648.0) return QAOA_ERR_INVALID_ARG;
+  if (g->weight_kind == QAOA_WEIGHT_F64 && !(*sum_abs < 1e300)) return QAOA_ERR_INVALID_ARG;
+  return QAOA_OK;
+}
+
+bool cost_ok(const qaoa_cost_t* c) {
+  return c != nullptr && c->C_dev != nullptr && (c->dtype == QAOA_COST_I32 || c->dtype == QAOA_COST_F64);
+}
+
+template <typename T>
+int expectation_t(const XYShape& s, const T* psi, const qaoa_cost_t* cost, double* out, double* part,
+                  cudaStream_t st) {
+  const int nb = (int)(s.D < (unsigned long long)kXYRedBlocks * kXYThreads ? (s.D + kXYThreads - 1) / kXYThreads
+                                                                         : kXYRedBlocks);
+  note_launch(3, st, true);
+  xy_expect_kernel<T><<<nb, kXYThreads, 0, st>>>(psi, cost->C_dev, cost->dtype, s.D, part);
+  note_launch(3, st, false, (double)s.D * (sizeof(T) + cost_bytes(cost->dtype)));
+  note_launch(3, st, true);
+  xy_finish_kernel<<<1, kXYThreads, 0, st>>>(part, nb, out);
+  note_launch(3, st, false);
+  return status_of(cudaGetLastError());
+}
+
+template <typename T>
+int layers_t(const XYShape& s, T* psi, const qaoa_cost_t* cost, const double* gamma, const double* beta, int p,
+             int init, double* expect_dev, char* ws, cudaStream_t st) {
+  using R = typename Real<T>::type;
+  const int sms = sm_count();
+  const size_t sb = sizeof(T);
+  double* part = (double*)ws;
+  const long long span = p > 0 ? table_span(cost) : 0;
+  T* tab = span > 0 ? (T*)(ws + round256(2 * (size_t)kXYRedBlocks * sizeof(double))) : nullptr;
+  if (init) {
+    note_launch(3, st, true);
+    xy_init_kernel<T><<<grid_for(s.D, sms), kXYThreads, 0, st>>>(psi, s.D, 1.0 / std::sqrt((double)s.D));
+    note_launch(3, st, false, (double)s.D * sb);
+  }
+  if (tab != nullptr) {
+    XYTableArgs ta;
+    std::memset(&ta, 0, sizeof(ta));
+    for (int l = 0; l < p; ++l) ta.gam[l] = gamma[l];
+    ta.p = p;
+    ta.cmin = cost->cmin;
+    ta.span = span;
+    ta.tab = tab;
+    note_launch(3, st, true);
+    xy_tables_kernel<T><<<grid_for((unsigned long long)p * span, sms), kXYThreads, 0, st>>>(ta);
+    note_launch(3, st, false);
+  }
+  int pr[QAOA_XY_MAX_N][2];
+  const int np = (s.k > 0 && s.k < s.n) ? ring_pairs(s.n, pr) : 0;
+  const unsigned long long moved = s.n >= 2 && s.k >= 1 && s.k <= s.n - 1 ? 2 * s.binom[s.n - 2][s.k - 1] : 0;
+  const unsigned long long nch = (s.D + kXYChunk - 1) / kXYChunk;
+  for (int l = 0; l < p; ++l) {
+    note_launch(0, st, true);
+    xy_phase_kernel<T><<<grid_for(s.D, sms), kXYThreads, 0, st>>>(psi, cost->C_dev, cost->dtype, s.D,
+                                                                  tab ? tab + (size_t)l * span : nullptr,
+                                                                  cost->cmin, span, gamma[l]);
+    note_launch(0, st, false, (double)s.D * (2 * sb + cost_bytes(cost->dtype)));
+    const R cb = (R)std::cos(beta[l]), snb = (R)std::sin(beta[l]);
+    for (int q = 0; q < np; ++q) {
+      note_launch(0, st, true);
+      xy_gate_kernel<T><<<grid_for(nch, sms), kXYThreads, 0, st>>>(s, psi, pr[q][0], pr[q][1], cb, snb);
+      note_launch(0, st, false, (double)moved * 2 * sb);
+    }
+    const int rc = status_of(cudaGetLastError());
+    if (rc) return rc;
+  }
+  if (expect_dev != nullptr) return expectation_t<T>(s, psi, cost, expect_dev, part, st);
+  return status_of(cudaGetLastError());
+}
+
+}  // namespace
+}  // namespace qaoa
+
+using namespace qaoa;
+
+extern "C" {
+
+int qaoa_xy_dim(int n, int k, int64_t* dim) {
+  if (dim == nullptr || !shape_ok(n, k)) return QAOA_ERR_INVALID_ARG;
+  XYShape s;
+  fill_shape(s, n, k);
+  *dim = (int64_t)s.D;
+  return QAOA_OK;
+}
+
+int qaoa_xy_workspace_size(int n, int k, int dtype, int p, int64_t cost_span, size_t* bytes) {
+  if (bytes == nullptr || !shape_ok(n, k) || !dtype_ok(dtype) || p < 0 || p > QAOA_MAX_P || cost_span < 0)
+    return QAOA_ERR_INVALID_ARG;
+  *bytes = ws_bytes_for(dtype, p, cost_span <= QAOA_MAX_TABLE_SPAN ? cost_span : 0);
+  return QAOA_OK;
+}
+
+int qaoa_xy_cost_vector(const qaoa_graph_t* g, int k, void* C_dev, int cost_dtype, qaoa_cost_t* desc, void* stream) {
+  long long neg = 0, pos = 0;
+  double sum_abs = 0.0;
+  int rc = graph_check(g, &neg, &pos, &sum_abs);
+  if (rc) return rc;
+  if (k < 0 || k > g->n || C_dev == nullptr) return QAOA_ERR_INVALID_ARG;
+  if (cost_dtype != QAOA_COST_I32 && cost_dtype != QAOA_COST_F64) return QAOA_ERR_INVALID_ARG;
+  if (cost_dtype == QAOA_COST_I32 && g->weight_kind != QAOA_WEIGHT_INT) return QAOA_ERR_INVALID_ARG;
+  XYCostArgs* a = new XYCostArgs;
+  std::memset(a, 0, sizeof(*a));
+  fill_shape(a->s, g->n, k);
+  a->m = (int)g->m;
+  a->cost_dtype = cost_dtype;
+  a->integer = g->weight_kind == QAOA_WEIGHT_INT;
+  a->C = C_dev;
+  if (!a->integer) {  // one common fixed point; every partial sum stays below 2^62
+    int e2 = 0;
+    std::frexp(sum_abs + 1.0, &e2);
+    a->fixed_shift = 62 - e2;
+  }
+  for (int e = 0; e < a->m; ++e) {
+    const double w = g->w ? g->w[e] : 1.0;
+    a->eu[e] = (unsigned char)g->uv[2 * e];
+    a->ev[e] = (unsigned char)g->uv[2 * e + 1];
+    a->ew[e] = a->integer ? (long long)w : (long long)std::llrint(std::ldexp(w, a->fixed_shift));
+  }
+  const cudaStream_t st = (cudaStream_t)stream;
+  const unsigned long long nch = (a->s.D + kXYChunk - 1) / kXYChunk;
+  note_launch(1, st, true);
+  xy_cost_kernel<<<grid_for(nch, sm_count()), kXYThreads, 0, st>>>(*a);
+  note_launch(1, st, false, (double)a->s.D * cost_bytes(cost_dtype));
+  rc = status_of(cudaGetLastError());
+  delete a;
+  if (rc) return rc;
+  if (desc) {
+    desc->C_dev = C_dev;
+    desc->dtype = cost_dtype;
+    desc->cmin = g->weight_kind == QAOA_WEIGHT_INT ? neg : 1;
+    desc->cmax = g->weight_kind == QAOA_WEIGHT_INT ? pos : 0;
+  }
+  return QAOA_OK;
+}
+
+int qaoa_xy_apply_layers(int n, int k, int dtype, void* psi_dev, const qaoa_cost_t* cost, const double* gamma,
+                         const double* beta, int p, int init, double* expect_dev, void* ws_dev, size_t ws_bytes,
+                         void* stream) {
+  if (!shape_ok(n, k) || !dtype_ok(dtype) || psi_dev == nullptr || p < 0 || p > QAOA_MAX_P) return QAOA_ERR_INVALID_ARG;
+  if ((p > 0 || expect_dev != nullptr) && !cost_ok(cost)) return QAOA_ERR_INVALID_ARG;
+  if (p > 0 && (gamma == nullptr || beta == nullptr)) return QAOA_ERR_INVALID_ARG;
+  for (int l = 0; l < p; ++l)
+    if (!std::isfinite(gamma[l]) || !std::isfinite(beta[l])) return QAOA_ERR_INVALID_ARG;
+  if (ws_dev == nullptr || ((uintptr_t)ws_dev & 255) != 0) return QAOA_ERR_INVALID_ARG;
+  if (ws_bytes < ws_bytes_for(dtype, p, p > 0 ? table_span(cost) : 0)) return QAOA_ERR_WORKSPACE;
+  XYShape* s = new XYShape;
+  fill_shape(*s, n, k);
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int rc = dtype == QAOA_C128
+                     ? layers_t<double2>(*s, (double2*)psi_dev, cost, gamma, beta, p, init, expect_dev, (char*)ws_dev, st)
+                     : layers_t<float2>(*s, (float2*)psi_dev, cost, gamma, beta, p, init, expect_dev, (char*)ws_dev, st);
+  delete s;
+  return rc;
+}
+
+int qaoa_xy_expectation(int n, int k, int dtype, const void* psi_dev, const qaoa_cost_t* cost, double* out_dev,
+                        void* ws_dev, size_t ws_bytes, void* stream) {
+  if (!shape_ok(n, k) || !dtype_ok(dtype) || psi_dev == nullptr || out_dev == nullptr || !cost_ok(cost))
+    return QAOA_ERR_INVALID_ARG;
+  if (ws_dev == nullptr || ((uintptr_t)ws_dev & 255) != 0) return QAOA_ERR_INVALID_ARG;
+  if (ws_bytes < ws_bytes_for(dtype, 0, 0)) return QAOA_ERR_WORKSPACE;
+  XYShape* s = new XYShape;
+  fill_shape(*s, n, k);
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int rc = dtype == QAOA_C128
+                     ? expectation_t<double2>(*s, (const double2*)psi_dev, cost, out_dev, (double*)ws_dev, st)
+                     : expectation_t<float2>(*s, (const float2*)psi_dev, cost, out_dev, (double*)ws_dev, st);
+  delete s;
+  return rc;
+}
+
+}  // extern "C"

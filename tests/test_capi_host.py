@@ -214,3 +214,50 @@ def test_optimizer_state_sizes_and_resume_checks():
                                     None, None, 1, None, 0, None) == q.QAOA_ERR_INVALID_ARG
     assert q.lib.qaoa_optimize_lbfgs(8, q.C128, None, None, ct.byref(cost), ang, 2, 5, 4, 1e-6, None, None,
                                      None, 1, None, 0, None) == q.QAOA_ERR_INVALID_ARG
+
+
+def test_xy_dim_and_workspace_sizes():
+    from math import comb
+    d = ct.c_int64()
+    for n, k in [(1, 0), (1, 1), (10, 3), (32, 16), (36, 18), (40, 20)]:
+        assert q.lib.qaoa_xy_dim(n, k, ct.byref(d)) == 0 and d.value == comb(n, k)
+        assert q.xy_dim(n, k) == comb(n, k)
+    for n, k in [(0, 0), (41, 1), (5, -1), (5, 6)]:
+        assert q.lib.qaoa_xy_dim(n, k, ct.byref(d)) == q.QAOA_ERR_INVALID_ARG
+    b0, b1, b2 = ct.c_size_t(), ct.c_size_t(), ct.c_size_t()
+    assert q.lib.qaoa_xy_workspace_size(20, 10, q.C128, 0, 0, ct.byref(b0)) == 0
+    assert q.lib.qaoa_xy_workspace_size(20, 10, q.C128, 4, 100, ct.byref(b1)) == 0
+    assert q.lib.qaoa_xy_workspace_size(20, 10, q.C64, 4, 100, ct.byref(b2)) == 0
+    assert b0.value % 256 == 0 and b1.value >= b0.value + 4 * 100 * 16 and b2.value >= b0.value + 4 * 100 * 8
+    assert q.lib.qaoa_xy_workspace_size(20, 10, 7, 0, 0, ct.byref(b0)) == q.QAOA_ERR_INVALID_ARG
+    assert q.lib.qaoa_xy_workspace_size(20, 10, q.C128, q.MAX_P + 1, 0, ct.byref(b0)) == q.QAOA_ERR_INVALID_ARG
+
+
+def test_xy_calls_reject_bad_arguments_before_launch():
+    fake = ct.c_void_p(1 << 20)  # never dereferenced: every call below fails its checks first
+    g = q.Graph(4, np.array([[0, 1], [1, 2]]), np.array([1.5, 2.0]), integer=False).as_struct()
+    desc = q.CostT()
+    # float weights with int32 costs, k out of range, no output
+    assert q.lib.qaoa_xy_cost_vector(ct.byref(g), 2, fake, q.COST_I32, ct.byref(desc), None) == q.QAOA_ERR_INVALID_ARG
+    assert q.lib.qaoa_xy_cost_vector(ct.byref(g), 5, fake, q.COST_F64, ct.byref(desc), None) == q.QAOA_ERR_INVALID_ARG
+    assert q.lib.qaoa_xy_cost_vector(ct.byref(g), 2, None, q.COST_F64, ct.byref(desc), None) == q.QAOA_ERR_INVALID_ARG
+    big = q.Graph(41, np.array([[0, 40]]), None).as_struct()
+    assert q.lib.qaoa_xy_cost_vector(ct.byref(big), 2, fake, q.COST_I32, ct.byref(desc), None) == q.QAOA_ERR_INVALID_ARG
+    rep = q.Graph(36, np.array([[0, 35], [35, 0]]), None).as_struct()
+    assert q.lib.qaoa_xy_cost_vector(ct.byref(rep), 2, fake, q.COST_I32, ct.byref(desc), None) == q.QAOA_ERR_INVALID_ARG
+    cost = q.CostT(1 << 21, q.COST_I32, 0, 10)
+    gm = (ct.c_double * 2)(0.1, 0.2)
+    bt = (ct.c_double * 2)(0.3, float("nan"))
+    ok_b = (ct.c_double * 2)(0.3, 0.4)
+    args = lambda n, k, dt, psi, c, b, ws, wsb: q.lib.qaoa_xy_apply_layers(n, k, dt, psi, c, gm, b, 2, 1, None, ws, wsb, None)
+    E = q.QAOA_ERR_INVALID_ARG
+    assert args(10, 11, q.C128, fake, ct.byref(cost), ok_b, fake, 1 << 20) == E      # k > n
+    assert args(10, 5, 9, fake, ct.byref(cost), ok_b, fake, 1 << 20) == E            # dtype
+    assert args(10, 5, q.C128, None, ct.byref(cost), ok_b, fake, 1 << 20) == E       # no state
+    assert args(10, 5, q.C128, fake, None, ok_b, fake, 1 << 20) == E                 # no cost
+    assert args(10, 5, q.C128, fake, ct.byref(cost), bt, fake, 1 << 20) == E         # non-finite angle
+    assert args(10, 5, q.C128, fake, ct.byref(cost), ok_b, ct.c_void_p((1 << 20) + 8), 1 << 20) == E  # misaligned
+    assert args(10, 5, q.C128, fake, ct.byref(cost), ok_b, fake, 256) == q.QAOA_ERR_WORKSPACE
+    out = ct.c_void_p(1 << 22)
+    assert q.lib.qaoa_xy_expectation(10, 5, q.C64, fake, ct.byref(cost), out, fake, 16, None) == q.QAOA_ERR_WORKSPACE
+    assert q.lib.qaoa_xy_expectation(10, 5, q.C64, fake, ct.byref(cost), None, fake, 1 << 20, None) == E

@@ -78,6 +78,7 @@ def test_rank_order_is_the_combinatorial_number_system(n):
             assert sum(comb(c, i + 1) for i, c in enumerate(bits)) == r
         subsets = sorted(sum(1 << j for j in c) for c in itertools.combinations(range(n), k))
         assert list(fk) == subsets
+        assert [ox.state_of_rank(n, k, r) for r in range(len(fk))] == subsets
 
 
 @pytest.mark.parametrize("n,k", [(4, 2), (5, 2), (6, 3), (7, 1)])
