@@ -142,3 +142,17 @@ def test_phase_only_layer_keeps_the_expectation():
     e1 = ox.xy_expectation(ox.restrict(psi, n, k), Cs)[0]
     e0 = ox.xy_expectation(ox.restrict(before, n, k), Cs)[0]
     assert abs(e1 - e0) < 1e-13
+
+
+@pytest.mark.parametrize("n,k", [(2, 1), (5, 2), (8, 4), (9, 1)])
+def test_moved_amplitudes_per_pair_gate(n, k):
+    # the algorithmic bytes of a pair-gate pass count the states of F_k with z_a != z_b:
+    # 2 binom(n - 2, k - 1) for every pair, the states the gate actually changes
+    fk = ox.feasible_states(n, k)
+    rng = np.random.default_rng(n + k)
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[fk] = rng.standard_normal(len(fk)) + 1j * rng.standard_normal(len(fk))
+    for s in ox.ring_pair_sets(n):
+        for a, b in s:
+            moved = np.count_nonzero(ox.apply_pair_gate(psi, n, a, b, 0.7) != psi)
+            assert moved == 2 * comb(n - 2, k - 1)
