@@ -132,3 +132,37 @@ def xy_expectation(psi_sub: np.ndarray, C_sub: np.ndarray):
     """[<C>, <psi|psi>] of a subspace state (rank order)."""
     pr = np.abs(psi_sub) ** 2
     return float(np.sum(np.asarray(C_sub, dtype=np.float64) * pr)), float(np.sum(pr))
+
+
+def xy_adjoint_gradient(n: int, k: int, C: np.ndarray, gammas, betas):
+    """[E, dE/dgamma_1..p, dE/dbeta_1..p] of E = <psi|C|psi> for the subspace QAOA above.
+
+    The circuit is a sequence of gates exp(-i theta H_g): per layer the cost unitary
+    (H = diag(C), theta = gamma_l), then every ring pair gate in order (H = K_ab, the
+    swap of z_a = 1, z_b = 0 with its partner, theta = beta_l).  For gate g with state
+    psi_g right after it and lambda_g = (gates after g)^dagger C psi_final,
+    dE/dtheta_g = 2 Im <lambda_g | H_g | psi_g>; a parameter's derivative sums over its
+    gates.  psi_g is recovered by undoing the later gates (exp(+i theta H_g)).
+    """
+    Cf = np.asarray(C, dtype=np.float64)
+    psi = xy_state(n, k, Cf, gammas, betas)
+    E = float(np.real(np.vdot(psi, Cf * psi)))
+    lam = Cf * psi
+    p = len(gammas)
+    dg, db = np.zeros(p), np.zeros(p)
+    z = np.arange(1 << n, dtype=np.int64)
+    for l in range(p - 1, -1, -1):
+        for pair_set in reversed(ring_pair_sets(n)):
+            for a, b in reversed(pair_set):
+                own = (((z >> a) & 1) == 1) & (((z >> b) & 1) == 0)
+                kpsi = np.zeros_like(psi)
+                zs = z[own]
+                zp = zs ^ (1 << a) ^ (1 << b)
+                kpsi[zs], kpsi[zp] = psi[zp], psi[zs]
+                db[l] += 2.0 * np.imag(np.vdot(lam, kpsi))
+                psi = apply_pair_gate(psi, n, a, b, -betas[l])
+                lam = apply_pair_gate(lam, n, a, b, -betas[l])
+        dg[l] = 2.0 * np.imag(np.vdot(lam, Cf * psi))
+        psi = psi * np.exp(1j * gammas[l] * Cf)
+        lam = lam * np.exp(1j * gammas[l] * Cf)
+    return E, dg, db

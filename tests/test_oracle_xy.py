@@ -156,3 +156,36 @@ def test_moved_amplitudes_per_pair_gate(n, k):
         for a, b in s:
             moved = np.count_nonzero(ox.apply_pair_gate(psi, n, a, b, 0.7) != psi)
             assert moved == 2 * comb(n - 2, k - 1)
+
+
+@pytest.mark.parametrize("n,k", [(4, 2), (5, 2), (6, 3), (7, 3)])
+def test_adjoint_gradient_matches_central_differences(n, k):
+    rng = np.random.default_rng(17 * n + k)
+    edges = [(u, v) for u in range(n) for v in range(u + 1, n) if rng.random() < 0.6]
+    w = rng.uniform(0.2, 1.5, len(edges))
+    C = oq.cut_values(n, edges, w, integer=False)
+    p = 3
+    gammas, betas = rng.uniform(-1, 1, p), rng.uniform(-1, 1, p)
+
+    def energy(g, b):
+        psi = ox.xy_state(n, k, C, g, b)
+        return float(np.real(np.vdot(psi, C * psi)))
+
+    E, dg, db = ox.xy_adjoint_gradient(n, k, C, gammas, betas)
+    assert abs(E - energy(gammas, betas)) < 1e-12
+    h = 1e-6
+    for l in range(p):
+        e = np.zeros(p)
+        e[l] = h
+        fd_g = (energy(gammas + e, betas) - energy(gammas - e, betas)) / (2 * h)
+        fd_b = (energy(gammas, betas + e) - energy(gammas, betas - e)) / (2 * h)
+        assert abs(dg[l] - fd_g) < 1e-7 * max(1.0, abs(fd_g))
+        assert abs(db[l] - fd_b) < 1e-7 * max(1.0, abs(fd_b))
+
+
+def test_adjoint_gradient_vanishes_where_the_mixer_cannot_act():
+    # k = 0: a one-dimensional subspace, E = 0 and every derivative is 0
+    n = 5
+    C = oq.cut_values(n, [(0, 1), (1, 2), (2, 4)], [1.0, 2.0, 3.0])
+    E, dg, db = ox.xy_adjoint_gradient(n, 0, C, [0.3, 0.5], [0.2, -0.4])
+    assert E == 0.0 and np.all(dg == 0) and np.all(db == 0)
