@@ -13,7 +13,6 @@ psi *= exp(-i gamma C) followed by RX(2 beta) on every qubit.
 from __future__ import annotations
 
 import ctypes as ct
-import math
 from dataclasses import dataclass
 from pathlib import Path
 
@@ -269,11 +268,25 @@ def new_state(n: int, dtype: str = "c128", device="cuda"):
     return torch.empty(1 << n, dtype=torch.complex128 if dtype == "c128" else torch.complex64, device=device)
 
 
+def _state_qubits(psi, cost: CostVector | None = None, *others) -> int:
+    """n of a 2^n-amplitude state.  The C ABI takes plain pointers, so check here that the
+    state is a power-of-two length >= 2 and that the cost vector and any second state
+    hold as many entries."""
+    m = psi.numel()
+    n = m.bit_length() - 1
+    if m < 2 or m != 1 << n:
+        raise ValueError(f"a state holds 2^n amplitudes (n >= 1), got {m}")
+    for t in ([cost.C] if cost is not None else []) + list(others):
+        if t.numel() != m:
+            raise ValueError(f"every buffer must hold 2^{n} = {m} entries, got {t.numel()}")
+    return n
+
+
 def apply_layers(psi, cost: CostVector, gammas, betas, init: bool = True, expect: bool = False):
     """S2+S3 in place; returns the device tensor [<C>, norm] when expect=True."""
     torch = _torch()
     _require_cuda(psi)
-    n = int(round(math.log2(psi.numel())))
+    n = _state_qubits(psi, cost)
     g, b, gp, bp = _angles(gammas, betas)
     dt = _dtype_code(psi)
     ws_n = workspace_size(n, dt, OP_LAYERS, len(g), 0, cost.span)
@@ -291,7 +304,7 @@ def expectation(psi, cost: CostVector):
     """S4: device tensor [<C>, <psi|psi>]."""
     torch = _torch()
     _require_cuda(psi)
-    n = int(round(math.log2(psi.numel())))
+    n = _state_qubits(psi, cost)
     dt = _dtype_code(psi)
     ws = _workspace(workspace_size(n, dt, OP_EXPECTATION), psi.device)
     out = torch.empty(2, dtype=torch.float64, device=psi.device)
@@ -306,7 +319,7 @@ def sample(psi, cost: CostVector, shots: int, seed: int):
     """S5+S6: (z uint64 as int64 tensor, cost float64 tensor) on the device, in draw order."""
     torch = _torch()
     _require_cuda(psi)
-    n = int(round(math.log2(psi.numel())))
+    n = _state_qubits(psi, cost)
     dt = _dtype_code(psi)
     ws = _workspace(workspace_size(n, dt, OP_SAMPLE, 0, shots), psi.device)
     z = torch.empty(max(shots, 1), dtype=torch.int64, device=psi.device)
@@ -322,7 +335,7 @@ def gradient(psi, lam, cost: CostVector, gammas, betas):
     """S7: device tensor [E, norm, dE/dgamma_1..p, dE/dbeta_1..p] (psi ends uncomputed)."""
     torch = _torch()
     _require_cuda(psi, lam)
-    n = int(round(math.log2(psi.numel())))
+    n = _state_qubits(psi, cost, lam)
     g, b, gp, bp = _angles(gammas, betas)
     dt = _dtype_code(psi)
     if lam.dtype != psi.dtype or lam.numel() != psi.numel():
@@ -342,7 +355,7 @@ def gradient_dev(psi, lam, cost: CostVector, angles):
     _require_cuda(psi, lam, angles)
     if angles.dtype != torch.float64 or angles.numel() % 2:
         raise ValueError("angles must be a float64 tensor of length 2p")
-    n = int(round(math.log2(psi.numel())))
+    n = _state_qubits(psi, cost, lam)
     p = angles.numel() // 2
     dt = _dtype_code(psi)
     ws = _workspace(workspace_size(n, dt, OP_GRADIENT, p, 0, cost.span), psi.device)
@@ -561,10 +574,19 @@ def _xy_workspace(n: int, k: int, dt: int, p: int, span: int, device):
     return _workspace(b.value, device)
 
 
+def _xy_sizes(n: int, k: int, psi, cost: CostVector) -> None:
+    """The C ABI takes plain pointers: check here that both buffers hold binom(n, k) entries."""
+    d = xy_dim(n, k)
+    if psi.numel() != d or cost.C.numel() != d:
+        raise ValueError(f"state and cost vector must hold binom({n}, {k}) = {d} entries, "
+                         f"got {psi.numel()} and {cost.C.numel()}")
+
+
 def xy_apply_layers(psi, n: int, k: int, cost: CostVector, gammas, betas, init: bool = True, expect: bool = False):
     """p layers of phase + ring XY mixer in place on a subspace state; returns the device
     tensor [<C>, norm] when expect=True."""
     torch = _torch()
+    _xy_sizes(n, k, psi, cost)
     _require_cuda(psi)
     g, b, gp, bp = _angles(gammas, betas)
     dt = _dtype_code(psi)
@@ -581,6 +603,7 @@ def xy_apply_layers(psi, n: int, k: int, cost: CostVector, gammas, betas, init: 
 def xy_expectation(psi, n: int, k: int, cost: CostVector):
     """Device tensor [<C>, <psi|psi>] of a subspace state."""
     torch = _torch()
+    _xy_sizes(n, k, psi, cost)
     _require_cuda(psi)
     dt = _dtype_code(psi)
     ws = _xy_workspace(n, k, dt, 0, 0, psi.device)

@@ -261,3 +261,24 @@ def test_xy_calls_reject_bad_arguments_before_launch():
     out = ct.c_void_p(1 << 22)
     assert q.lib.qaoa_xy_expectation(10, 5, q.C64, fake, ct.byref(cost), out, fake, 16, None) == q.QAOA_ERR_WORKSPACE
     assert q.lib.qaoa_xy_expectation(10, 5, q.C64, fake, ct.byref(cost), None, fake, 1 << 20, None) == E
+
+
+def test_xy_binding_checks_buffer_sizes_first():
+    torch = pytest.importorskip("torch")
+    cv = q.CostVector(torch.zeros(q.xy_dim(10, 5), dtype=torch.int32), 10)
+    short = torch.zeros(q.xy_dim(10, 5) - 1, dtype=torch.complex128)
+    with pytest.raises(ValueError):
+        q.xy_apply_layers(short, 10, 5, cv, [0.1], [0.2])
+    with pytest.raises(ValueError):
+        q.xy_expectation(torch.zeros(q.xy_dim(10, 4), dtype=torch.complex128), 10, 5, cv)
+
+
+def test_binding_checks_state_and_cost_sizes():
+    torch = pytest.importorskip("torch")
+    cv = q.CostVector(torch.zeros(1 << 10, dtype=torch.int32), 10)
+    assert q._state_qubits(torch.zeros(1 << 10, dtype=torch.complex128), cv) == 10
+    for bad in (1000, 1, 1 << 11):
+        with pytest.raises(ValueError):
+            q._state_qubits(torch.zeros(bad, dtype=torch.complex128), cv)
+    with pytest.raises(ValueError):  # second state of another size
+        q._state_qubits(torch.zeros(1 << 10, dtype=torch.complex128), cv, torch.zeros(1 << 9, dtype=torch.complex128))
