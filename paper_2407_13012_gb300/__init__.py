@@ -222,11 +222,22 @@ class CostVector:
         return CostT(self.C.data_ptr(), self.code, self.cmin, self.cmax)
 
 
+def _cost_out(out, entries: int, tdt, device):
+    """The caller's cost-vector buffer, or a new one: `entries` elements of dtype tdt (the
+    kernels write exactly that many)."""
+    torch = _torch()
+    if out is None:
+        return torch.empty(entries, dtype=tdt, device=device)
+    if out.numel() != entries or out.dtype != tdt or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous {tdt} tensor of {entries} entries")
+    return out
+
+
 def cost_vector(graph: Graph, dtype: str = "i32", device="cuda", out=None) -> CostVector:
     """S1: C(z) for all z on the device (int32 exact, or float64)."""
     torch = _torch()
     tdt = torch.int32 if dtype == "i32" else torch.float64
-    C = out if out is not None else torch.empty(1 << graph.n, dtype=tdt, device=device)
+    C = _cost_out(out, 1 << graph.n, tdt, device)
     _require_cuda(C)
     desc = CostT()
     g = graph.as_struct()
@@ -253,7 +264,7 @@ def cost_vector_pubo(n: int, masks, weights, integer: bool = True, dtype: str = 
     if len(m) != len(w):
         raise ValueError("masks and weights must have the same length")
     tdt = torch.int32 if dtype == "i32" else torch.float64
-    C = out if out is not None else torch.empty(1 << n, dtype=tdt, device=device)
+    C = _cost_out(out, 1 << n, tdt, device)
     _require_cuda(C)
     desc = CostT()
     _check(_lib.qaoa_cost_vector_pubo(n, len(m), ct.c_void_p(m.ctypes.data), w.ctypes.data_as(ct.POINTER(ct.c_double)),
@@ -554,7 +565,7 @@ def xy_cost_vector(graph: Graph, k: int, dtype: str = "i32", device="cuda", out=
     """C(z) of every z in F_k, in rank order (increasing z), on the device."""
     torch = _torch()
     tdt = torch.int32 if dtype == "i32" else torch.float64
-    C = out if out is not None else torch.empty(xy_dim(graph.n, k), dtype=tdt, device=device)
+    C = _cost_out(out, xy_dim(graph.n, k), tdt, device)
     _require_cuda(C)
     desc = CostT()
     g = graph.as_struct()

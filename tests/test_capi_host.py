@@ -282,3 +282,16 @@ def test_binding_checks_state_and_cost_sizes():
             q._state_qubits(torch.zeros(bad, dtype=torch.complex128), cv)
     with pytest.raises(ValueError):  # second state of another size
         q._state_qubits(torch.zeros(1 << 10, dtype=torch.complex128), cv, torch.zeros(1 << 9, dtype=torch.complex128))
+
+
+def test_binding_checks_cost_vector_out_buffers():
+    torch = pytest.importorskip("torch")
+    g = q.Graph(6, np.array([[0, 1], [1, 2]]), None, True)
+    for bad in (torch.zeros(63, dtype=torch.int32), torch.zeros(64, dtype=torch.float64),
+                torch.zeros(128, dtype=torch.int32)[::2]):
+        with pytest.raises(ValueError):
+            q.cost_vector(g, "i32", out=bad)
+    with pytest.raises(ValueError):
+        q.cost_vector_pubo(6, [1], [1.0], out=torch.zeros(32, dtype=torch.int32))
+    with pytest.raises(ValueError):
+        q.xy_cost_vector(g, 3, out=torch.zeros(q.xy_dim(6, 3) + 1, dtype=torch.int32))
