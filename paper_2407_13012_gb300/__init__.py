@@ -287,10 +287,18 @@ def _state_qubits(psi, cost: CostVector | None = None, *others) -> int:
     n = m.bit_length() - 1
     if m < 2 or m != 1 << n:
         raise ValueError(f"a state holds 2^n amplitudes (n >= 1), got {m}")
-    for t in ([cost.C] if cost is not None else []) + list(others):
-        if t.numel() != m:
-            raise ValueError(f"every buffer must hold 2^{n} = {m} entries, got {t.numel()}")
+    if cost is not None:
+        _check_cost_tensor(cost)
+    for t in [psi] + ([cost.C] if cost is not None else []) + list(others):
+        if t.numel() != m or not t.is_contiguous():
+            raise ValueError(f"every buffer must be contiguous with 2^{n} = {m} entries, got {t.numel()}")
     return n
+
+
+def _check_cost_tensor(cost: CostVector) -> None:
+    torch = _torch()
+    if cost.C.dtype not in (torch.int32, torch.float64):
+        raise ValueError(f"cost vectors are int32 or float64, got {cost.C.dtype}")
 
 
 def apply_layers(psi, cost: CostVector, gammas, betas, init: bool = True, expect: bool = False):
@@ -588,7 +596,8 @@ def _xy_workspace(n: int, k: int, dt: int, p: int, span: int, device):
 def _xy_sizes(n: int, k: int, psi, cost: CostVector) -> None:
     """The C ABI takes plain pointers: check here that both buffers hold binom(n, k) entries."""
     d = xy_dim(n, k)
-    if psi.numel() != d or cost.C.numel() != d:
+    _check_cost_tensor(cost)
+    if psi.numel() != d or cost.C.numel() != d or not psi.is_contiguous() or not cost.C.is_contiguous():
         raise ValueError(f"state and cost vector must hold binom({n}, {k}) = {d} entries, "
                          f"got {psi.numel()} and {cost.C.numel()}")
 

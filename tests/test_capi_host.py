@@ -295,3 +295,14 @@ def test_binding_checks_cost_vector_out_buffers():
         q.cost_vector_pubo(6, [1], [1.0], out=torch.zeros(32, dtype=torch.int32))
     with pytest.raises(ValueError):
         q.xy_cost_vector(g, 3, out=torch.zeros(q.xy_dim(6, 3) + 1, dtype=torch.int32))
+
+
+def test_binding_checks_layout_and_cost_dtype():
+    torch = pytest.importorskip("torch")
+    psi = torch.zeros(1 << 10, dtype=torch.complex128)
+    with pytest.raises(ValueError):  # float32 costs would be read as float64
+        q._state_qubits(psi, q.CostVector(torch.zeros(1 << 10, dtype=torch.float32), 10))
+    cv = q.CostVector(torch.zeros(1 << 10, dtype=torch.float64), 10)
+    assert q._state_qubits(psi, cv) == 10
+    with pytest.raises(ValueError):  # strided view
+        q._state_qubits(torch.zeros(1 << 11, dtype=torch.complex128)[::2], cv)
