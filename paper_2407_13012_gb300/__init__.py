@@ -372,8 +372,7 @@ def gradient_dev(psi, lam, cost: CostVector, angles):
     """S7 with device-resident angles [gamma_1..p, beta_1..p] (float64 CUDA tensor)."""
     torch = _torch()
     _require_cuda(psi, lam, angles)
-    if angles.dtype != torch.float64 or angles.numel() % 2:
-        raise ValueError("angles must be a float64 tensor of length 2p")
+    _check_angles(angles)
     n = _state_qubits(psi, cost, lam)
     p = angles.numel() // 2
     dt = _dtype_code(psi)
@@ -432,6 +431,28 @@ def optimizer_state(kind: str, p: int, device="cuda"):
     return torch.zeros(nbytes.value // 8, dtype=torch.float64, device=device)
 
 
+def _check_angles(angles) -> None:
+    torch = _torch()
+    if angles.dtype != torch.float64 or angles.numel() < 2 or angles.numel() % 2 or not angles.is_contiguous():
+        raise ValueError("angles must be a contiguous float64 tensor of length 2p, p >= 1")
+
+
+def _check_optimizer_args(kind: str, cost: CostVector, angles, state) -> None:
+    """Device buffers of the optimiser loops: the angles, the cost vector (2^n entries) and
+    an optional state buffer at least optimizer_state(kind, p) long."""
+    torch = _torch()
+    _check_angles(angles)
+    _check_cost_tensor(cost)
+    if cost.C.numel() != 1 << cost.n or not cost.C.is_contiguous():
+        raise ValueError(f"the cost vector must hold 2^{cost.n} entries")
+    if state is not None:
+        nbytes = ct.c_size_t()
+        _check(_lib.qaoa_optimizer_state_size(OPTIMIZER_ADAM if kind == "adam" else OPTIMIZER_LBFGS,
+                                              angles.numel() // 2, ct.byref(nbytes)), "optimizer_state_size")
+        if state.dtype != torch.float64 or not state.is_contiguous() or state.numel() * 8 < nbytes.value:
+            raise ValueError(f"state must be a contiguous float64 tensor of at least {nbytes.value // 8} values")
+
+
 def optimize_adam(cost: CostVector, angles, steps: int, lr: float = 0.01, betas=(0.9, 0.999), eps: float = 1e-8,
                   dtype: str = "c128", history: bool = True, state=None, resume: bool = False):
     """Adam ascent on <C> for `steps` steps, entirely on the device (one CUDA graph per
@@ -440,6 +461,7 @@ def optimize_adam(cost: CostVector, angles, steps: int, lr: float = 0.01, betas=
     Returns the history tensor (steps x (4p + 2)): [E, norm, dE/dgamma, dE/dbeta, gamma, beta]."""
     torch = _torch()
     _require_cuda(angles)
+    _check_optimizer_args("adam", cost, angles, state)
     p = angles.numel() // 2
     n = cost.n
     dt = C128 if dtype == "c128" else C64
@@ -513,6 +535,7 @@ def optimize_lbfgs(cost: CostVector, angles, max_evals: int = 200, m: int = 10, 
     evaluations (rows x (4p + 2)) device tensor, info dict with running totals)."""
     torch = _torch()
     _require_cuda(angles)
+    _check_optimizer_args("lbfgs", cost, angles, state)
     p = angles.numel() // 2
     n = cost.n
     dt = C128 if dtype == "c128" else C64

@@ -306,3 +306,20 @@ def test_binding_checks_layout_and_cost_dtype():
     assert q._state_qubits(psi, cv) == 10
     with pytest.raises(ValueError):  # strided view
         q._state_qubits(torch.zeros(1 << 11, dtype=torch.complex128)[::2], cv)
+
+
+def test_binding_checks_optimizer_buffers():
+    torch = pytest.importorskip("torch")
+    cv = q.CostVector(torch.zeros(1 << 8, dtype=torch.float64), 8)
+    ang = torch.zeros(6, dtype=torch.float64)
+    st_size = ct.c_size_t()
+    assert q.lib.qaoa_optimizer_state_size(q.OPTIMIZER_LBFGS, 3, ct.byref(st_size)) == 0
+    q._check_optimizer_args("lbfgs", cv, ang, torch.zeros(st_size.value // 8, dtype=torch.float64))
+    for bad_ang in (torch.zeros(6, dtype=torch.float32), torch.zeros(5, dtype=torch.float64),
+                    torch.zeros(12, dtype=torch.float64)[::2]):
+        with pytest.raises(ValueError):
+            q._check_optimizer_args("adam", cv, bad_ang, None)
+    with pytest.raises(ValueError):  # state too short for p = 3
+        q._check_optimizer_args("lbfgs", cv, ang, torch.zeros(st_size.value // 8 - 1, dtype=torch.float64))
+    with pytest.raises(ValueError):  # cost vector of the wrong length for n
+        q._check_optimizer_args("adam", q.CostVector(torch.zeros(100, dtype=torch.int32), 8), ang, None)
