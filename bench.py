@@ -81,6 +81,20 @@ def workload_name(a):
             f"{a.p} layers with <C> + {a.shots} samples + adjoint gradient (2p layers)")
 
 
+# What the kernels compute in.  complex128 states are stored as float64 pairs but, inside a
+# call, held and transformed as int64 fixed point with a fixed resolution of 2^-54 (Q54):
+# an amplitude of magnitude 2^-15 (n = 30) carries ~39 significant bits, not float64's 53.
+ARITHMETIC = {
+    "c128": "int64 fixed point, value = integer x 2^-54 (Q54), inside each call; float64 pairs (complex128) "
+            "in memory between calls; reductions exact in int128, converted to float64",
+    "c64": "float32 (complex64 state), reductions accumulated in float64",
+}
+
+
+def arith_dtype(state_dtype: str) -> str:
+    return "int64" if state_dtype == "c128" else "f32"
+
+
 def make_instance(a):
     import synth
     fam = "gnp" if (a.family == "reg3" and a.n % 2) else a.family  # 3-regular needs even n
@@ -197,59 +211,110 @@ def traffic_record(kernel_hash: str, key: str):
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
+#
+# The oracle (numpy, as it stands) applies one full QAOA layer -- the phase on all 2^m
+# amplitudes, then RX on each of the m qubits -- to the |+> state of the workload's graph
+# family at a size m the host finishes in seconds.  It runs once on one core, then as
+# independent copies on all cores at the same time (one process each, started with
+# `spawn`, released together by a barrier): layers/s on the host = copies / wall time.
+# Both rates are measured; the workload's n-qubit rate is their extrapolation by the
+# layer's work, 2^(n - m) n / m (amplitudes x qubit passes), and the line says so.
 
-def oracle_layer_sample(a, e, w, integer, gam, bet):
-    """Time the oracle on a bounded slice of the workload: one layer (phase + RX on the
-    slice's low qubits) over the first 2^k amplitudes of the n-qubit state.  Returns
-    (seconds for the slice, k, the scale factor to one full layer)."""
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_layer_child(m, family, weights, prob, seed, p, barrier, results):
+    """One full oracle layer at m qubits; puts (start, end) wall-clock times on `results`."""
+    import synth
     from oracle import qaoa
-    k = min(a.n, 22)
-    zs = np.arange(1 << k, dtype=np.int64)
-    C = np.zeros(1 << k, dtype=np.int64 if integer else np.float64)
-    for (u, v), we in zip(e, w):  # the slice of C(z) (bits >= k are 0)
-        cut = ((zs >> u) ^ (zs >> v)) & 1
-        C = C + (int(we) * cut if integer else we * cut.astype(np.float64))
-    psi = np.full(1 << k, 2.0 ** (-a.n / 2), dtype=np.complex128)
-    t0 = time.perf_counter()
+    fam = "gnp" if (family == "reg3" and m % 2) else family
+    e, w, integer = synth.graph(fam, m, seed, weights=weights, prob=prob)
+    gam, bet = synth.angles(p, seed)
+    C = qaoa.cut_values(m, e, w, integer=integer)
+    psi = qaoa.plus_state(m)
+    barrier.wait()
+    t0 = time.time()
     psi = qaoa.apply_cost_unitary(psi, C, gam[0])
-    psi = qaoa.apply_rx_all(psi, k, bet[0])
-    dt = time.perf_counter() - t0
-    scale = (2.0 ** (a.n - k)) * (a.n / k)
-    return dt, k, scale
+    psi = qaoa.apply_rx_all(psi, m, bet[0])
+    results.put((t0, time.time()))
 
 
-def cpu_baseline(a, e, w, integer, gam, bet):
-    reps, total, k, scale = 0, 0.0, 0, 1.0
-    t_end = time.perf_counter() + 12.0
-    while time.perf_counter() < t_end or reps == 0:
-        dt, k, scale = oracle_layer_sample(a, e, w, integer, gam, bet)
-        total += dt
-        reps += 1
-    per_layer = total / reps * scale
-    return {"value": 1.0 / per_layer, "unit": "layers/s", "cores": 1, "kind": "oracle",
-            "sample": (f"numpy oracle, one layer (phase + RX on {k} qubits) over a 2^{k}-amplitude slice of the "
-                       f"n={a.n} state, {reps} repetitions, scaled x{scale:.1f} to one full n={a.n} layer")}
+def oracle_layers(a, m: int, copies: int):
+    """Wall time of `copies` concurrent full oracle layers at m qubits (one process each)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(copies)
+    results = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_layer_child, args=(m, a.family, a.weights, a.prob, a.seed, a.p, barrier,
+                                                          results)) for _ in range(copies)]
+    for pr in procs:
+        pr.start()
+    spans = [results.get() for _ in procs]
+    for pr in procs:
+        pr.join()
+    return max(t1 for _, t1 in spans) - min(t0 for t0, _ in spans)
 
 
-def run_reference(a):
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(a, m: int = 24):
+    """The oracle's layer rate on the host: measured at m qubits on one core and on all
+    cores, extrapolated to the workload's n qubits."""
+    cores = min(host_cores(), 16)  # each copy holds ~1 GB at m = 24
+    t1 = oracle_layers(a, m, 1)
+    tall = oracle_layers(a, m, cores)
+    scale = 2.0 ** (a.n - m) * a.n / m
+    rate_all = cores / tall
+    return {"value": rate_all / scale, "unit": "layers/s", "cores": cores, "kind": "oracle",
+            "extrapolated": True, "scale": scale,
+            "measured": {"m": m, "layer_s_one_core": t1, "layers_per_s_one_core": 1.0 / t1,
+                         "layers_per_s_all_cores": rate_all, "copies": cores},
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "sample": (f"numpy oracle: one full layer (phase + RX on all {m} qubits) of the workload's graph family "
+                       f"at m={m}, timed on 1 core ({t1:.2f} s) and as {cores} concurrent copies on {cores} cores "
+                       f"({tall:.2f} s wall); layers/s extrapolated to n={a.n} by 2^(n-m) n/m = x{scale:.1f}")}
+
+
+def run_reference(a, m: int = 22):
+    """The oracle as the reference arm: each step is one round of concurrent full layers at
+    m qubits on all host cores; layers/s extrapolated to the workload by 2^(n-m) n/m."""
     world, rank, local = dist_env()
     if rank != 0:
         return 0
-    e, w, integer, gam, bet = make_instance(a)
-    times = []
+    cores = min(host_cores(), 16)
+    scale = 2.0 ** (a.n - m) * a.n / m
+    walls = []
     for i in range(a.warmup + a.steps):
-        dt, k, scale = oracle_layer_sample(a, e, w, integer, gam, bet)
+        wall = oracle_layers(a, m, cores)
         if i >= a.warmup:
-            times.append(dt * scale * 3 * a.p)  # one step = 3p layer applications
-    step = statistics.mean(times)
-    value = 3 * a.p / step
+            walls.append(wall)
+    wall = statistics.mean(walls)
+    value = cores / wall / scale            # workload layers per second on the host
+    step = 3 * a.p / value                  # one step = 3p layer applications
     line = {"metric": METRIC, "impl": "reference", "value": value, "unit": "layers/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(a), "n": a.n, "p": a.p, "state_dtype": a.dtype},
-            "cpu_baseline": {"value": value, "unit": "layers/s", "cores": 1, "kind": "oracle",
-                             "sample": f"numpy oracle layer over a 2^{k}-amplitude slice of the n={a.n} state, "
-                                       f"scaled x{scale:.1f} per layer, 3p layers per step"},
+            "cpu_baseline": {"value": value, "unit": "layers/s", "cores": cores, "kind": "oracle",
+                             "extrapolated": True, "scale": scale, "cpu_model": cpu_model(),
+                             "nproc": os.cpu_count(),
+                             "sample": f"each step: {cores} concurrent full numpy-oracle layers at m={m} qubits "
+                                       f"({wall:.2f} s wall), extrapolated to n={a.n} by 2^(n-m) n/m = x{scale:.1f}; "
+                                       f"3p layers per step"},
             "e2e": {"value": value, "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     emit(line, a)
     return 0
@@ -476,8 +541,9 @@ def run_ours(a):
         line = {
             "metric": METRIC, "value": value, "unit": "layers/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if a.dtype == "c128" else "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": arith_dtype(a.dtype), "data": "synthetic",
             "config": {"workload": workload_name(a), "n": a.n, "p": a.p, "state_dtype": a.dtype,
+                       "arithmetic": ARITHMETIC[a.dtype],
                        "family": a.family, "weights": a.weights, "shots": shots,
                        "layers_per_step": layers_per_step, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (state %.1f GB)" % ((16 if a.dtype == 'c128' else 8) * 2 ** a.n / 1e9)},
@@ -498,7 +564,7 @@ def run_ours(a):
         if batched is not None:
             line["batched"] = batched
         if not a.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(a, e, w, integer, gam, bet)
+            line["cpu_baseline"] = cpu_baseline(a)
         emit(line, a)
     if world > 1:
         dist.destroy_process_group()
@@ -517,8 +583,8 @@ def run_batched(a):
         emit({"metric": "batched adjoint gradients (graph gradients/s)", "value": res["graph_grads_per_s"],
               "unit": "graph gradients/s", "n_gpus": 1, "steps": a.steps, "warmup": 1,
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-              "dtype": "f64" if a.dtype == "c128" else "f32", "data": "synthetic",
-              "config": {"workload": res["workload"]}, "batched": res}, a)
+              "dtype": arith_dtype(a.dtype), "data": "synthetic",
+              "config": {"workload": res["workload"], "arithmetic": ARITHMETIC[a.dtype]}, "batched": res}, a)
     return 0
 
 

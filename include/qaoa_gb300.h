@@ -17,6 +17,15 @@
  *    (MaxCut, Sec. V).
  *  - State buffers are interleaved (re, im): QAOA_C128 = 2 x float64 per
  *    amplitude (16 B), QAOA_C64 = 2 x float32 (8 B).  Layout is index order.
+ *  - Arithmetic.  QAOA_C64 computes in float32 (reductions in float64).
+ *    QAOA_C128 stores float64 pairs between calls but, inside a call, holds
+ *    the state as int64 fixed point with the fixed resolution 2^-54 (value =
+ *    integer x 2^-54): an amplitude of magnitude 2^-k keeps 54 - k significant
+ *    bits (39 at 2^-15, a typical amplitude at n = 30), not float64's 53.
+ *    Each group mixer adds a rounding error of 2-norm about
+ *    0.41 x 2^((n + t)/2 - 54) for a group of t <= 12 qubits; <C> and the
+ *    gradient are reduced exactly in int128 and see far less (their error
+ *    stays below 1e-10 x max(1, sum|w|) at every tested n <= 31).
  *  - Every pointer named *_dev is device memory owned by the caller; the
  *    library never allocates or frees device memory.  Host pointers are read
  *    during the call only.

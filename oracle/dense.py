@@ -44,3 +44,36 @@ def dense_expectation(n: int, C, gammas, betas, mixer_sign: int = 1) -> float:
     psi = dense_state(n, C, gammas, betas, mixer_sign)
     HC = np.diag(np.asarray(C, dtype=np.float64))
     return float(np.real(np.conj(psi) @ HC @ psi))
+
+
+def dense_gradient(n: int, C, gammas, betas, mixer_sign: int = 1):
+    """Exact dE/dgamma_l and dE/dbeta_l of Eq. 1 from dense matrices (forward mode).
+
+    Each factor is expm(-i t G) with a fixed generator G, so its t-derivative is
+    (-i G) expm(-i t G).  The state with factor l differentiated is
+    d psi / d t_l = U_p ... U_(l+1) (-i G_l) U_l ... U_1 |+>, and
+    dE/dt_l = 2 Re <psi| H_C |d psi / d t_l>.  No adjoint recursion and no
+    uncompute: an independent route to the gradient of Sec. II-B, IV-C.
+    """
+    if n > 6:
+        raise ValueError("dense check is for n <= 6")
+    HC = np.diag(np.asarray(C, dtype=np.float64)).astype(np.complex128)
+    B = b_matrix(n)
+    factors = []  # (generator, unitary) in application order
+    for g, b in zip(gammas, betas):
+        factors.append((HC, expm(-1j * g * HC)))
+        factors.append((mixer_sign * B, expm(-1j * mixer_sign * b * B)))
+    plus = np.full(1 << n, 2.0 ** (-n / 2), dtype=np.complex128)
+    psi = plus.copy()
+    for _, U in factors:
+        psi = U @ psi
+    grads = []
+    for k in range(len(factors)):
+        d = plus.copy()
+        for j, (G, U) in enumerate(factors):
+            d = U @ d
+            if j == k:
+                d = -1j * (G @ d)
+        grads.append(2.0 * float(np.real(np.conj(psi) @ (HC @ d))))
+    grads = np.array(grads)
+    return grads[0::2], grads[1::2]

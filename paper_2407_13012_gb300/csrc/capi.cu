@@ -112,7 +112,6 @@ struct Sweep {
 
 static int64_t tiles_of(const Group& g, int n) { return 1ll << (n - g.t - g.c); }
 
-constexpr int kGridCap = 2048;
 constexpr size_t kScalarBytes = 256;                     // norm^2 (double), max|C| bits (u64)
 constexpr size_t kNormPartialBytes = 1024 * sizeof(double);
 constexpr size_t kTrigBytes = 3 * QAOA_MAX_P * sizeof(double);  // per-layer terms of device angles
@@ -530,7 +529,7 @@ int qaoa_workspace_size(int n, int dtype, int op, int p, int64_t shots, int64_t 
   switch (op) {
     case QAOA_OP_COST: b = 0; break;
     case QAOA_OP_LAYERS: b = layer_ws_bytes(dtype, p, cost_span, 2); break;
-    case QAOA_OP_EXPECTATION: b = partial_bytes(2) + 256; break;
+    case QAOA_OP_EXPECTATION: b = kExpectPartialBytes + kHostResultBytes; break;
     case QAOA_OP_SAMPLE: b = round256(sample_ws_bytes(n, dtype)); break;
     case QAOA_OP_GRADIENT: b = layer_ws_bytes(dtype, p, cost_span, 2 * p + 2); break;
     case QAOA_OP_OPTIMIZE: b = layer_ws_bytes(dtype, p, cost_span, 2 * p + 2) + adam_extra_bytes(p); break;
@@ -559,7 +558,7 @@ int qaoa_cost_vector(const qaoa_graph_t* g, void* C_dev, int cost_dtype, qaoa_co
   if (!a.integer) {
     // fixed point: every partial sum is bounded by sum|w|, keep it below 2^62
     int e2 = 0;
-    std::frexp(sum_abs + 1.0, &e2);  // sum_abs + 1 < 2^e2
+    std::frexp(sum_abs > 0.0 ? sum_abs : 1.0, &e2);  // sum_abs < 2^e2, so the scale follows the weights
     a.fixed_shift = 62 - e2;
   }
   for (int64_t e = 0; e < g->m; ++e) {
@@ -603,7 +602,7 @@ int qaoa_cost_vector_pubo(int n, int64_t nterms, const uint32_t* masks, const do
   int fixed_shift = 0;
   if (!integer) {
     int e2 = 0;
-    std::frexp(sum_abs + 1.0, &e2);  // every partial sum stays below 2^62
+    std::frexp(sum_abs > 0.0 ? sum_abs : 1.0, &e2);  // sum_abs < 2^e2: every partial sum stays below 2^62 + terms / 2
     fixed_shift = 62 - e2;
   }
   PuboArgs* a = new PuboArgs;
@@ -680,8 +679,8 @@ int qaoa_expectation(int n, int dtype, const void* psi_dev, const qaoa_cost_t* c
   if (n < 1 || n > QAOA_MAX_N || !valid_dtype(dtype) || psi_dev == nullptr || out_dev == nullptr ||
       !valid_cost(cost))
     return QAOA_ERR_INVALID_ARG;
-  // the last 256 bytes of the reported size are for qaoa_expectation_host's result
-  if (ws_dev == nullptr || ws_bytes < partial_bytes(2)) return QAOA_ERR_WORKSPACE;
+  // the last kHostResultBytes of the reported size are for qaoa_expectation_host's result
+  if (ws_dev == nullptr || ws_bytes < kExpectPartialBytes) return QAOA_ERR_WORKSPACE;
   int grid = 0;
   {
     int dev = 0, sms = 1;
@@ -709,8 +708,8 @@ int qaoa_expectation_host(int n, int dtype, const void* psi_dev, const qaoa_cost
   size_t need = 0;
   if (qaoa_workspace_size(n, dtype, QAOA_OP_EXPECTATION, 0, 0, 0, &need)) return QAOA_ERR_INVALID_ARG;
   if (ws_dev == nullptr || ws_bytes < need) return QAOA_ERR_WORKSPACE;
-  double* out_dev = (double*)((char*)ws_dev + partial_bytes(2));
-  int rc = qaoa_expectation(n, dtype, psi_dev, cost, out_dev, ws_dev, partial_bytes(2), stream);
+  double* out_dev = (double*)((char*)ws_dev + kExpectPartialBytes);
+  int rc = qaoa_expectation(n, dtype, psi_dev, cost, out_dev, ws_dev, kExpectPartialBytes, stream);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemcpyAsync(out_host, out_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)

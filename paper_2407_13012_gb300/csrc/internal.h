@@ -36,6 +36,12 @@ inline uint32_t make_op(uint32_t kind, uint32_t flags, uint32_t layer, uint32_t 
 constexpr int kMaxOps = 200;
 constexpr int kMaxAcc = 2 * QAOA_MAX_P + 2;  // reduction accumulators per sweep (double each)
 constexpr int kMaxContrib = 8;               // partial slots per output
+constexpr int kGridCap = 2048;               // most blocks a reduction writes partials for
+// qaoa_expectation's workspace: partials of its 2 outputs (kMaxContrib slots x kGridCap
+// blocks each); the size qaoa_workspace_size reports adds kHostResultBytes, the slot where
+// qaoa_expectation_host lets the device write the result before copying it out
+constexpr size_t kExpectPartialBytes = 2 * (size_t)kMaxContrib * kGridCap * sizeof(double);
+constexpr size_t kHostResultBytes = 256;
 constexpr int kSmemTable = 1024;             // phase-table entries a sweep may keep in shared memory
 
 struct SweepGeom {

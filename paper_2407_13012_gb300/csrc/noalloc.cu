@@ -15,8 +15,9 @@
 
 namespace {
 
-// Reduction partials for qaoa_expectation: 2 outputs x 8 slots x 2048 blocks doubles.
-constexpr size_t kScratchBytes = 2 * 8 * 2048 * sizeof(double);  // 256 KiB
+// Reduction partials for qaoa_expectation (2 outputs x 8 slots x 2048 blocks doubles,
+// 256 KiB): the workspace qaoa_expectation itself needs, without the host-result slot.
+constexpr size_t kScratchBytes = qaoa::kExpectPartialBytes;
 static __device__ __align__(256) unsigned char g_expect_scratch[kScratchBytes];
 
 std::mutex g_mu;
@@ -45,8 +46,8 @@ extern "C" int qaoa_expectation_noalloc(int n, int dtype, const void* psi_dev, c
   size_t need = 0;
   int rc = qaoa_workspace_size(n, dtype, QAOA_OP_EXPECTATION, 0, 0, 0, &need);
   if (rc) return rc;
-  need -= 256;  // the reported size includes qaoa_expectation_host's result slot
-  if (need > kScratchBytes) return QAOA_ERR_UNSUPPORTED;
+  // the reported size is qaoa_expectation's partials plus qaoa_expectation_host's result slot
+  if (need - qaoa::kHostResultBytes > kScratchBytes) return QAOA_ERR_UNSUPPORTED;
   void* scratch = nullptr;
   rc = scratch_for_current_device(&scratch);
   if (rc) return rc;

@@ -475,7 +475,7 @@ int qaoa_xy_cost_vector(const qaoa_graph_t* g, int k, void* C_dev, int cost_dtyp
   a->C = C_dev;
   if (!a->integer) {  // one common fixed point; every partial sum stays below 2^62
     int e2 = 0;
-    std::frexp(sum_abs + 1.0, &e2);
+    std::frexp(sum_abs > 0.0 ? sum_abs : 1.0, &e2);  // sum_abs < 2^e2, so the scale follows the weights
     a->fixed_shift = 62 - e2;
   }
   for (int e = 0; e < a->m; ++e) {

@@ -62,6 +62,21 @@ def test_xy_cost_vector_float_weights(n, k):
     assert np.max(np.abs(got - want)) <= bound
 
 
+@pytest.mark.parametrize("scale", [1e-12, 1e-300, 1e12])
+def test_xy_cost_vector_float_weights_any_scale(scale):
+    """The common fixed point follows sum|w|, so tiny or huge weights keep their relative precision."""
+    q = _q()
+    n, k = 12, 6
+    rng = np.random.default_rng(5)
+    edges, w = random_graph(rng, n, 0.5, integer=False)
+    w = w * scale
+    g = q.Graph(n, np.array(edges, dtype=np.int32).reshape(-1, 2), w, integer=False)
+    got = q.xy_cost_vector(g, k, "f64").C.cpu().numpy()
+    want = ox.subspace_costs(oq.cut_values(n, edges, w, integer=False), n, k)
+    bound = (g.m + 1) * 2.0 ** -52 * float(np.abs(w).sum())
+    assert np.max(np.abs(got - want)) <= bound
+
+
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("n,k", CASES)
 @pytest.mark.parametrize("integer", [True, False])

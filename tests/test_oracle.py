@@ -270,6 +270,49 @@ def test_adjoint_p1_matches_closed_form_derivative():
     assert abs(dg[0] - cg) < 1e-6 and abs(db[0] - cb) < 1e-6
 
 
+@pytest.mark.parametrize("n,fam,kind,seed", [(3, "gnp", "u01", 1), (4, "gnp", "int", 2), (5, "gnp", "u01", 3),
+                                          (6, "reg3", "int", 4), (6, "gnp", "u01", 5), (6, "complete", "unit", 6)])
+def test_dense_gradient_against_finite_differences(n, fam, kind, seed):
+    """The dense forward-mode derivative equals central differences of the dense expm state."""
+    e, w, integer = synth.graph(fam, n, seed, weights=kind, prob=0.6)
+    C = qaoa.cut_values(n, e, w, integer=integer)
+    g, b = synth.angles(2, seed)
+    dg, db = dense.dense_gradient(n, C, g, b)
+    h = 1e-6
+    for l in range(2):
+        d = np.zeros(2)
+        d[l] = h
+        fg = (dense.dense_expectation(n, C, g + d, b) - dense.dense_expectation(n, C, g - d, b)) / (2 * h)
+        fb = (dense.dense_expectation(n, C, g, b + d) - dense.dense_expectation(n, C, g, b - d)) / (2 * h)
+        scale = max(1.0, float(np.sum(np.abs(w))))
+        assert abs(dg[l] - fg) < 1e-7 * scale and abs(db[l] - fb) < 1e-7 * scale
+
+
+@pytest.mark.parametrize("n,fam,kind,seed", [(2, "gnp", "int", 0), (4, "gnp", "u01", 1), (5, "gnp", "int", 2),
+                                          (6, "reg3", "int", 3), (6, "gnp", "u01", 4), (6, "complete", "unit", 5)])
+def test_p1_gradient_closed_form_against_dense(n, fam, kind, seed):
+    """The analytic derivative of the p = 1 closed form equals the dense expm derivative."""
+    e, w, integer = synth.graph(fam, n, seed, weights=kind, prob=0.7)
+    C = qaoa.cut_values(n, e, w, integer=integer)
+    scale = max(1.0, float(np.sum(np.abs(w))))
+    for s in range(4):
+        g, b = synth.angles(1, 10 * seed + s)
+        dg, db = dense.dense_gradient(n, C, g, b)
+        cg, cb = closed_form.gradient_p1_exact(n, e, w, g[0], b[0])
+        assert abs(dg[0] - cg) < 1e-12 * scale and abs(db[0] - cb) < 1e-12 * scale
+
+
+@pytest.mark.parametrize("n,fam,kind", [(12, "reg3", "int"), (13, "gnp", "u01")])
+def test_p1_gradient_closed_form_against_adjoint(n, fam, kind):
+    e, w, integer = synth.graph(fam, n, 7, weights=kind, prob=0.3)
+    C = qaoa.cut_values(n, e, w, integer=integer)
+    g, b = synth.angles(1, 9)
+    _, dg, db, _ = qaoa.adjoint_gradient(n, C, g, b)
+    cg, cb = closed_form.gradient_p1_exact(n, e, w, g[0], b[0])
+    scale = max(1.0, float(np.sum(np.abs(w))))
+    assert abs(dg[0] - cg) < 1e-11 * scale and abs(db[0] - cb) < 1e-11 * scale
+
+
 def test_linear_ramp():
     g, b = qaoa.linear_ramp(4)
     assert np.allclose(g, [0.25, 0.5, 0.75, 1.0]) and np.allclose(b, [0.75, 0.5, 0.25, 0.0])
@@ -322,3 +365,19 @@ def test_pins_detect_planted_gradient_sign(monkeypatch):
     fg, fb = qaoa.finite_difference_gradient(n, C, g, b)
     # a real-part (instead of imaginary-part) gradient would not match
     assert np.max(np.abs(-dg - fg)) > 1e-3 or np.max(np.abs(-db - fb)) > 1e-3
+
+
+def test_pins_detect_planted_p1_gradient_sign(monkeypatch):
+    # a wrong sign in the derivative of the cosine products must fail the dense pin
+    def bad(gamma, c):
+        cs = np.cos(gamma * c)
+        deriv = sum(c[j] * np.sin(gamma * c[j]) * np.prod(np.delete(cs, j)) for j in range(len(c)))
+        return float(np.prod(cs)), float(deriv)
+    monkeypatch.setattr(closed_form, "_cos_product_and_derivative", bad)
+    n = 6
+    e, w, integer = synth.graph("gnp", n, 4, weights="u01", prob=0.7)
+    C = qaoa.cut_values(n, e, w, integer=False)
+    g, b = synth.angles(1, 3)
+    dg, _ = dense.dense_gradient(n, C, g, b)
+    cg, _ = closed_form.gradient_p1_exact(n, e, w, g[0], b[0])
+    assert abs(dg[0] - cg) > 1e-3
