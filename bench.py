@@ -61,10 +61,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-ratio measurement")
+    ap.add_argument("--ttr-graphs", type=int, default=256)
+    ap.add_argument("--ttr-target", type=float, default=0.88)
     ap.add_argument("--jsonl", default=None, help="also append the JSON line to this file (a run log)")
-    ap.add_argument("--workload", default="layers", choices=["layers", "batched", "xy"],
+    ap.add_argument("--workload", default="layers", choices=["layers", "batched", "xy", "ttr"],
                     help="layers: the n-qubit step (default); batched: only the batched-gradient workload; "
-                         "xy: QAOA on the Hamming-weight-k subspace with the ring XY mixer (balanced cut)")
+                         "xy: QAOA on the Hamming-weight-k subspace with the ring XY mixer (balanced cut); "
+                         "ttr: only the time-to-ratio comparison of the optimisers")
     ap.add_argument("--k", type=int, default=None, help="Hamming weight of the xy workload (default n/2)")
     a = ap.parse_args()
     if a.n is None:
@@ -373,6 +377,103 @@ def measure_batched(q, dev, dtype: str, count: int, reps: int = 3):
             "timing": "CUDA events, median of %d batched runs; plain: one run over all graphs" % reps}
 
 
+TTR_WORKLOAD = ("{g} held-out graphs of the proposer family (G(n,0.3), n ~ U{{12..18}}, U(0,1) weights, seed 1002), "
+                "p={p}; approximation ratio = <C> / max_z C(z); target ratio {r}")
+
+
+def measure_time_to_ratio(q, dev, dtype: str = "c128", count: int = 256, target: float = 0.88,
+                          max_steps: int = 300, lr: float = 0.03, max_evals: int = 60):
+    """Time for every graph of a set to reach a fixed approximation ratio, four ways:
+    plain (one graph at a time: cost vector + on-device L-BFGS, the paper's optimiser) or
+    batched (all graphs per step in one persistent launch, Adam on the host between steps,
+    graphs leave the batch once they reach the target), each from the linear ramp or from the
+    learned proposer's angles (its inference inside the timed region).
+
+    Host wall clock with the device synchronised.  plain: graphs run in order, so the time
+    is that of every run before the last graph that reaches the target plus the share of that
+    graph's run up to its first evaluation at the target (evaluations are equally long).
+    batched: the step at which the last graph reaching the target reached it."""
+    import torch
+    import synth
+    from paper_2407_13012_gb300 import proposer
+    params, p, _ = proposer.load_weights()
+    insts = synth.proposer_instances(count, 1002)
+    graphs = [q.Graph(n, e, w, False) for n, e, w in insts]
+    maxcut = np.array([float(q.cost_vector(g, "f64", device=dev).C.max().item()) for g in graphs])
+    pt = torch.as_tensor(params, device=dev)
+    q.propose_angles(graphs, pt, p, device=dev)  # warm-up of the inference kernel
+    q.batch_gradient(graphs[:8], proposer.ramp_init(8, p), dtype, device=dev)
+    torch.cuda.synchronize()
+
+    def start_angles(kind):
+        if kind == "ramp":
+            return proposer.ramp_init(count, p)
+        return q.propose_angles(graphs, pt, p, device=dev).cpu().numpy()
+
+    def batched(kind):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ang = start_angles(kind)
+        m, v = np.zeros_like(ang), np.zeros_like(ang)
+        reached = np.full(count, np.nan)
+        active = np.arange(count)
+        steps = 0
+        for t in range(1, max_steps + 1):
+            out = q.batch_gradient([graphs[i] for i in active], ang[active], dtype, device=dev).cpu().numpy()
+            steps = t
+            hit = out[:, 0] / maxcut[active] >= target
+            reached[active[hit]] = time.perf_counter() - t0
+            keep = ~hit
+            idx, g = active[keep], out[keep, 2:]
+            m[idx] = 0.9 * m[idx] + 0.1 * g
+            v[idx] = 0.999 * v[idx] + 0.001 * g * g
+            ang[idx] += lr * (m[idx] / (1 - 0.9 ** t)) / (np.sqrt(v[idx] / (1 - 0.999 ** t)) + 1e-8)
+            active = idx
+            if len(active) == 0:
+                break
+        ok = ~np.isnan(reached)
+        return {"reached": float(ok.mean()), "ms_to_ratio": float(np.max(reached[ok]) * 1e3) if ok.any() else None,
+                "steps": steps}
+
+    def plain(kind):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ang0 = start_angles(kind)
+        elapsed = time.perf_counter() - t0
+        at_last, evals, nreached = None, [], 0
+        for i, g in enumerate(graphs):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            cv = q.cost_vector(g, "f64", device=dev)
+            a = torch.as_tensor(ang0[i], device=dev)
+            hist, info = q.optimize_lbfgs(cv, a, max_evals=max_evals, m=10, gtol=1e-6, dtype=dtype)
+            best = np.maximum.accumulate(hist[:, 0].cpu().numpy()) / maxcut[i]
+            wall = time.perf_counter() - t1
+            hit = np.nonzero(best >= target)[0]
+            if len(hit):
+                k = int(hit[0]) + 1
+                at_last = elapsed + wall * k / len(best)
+                evals.append(k)
+                nreached += 1
+            elapsed += wall
+        return {"reached": nreached / count, "ms_to_ratio": at_last * 1e3 if at_last is not None else None,
+                "mean_evals_to_ratio": float(np.mean(evals)) if evals else None}
+
+    res = {"workload": TTR_WORKLOAD.format(g=count, p=p, r=target), "state_dtype": dtype,
+           "timing": "host wall clock, device synchronised; proposer inference inside the proposer arms",
+           "batched": {"optimiser": f"Adam lr {lr}, at most {max_steps} steps, graphs leave once at the target"},
+           "plain": {"optimiser": f"on-device L-BFGS (m = 10), at most {max_evals} evaluations per graph"}}
+    for kind in ("ramp", "proposer"):
+        res["plain"][kind] = plain(kind)
+        res["batched"][kind] = batched(kind)
+    base = res["plain"]["ramp"]["ms_to_ratio"]
+    for arm in ("plain", "batched"):
+        for kind in ("ramp", "proposer"):
+            r = res[arm][kind]
+            r["speedup_vs_plain_ramp"] = (base / r["ms_to_ratio"]) if (base and r["ms_to_ratio"]) else None
+    return res
+
+
 def measure_gradient(q, gradient_once, steps: int):
     """Gradient evaluations per second at the main configuration (CUDA events)."""
     import torch
@@ -527,6 +628,7 @@ def run_ours(a):
     # ---- secondary measurements (outside the timed step): gradient rate, batched vs plain
     grad = measure_gradient(q, gradient_once, max(1, min(a.steps, 3)))
     batched = None if a.no_batched else measure_batched(q, dev, "c128", a.batch_graphs)
+    ttr = None if a.no_ttr else measure_time_to_ratio(q, dev, "c128")
 
     # ---- roofline of the dominant kernel (layer sweeps), measured live
     peak, peak_kind = measured_peak_hbm()
@@ -563,6 +665,8 @@ def run_ours(a):
         }
         if batched is not None:
             line["batched"] = batched
+        if ttr is not None:
+            line["time_to_ratio"] = ttr
         if not a.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(a)
         emit(line, a)
@@ -585,6 +689,24 @@ def run_batched(a):
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
               "dtype": arith_dtype(a.dtype), "data": "synthetic",
               "config": {"workload": res["workload"], "arithmetic": ARITHMETIC[a.dtype]}, "batched": res}, a)
+    return 0
+
+
+def run_ttr(a):
+    """The time-to-ratio comparison alone: one JSON line, milliseconds for the batched
+    optimiser from proposer starts to bring every graph to the target ratio."""
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_2407_13012_gb300 as q
+    dev = torch.device("cuda", local)
+    res = measure_time_to_ratio(q, dev, a.dtype, a.ttr_graphs, a.ttr_target)
+    if rank == 0:
+        emit({"metric": "time to approximation ratio (batched + proposer)",
+              "value": res["batched"]["proposer"]["ms_to_ratio"], "unit": "ms", "n_gpus": 1, "steps": 1,
+              "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+              "dtype": arith_dtype(a.dtype), "data": "synthetic",
+              "config": {"workload": res["workload"], "arithmetic": ARITHMETIC[a.dtype]}, "time_to_ratio": res}, a)
     return 0
 
 
@@ -679,6 +801,8 @@ def main():
         return run_reference(a)
     if a.workload == "batched":
         return run_batched(a)
+    if a.workload == "ttr":
+        return run_ttr(a)
     return run_ours(a)
 
 
