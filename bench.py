@@ -767,6 +767,18 @@ def run_xy(a):
     q.timing_enable(False)
     launches = q.launch_count()
     E, nrm = out.cpu().numpy().tolist()
+    # the subspace adjoint gradient (forward layers, lambda, backward pass over both buffers)
+    lam = q.xy_new_state(n, k, a.dtype)
+    q.xy_gradient(psi, lam, n, k, cv, gam, bet)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record()
+    for _ in range(max(1, min(a.steps, 3))):
+        q.xy_gradient(psi, lam, n, k, cv, gam, bet)
+    g1.record()
+    torch.cuda.synchronize()
+    grad_ms = g0.elapsed_time(g1) / max(1, min(a.steps, 3))
+    del lam
     peak, src = measured_peak_hbm()
     achieved = kby[0] / (kms[0] * 1e-3) / 1e9 if kms[0] > 0 else None
     line = {"metric": "xy-mixer QAOA layers per second (Hamming-weight subspace)", "value": a.p * 1e3 / ms,
@@ -781,7 +793,9 @@ def run_xy(a):
                          "frac": achieved / peak if achieved else None, "traffic": None,
                          "kernel": "phase + pair-gate passes", "launches": kla[0],
                          "peak_source": f"{src} hbm_gbs"},
-            "gpu_launches": launches, "result": {"E": E, "norm": nrm}, "clocks": clk}
+            "gpu_launches": launches, "result": {"E": E, "norm": nrm}, "clocks": clk,
+            "gradient": {"workload": f"subspace adjoint gradient, n={n}, k={k}, p={a.p}", "evals_per_s": 1e3 / grad_ms,
+                         "ms": grad_ms}}
     if not a.no_cpu_baseline:
         sec, amps = xy_cpu_baseline()
         scale = D / amps * (n / 20)

@@ -492,6 +492,29 @@ int qaoa_xy_apply_layers(int n, int k, int dtype, void* psi_dev, const qaoa_cost
 int qaoa_xy_expectation(int n, int k, int dtype, const void* psi_dev, const qaoa_cost_t* cost, double* out_dev,
                         void* ws_dev, size_t ws_bytes, void* stream);
 
+/* Bytes of device scratch for qaoa_xy_gradient (depth p, integer cost span as
+ * for qaoa_xy_workspace_size).  Host-only. */
+int qaoa_xy_gradient_workspace_size(int n, int k, int dtype, int p, int64_t cost_span, size_t* bytes);
+
+/*
+ * Adjoint gradient on F_k (the adjoint method of Sec. II-B and IV-C applied to the
+ * subspace circuit): every gate is exp(-i theta H_g) -- the cost unitary of layer l
+ * (H = diag(C), theta = gamma_l) and each ring pair gate (H = (X_a X_b + Y_a Y_b)/2,
+ * theta = beta_l) -- and dE/dtheta_g = 2 Im <lambda_g|H_g|psi_g> with psi_g the
+ * state right after gate g and lambda_g the later gates undone on C psi_final.
+ * The call runs the p forward layers from the Dicke state into psi_dev, sets
+ * lambda = C psi in lam_dev (two distinct buffers of binom(n, k) amplitudes,
+ * caller-owned), then walks the gates backwards, undoing each on both buffers
+ * after taking its term.  out_dev (device, 2p + 2 doubles): [E, <psi|psi>,
+ * dE/dgamma_1..p, dE/dbeta_1..p]; psi_dev ends back at the Dicke state (up to
+ * rounding).  Every sum is float64 with a fixed order.  Errors as for
+ * qaoa_xy_apply_layers, QAOA_ERR_WORKSPACE below
+ * qaoa_xy_gradient_workspace_size.
+ */
+int qaoa_xy_gradient(int n, int k, int dtype, void* psi_dev, void* lam_dev, const qaoa_cost_t* cost,
+                     const double* gamma, const double* beta, int p, double* out_dev, void* ws_dev, size_t ws_bytes,
+                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,6 +95,8 @@ def _load() -> ct.CDLL:
         "qaoa_xy_cost_vector": ([ct.POINTER(GraphT), i32, vp, i32, ct.POINTER(CostT), vp], i32),
         "qaoa_xy_apply_layers": ([i32, i32, i32, vp, ct.POINTER(CostT), dp, dp, i32, i32, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_xy_expectation": ([i32, i32, i32, vp, ct.POINTER(CostT), vp, vp, ct.c_size_t, vp], i32),
+        "qaoa_xy_gradient_workspace_size": ([i32, i32, i32, i32, i64, szp], i32),
+        "qaoa_xy_gradient": ([i32, i32, i32, vp, vp, ct.POINTER(CostT), dp, dp, i32, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_launch_count": ([], i64),
         "qaoa_launch_count_reset": ([], None),
         "qaoa_timing_enable": ([i32], i32),
@@ -655,6 +657,31 @@ def xy_expectation(psi, n: int, k: int, cost: CostVector):
     _check(_lib.qaoa_xy_expectation(n, k, dt, ct.c_void_p(psi.data_ptr()), ct.byref(cs), ct.c_void_p(out.data_ptr()),
                                     ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(_stream(psi.device))),
            "xy_expectation")
+    return out
+
+
+def xy_gradient(psi, lam, n: int, k: int, cost: CostVector, gammas, betas):
+    """Adjoint gradient on the Hamming-weight subspace: runs the forward layers from the Dicke
+    state in psi, lambda in lam (both binom(n, k) entries, same dtype), and returns the device
+    tensor [E, norm, dE/dgamma_1..p, dE/dbeta_1..p]."""
+    torch = _torch()
+    _xy_sizes(n, k, psi, cost)
+    _require_cuda(psi, lam)
+    if lam.dtype != psi.dtype or lam.numel() != psi.numel() or not lam.is_contiguous():
+        raise ValueError("lambda buffer must match psi")
+    if lam.data_ptr() == psi.data_ptr():
+        raise ValueError("psi and lambda must be distinct buffers")
+    g, b, gp, bp = _angles(gammas, betas)
+    dt = _dtype_code(psi)
+    nb = ct.c_size_t()
+    _check(_lib.qaoa_xy_gradient_workspace_size(n, k, dt, len(g), cost.span, ct.byref(nb)),
+           "xy_gradient_workspace_size")
+    ws = _workspace(nb.value, psi.device)
+    out = torch.empty(2 * len(g) + 2, dtype=torch.float64, device=psi.device)
+    cs = cost.struct()
+    _check(_lib.qaoa_xy_gradient(n, k, dt, ct.c_void_p(psi.data_ptr()), ct.c_void_p(lam.data_ptr()), ct.byref(cs),
+                                 gp, bp, len(g), ct.c_void_p(out.data_ptr()), ct.c_void_p(ws.data_ptr()), ws.numel(),
+                                 ct.c_void_p(_stream(psi.device))), "xy_gradient")
     return out
 
 

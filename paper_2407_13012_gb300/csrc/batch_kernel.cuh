@@ -44,12 +44,12 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) batch_kernel(const __grid_co
   using S = Lean<CF, FX, true>;
   using V = typename S::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* X = (V*)smem_raw;
-  void* Cs = smem_raw + (sizeof(V) << CF::B);
+  V* X = (V*)smem_raw;  // exchange area for two buffers: 2 x 2^B slots
+  void* Cs = smem_raw + ((sizeof(V) << CF::B) << 1);
   __shared__ SweepArgs sa;
   __shared__ double blk[kMaxAcc];
   __shared__ double red[2 * (CF::NT / 32)];
-  __shared__ longlong2 dsm[16];
+  __shared__ fx::Factor dsm[16];
   __shared__ int cur;
   const int tid = threadIdx.x;
   const int p = b.p;
@@ -122,8 +122,9 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) batch_kernel(const __grid_co
 
 template <class CF, bool FX, bool LEAN>
 cudaError_t launch_batch_cfg(const BatchArgs& b, int first, int count, int* queue, cudaStream_t s) {
-  const size_t smem = (sizeof(typename Sweeper<CF, FX, true>::V) << CF::B) + ((size_t)(b.cost_f64 ? 8 : 4) << CF::B);
-  const size_t smem_max = (sizeof(typename Sweeper<CF, FX, true>::V) << CF::B) + ((size_t)8 << CF::B);
+  const size_t xb = (sizeof(typename Sweeper<CF, FX, true>::V) << CF::B) << 1;  // two-buffer exchange area
+  const size_t smem = xb + ((size_t)(b.cost_f64 ? 8 : 4) << CF::B);
+  const size_t smem_max = xb + ((size_t)8 << CF::B);
   static std::mutex mu;
   static uint64_t done = 0;
   static int per_sm = 1, sms = 1;

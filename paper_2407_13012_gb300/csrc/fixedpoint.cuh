@@ -130,6 +130,41 @@ QAOA_HD C64 cmul_q62_exact(long long xr, long long xi, long long ur, long long u
   return o;
 }
 
+// A Q62 unit complex number u = ur + i ui prepared for repeated multiplies: the limbs of ur,
+// ui and -ui (the negation done once here instead of once per product).
+struct Factor {
+  Limbs r, i, ni;
+};
+
+QAOA_HD Factor factor(long long ur, long long ui) {
+  Factor f;
+  f.r = split(ur);
+  f.i = split(ui);
+  f.ni = split(-ui);
+  return f;
+}
+
+// x * u / 2^(62 + e) with u given as a Factor (conjugated when CONJ): the real part is
+// xr ur + xi (-ui), the imaginary part xr ui + xi ur (for conj(u): xr ur + xi ui and
+// xr (-ui) + xi ur).  FULL keeps every limb product (within one unit of exact rounding,
+// like cmul_q62); otherwise the low x low products are dropped: within one unit for
+// e >= 3 and within three units for e = 0.
+template <bool FULL, bool CONJ>
+QAOA_HD C64 cmul_factor(long long xr, long long xi, const Factor& f, int e) {
+  const Limbs r = split(xr), i = split(xi);
+  const Limbs& ui = CONJ ? f.ni : f.i;
+  const Limbs& nui = CONJ ? f.i : f.ni;
+  C64 o;
+  if (FULL) {
+    o.x = dot2_q62(r, f.r, i, nui, e);
+    o.y = dot2_q62(r, ui, i, f.r, e);
+  } else {
+    o.x = dot2_q62_hi(r, f.r, i, nui, e);
+    o.y = dot2_q62_hi(r, ui, i, f.r, e);
+  }
+  return o;
+}
+
 // float64 of x * 2^-s, correctly rounded (round to nearest, ties to even), assembled from
 // the binary64 layout sign | 11-bit biased exponent | 52-bit fraction.  The result must be
 // a normal number.

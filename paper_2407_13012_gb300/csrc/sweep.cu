@@ -7,6 +7,27 @@ namespace qaoa {
 namespace {
 
 
+// One layer's phase table in shared memory: float32 factors as they are, fixed-point factors
+// prepared for the limb multiply (fx::Factor, 24 bytes per entry).  Callers synchronise.
+template <bool FX, class S>
+__device__ __forceinline__ void stage_table(S& s, const SweepArgs& a, void* dst, int nt) {
+  using V = typename S::V;
+  const V* src = (const V*)a.phase_table + (long long)a.smem_table_layer * a.span;
+  if constexpr (FX) {
+    fx::Factor* tf = (fx::Factor*)dst;
+    for (int k = threadIdx.x; k < a.span; k += nt) {
+      const longlong2 e = __ldg((const longlong2*)src + k);
+      tf[k] = fx::factor(e.x, e.y);
+    }
+    s.Tf = tf;
+  } else {
+    V* ts = (V*)dst;
+    for (int k = threadIdx.x; k < a.span; k += nt) ts[k] = __ldg(src + k);
+    s.Ts = ts;
+  }
+  s.ts_layer = a.smem_table_layer;
+}
+
 // Lean sweeps: full tiles, affine layout-0 addresses, state loaded in the internal format
 // or created as |+>, stored in the internal or the caller's format (complex64: the same).
 template <class CF, bool FX, bool TWO, bool OPS, int LAST>
@@ -14,21 +35,18 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
   using S = Lean<CF, FX, TWO>;
   using V = typename S::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* X = (V*)smem_raw;
-  void* Cs = smem_raw + (sizeof(V) << CF::B);
+  V* X = (V*)smem_raw;  // exchange area: 2^B slots, twice that for two-buffer sweeps
+  void* Cs = smem_raw + ((sizeof(V) << CF::B) << (TWO ? 1 : 0));
   const bool cost = OPS && a.needs_cost;
   V* Tsm = (V*)((unsigned char*)Cs + (cost ? ((a.cost_dtype == QAOA_COST_F64 ? 8 : 4) << CF::B) : 0));
   __shared__ double blk[kMaxAcc];
   __shared__ double red[2 * (CF::NT / 32)];
-  __shared__ longlong2 dsm[16];
+  __shared__ fx::Factor dsm[16];
   for (int r = threadIdx.x; r < kMaxAcc; r += CF::NT) blk[r] = 0.0;
   S s(a, X, Cs, blk, red);
   s.Ds = dsm;
   if (OPS && a.smem_table_layer >= 0) {
-    const V* src = (const V*)a.phase_table + (long long)a.smem_table_layer * a.span;
-    for (int k = threadIdx.x; k < a.span; k += CF::NT) Tsm[k] = __ldg(src + k);
-    s.Ts = Tsm;
-    s.ts_layer = a.smem_table_layer;
+    stage_table<FX>(s, a, Tsm, CF::NT);
   }
   s.evalid = 1u << CF::B;
   if constexpr (FX && TWO) {
@@ -52,21 +70,18 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) sweep_kernel(const __grid_co
   using S = Sweeper<CF, FX, TWO>;
   using V = typename S::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* X = (V*)smem_raw;
-  void* Cs = smem_raw + (sizeof(V) << CF::B);
+  V* X = (V*)smem_raw;  // exchange area: 2^B slots, twice that for two-buffer sweeps
+  void* Cs = smem_raw + ((sizeof(V) << CF::B) << (TWO ? 1 : 0));
   V* Tsm = (V*)((unsigned char*)Cs + (a.needs_cost ? ((a.cost_dtype == QAOA_COST_F64 ? 8 : 4) << CF::B) : 0));
   __shared__ double blk[kMaxAcc];
   __shared__ double red[2 * (CF::NT / 32)];
-  __shared__ longlong2 dsm[16];
+  __shared__ fx::Factor dsm[16];
   for (int r = threadIdx.x; r < kMaxAcc; r += CF::NT) blk[r] = 0.0;
 
   S s(a, X, Cs, blk, red);
   s.Ds = dsm;
   if (a.smem_table_layer >= 0) {  // one layer's phase table in shared memory
-    const V* src = (const V*)a.phase_table + (long long)a.smem_table_layer * a.span;
-    for (int k = threadIdx.x; k < a.span; k += CF::NT) Tsm[k] = __ldg(src + k);
-    s.Ts = Tsm;
-    s.ts_layer = a.smem_table_layer;
+    stage_table<FX>(s, a, Tsm, CF::NT);
     __syncthreads();
   }
   const SweepGeom& g = a.g;
@@ -230,7 +245,8 @@ int num_sms() {
 template <class CF, bool FX, bool TWO>
 size_t smem_bytes(int cost_bytes, int table_entries = 0) {
   const size_t vb = FX ? sizeof(longlong2) : sizeof(float2);
-  return (vb << CF::B) + ((size_t)cost_bytes << CF::B) + vb * table_entries;
+  const size_t tb = FX ? sizeof(fx::Factor) : sizeof(float2);  // staged phase-table entry
+  return ((vb << CF::B) << (TWO ? 1 : 0)) + ((size_t)cost_bytes << CF::B) + tb * table_entries;
 }
 
 // blocks per SM for a configuration with a cost tile of cost_bytes per amplitude (0, 4, 8)

@@ -196,10 +196,11 @@ struct Sweeper {
   const SweepArgs& a;
   V v[R];        // register tile of psi (layout cur)
   V w[R];        // register tile of lambda (two-buffer sweeps)
-  V* X;          // exchange buffer, 2^B slots
+  V* X;          // exchange buffer, 2^B slots (2 x 2^B for two-buffer sweeps: psi, then lambda)
   void* Cs;      // cost tile, 2^B slots
-  const V* Ts;   // shared-memory copy of one layer's phase table (or nullptr)
-  longlong2* Ds; // shared-memory mixer diagonal of the current fixed-point mixer (14 entries)
+  const V* Ts;   // shared-memory copy of one layer's phase table (or nullptr); float32 states
+  const fx::Factor* Tf;  // the same for fixed-point states, as prepared factors
+  fx::Factor* Ds;  // shared-memory mixer diagonal of the current fixed-point mixer (<= 14 entries)
   int ts_layer;  // layer whose table Ts holds (-1: none)
   double* blk;   // block accumulators
   double* red;   // reduction scratch [2][NT/32]
@@ -211,7 +212,8 @@ struct Sweeper {
   const uint32_t tid;
 
   __device__ Sweeper(const SweepArgs& a_, V* X_, void* Cs_, double* blk_, double* red_)
-      : a(a_), X(X_), Cs(Cs_), Ts(nullptr), Ds(nullptr), ts_layer(-1), blk(blk_), red(red_), cur(0), lam_shift(0),
+      : a(a_), X(X_), Cs(Cs_), Ts(nullptr), Tf(nullptr), Ds(nullptr), ts_layer(-1), blk(blk_), red(red_), cur(0),
+        lam_shift(0),
         in_shift(0), evalid(0), base(0), tid(threadIdx.x) {}
 
   __device__ __forceinline__ uint32_t idx(int r) const { return CF::idx(cur, tid, r); }
@@ -248,10 +250,46 @@ struct Sweeper {
     }
   }
   // both buffers always share one layout
+  // both buffers at once: psi through X, lambda through the second half X + 2^B, so one
+  // pair of barriers serves the two
+  template <int F, int T>
+  __device__ __forceinline__ void ex2() {
+    const uint32_t pf = CF::phys(CF::idx(F, tid, 0)), pt = CF::phys(CF::idx(T, tid, 0));
+    V* X2 = X + (1u << CF::B);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) X[pf ^ CF::phys((uint32_t)r << CF::lo(F))] = v[r];
+#pragma unroll
+    for (int r = 0; r < R; ++r) X2[pf ^ CF::phys((uint32_t)r << CF::lo(F))] = w[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = X[pt ^ CF::phys((uint32_t)r << CF::lo(T))];
+#pragma unroll
+    for (int r = 0; r < R; ++r) w[r] = X2[pt ^ CF::phys((uint32_t)r << CF::lo(T))];
+  }
+  template <int F>
+  __device__ __forceinline__ void ex2_from(int to) {
+    switch (to) {
+      case 0: ex2<F, 0>(); break;
+      case 1: if constexpr (CF::NR > 1) ex2<F, (CF::NR > 1 ? 1 : 0)>(); break;
+      case 2: if constexpr (CF::NR > 2) ex2<F, (CF::NR > 2 ? 2 : 0)>(); break;
+      default: if constexpr (CF::NR > 3) ex2<F, (CF::NR > 3 ? 3 : 0)>(); break;
+    }
+  }
+  __device__ __forceinline__ void exchange_both(int to) {
+    switch (cur) {
+      case 0: ex2_from<0>(to); break;
+      case 1: if constexpr (CF::NR > 1) ex2_from<(CF::NR > 1 ? 1 : 0)>(to); break;
+      case 2: if constexpr (CF::NR > 2) ex2_from<(CF::NR > 2 ? 2 : 0)>(to); break;
+      default: if constexpr (CF::NR > 3) ex2_from<(CF::NR > 3 ? 3 : 0)>(to); break;
+    }
+  }
+  // both buffers always share one layout; two-buffer kernels own an exchange area of 2 x 2^B
+  // slots
   __device__ __forceinline__ void go(int to) {
     if (to == cur) return;
-    exchange_one(v, to);
-    if (TWO) exchange_one(w, to);
+    if constexpr (TWO) exchange_both(to);
+    else exchange_one(v, to);
     cur = to;
   }
 
@@ -281,25 +319,6 @@ struct Sweeper {
   }
 
   // ---------------------------------------------------------------- phase
-  __device__ __forceinline__ V phase_factor(int layer, bool inverse, uint32_t i) const {
-    const bool f64 = a.cost_dtype == QAOA_COST_F64;
-    long long k = -1;
-    if (!f64 && a.phase_table != nullptr) k = (long long)cost_i(Cs, i) - a.cmin;
-    V e;
-    if (k >= 0 && k < a.span) {
-      e = layer == ts_layer ? Ts[k] : __ldg((const V*)a.phase_table + (long long)layer * a.span + k);
-    } else {
-      const double th = arg_g2pi(a, layer) * cost_f(Cs, f64, i);  // turns
-      if constexpr (FX) {
-        e = turn_phase(frac_turns(th), (const longlong2*)a.turn_table);
-      } else {
-        e = phase_f32_direct(th);
-      }
-    }
-    if (inverse) e.y = -e.y;
-    return e;
-  }
-
   __device__ __forceinline__ static V vmul(V x, V e) {
     if constexpr (FX) {
       return cmul_fx(x, e, 0);
@@ -318,8 +337,21 @@ struct Sweeper {
   __device__ __forceinline__ void phase_apply(V (&u)[R], int layer) {
     const bool f64 = a.cost_dtype == QAOA_COST_F64;
     unsigned miss = 0;
-    if (!f64 && a.phase_table != nullptr) {
-      const V* tab = layer == ts_layer ? Ts : (const V*)a.phase_table + (long long)layer * a.span;
+    if (FX && !f64 && layer == ts_layer && Tf != nullptr) {  // prepared factors in shared memory
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const long long k = (long long)cost_i(Cs, idx(r)) - a.cmin;
+        if (k >= 0 && k < a.span) {
+          if constexpr (FX) {
+            const fx::C64 o = fx::cmul_factor<false, INV>(u[r].x, u[r].y, Tf[k], 0);
+            u[r] = make_longlong2(o.x, o.y);
+          }
+        } else {
+          miss |= 1u << r;
+        }
+      }
+    } else if (!f64 && a.phase_table != nullptr) {
+      const V* tab = (layer == ts_layer && Ts != nullptr) ? Ts : (const V*)a.phase_table + (long long)layer * a.span;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const long long k = (long long)cost_i(Cs, idx(r)) - a.cmin;
@@ -350,8 +382,24 @@ struct Sweeper {
   __device__ __forceinline__ void phase_apply2(int layer) {
     const bool f64 = a.cost_dtype == QAOA_COST_F64;
     unsigned miss = 0;
-    if (!f64 && a.phase_table != nullptr) {
-      const V* tab = layer == ts_layer ? Ts : (const V*)a.phase_table + (long long)layer * a.span;
+    if (FX && !f64 && layer == ts_layer && Tf != nullptr) {  // prepared factors in shared memory
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const long long k = (long long)cost_i(Cs, idx(r)) - a.cmin;
+        if (k >= 0 && k < a.span) {
+          if constexpr (FX) {
+            const fx::Factor& f = Tf[k];
+            const fx::C64 o = fx::cmul_factor<false, INV>(v[r].x, v[r].y, f, 0);
+            const fx::C64 q = fx::cmul_factor<false, INV>(w[r].x, w[r].y, f, 0);
+            v[r] = make_longlong2(o.x, o.y);
+            w[r] = make_longlong2(q.x, q.y);
+          }
+        } else {
+          miss |= 1u << r;
+        }
+      }
+    } else if (!f64 && a.phase_table != nullptr) {
+      const V* tab = (layer == ts_layer && Ts != nullptr) ? Ts : (const V*)a.phase_table + (long long)layer * a.span;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const long long k = (long long)cost_i(Cs, idx(r)) - a.cmin;
@@ -550,21 +598,20 @@ struct Sweeper {
   // D multiply on the register tile: u[r] *= Ds[popcount] / 2^t; E = t >= 3 selects the
   // shift form of the limb multiply at compile time
   template <bool BIG>
-  __device__ __forceinline__ void d_mul(V (&u)[R], const longlong2* Ds, int gl, int t) {
+  __device__ __forceinline__ void d_mul(V (&u)[R], const fx::Factor* Ds, int gl, int t) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int pc = __popc((idx(r) >> gl) & ((1u << t) - 1));
-      const longlong2 e = Ds[pc];
-      fx::C64 o;
-      if constexpr (BIG) {
-        const fx::Limbs xr = fx::split(u[r].x), xi = fx::split(u[r].y), nxi = fx::split(-u[r].y);
-        const fx::Limbs er = fx::split(e.x), ei = fx::split(e.y);
-        o.x = fx::dot2_q62_hi(xr, er, nxi, ei, t);
-        o.y = fx::dot2_q62_hi(xr, ei, xi, er, t);
-      } else {
-        o = fx::cmul_q62(u[r].x, u[r].y, e.x, e.y, t);
-      }
+      const fx::Factor& f = Ds[__popc((idx(r) >> gl) & ((1u << t) - 1))];
+      const fx::C64 o = fx::cmul_factor<!BIG, false>(u[r].x, u[r].y, f, t);
       u[r] = make_longlong2(o.x, o.y);
+    }
+  }
+  // this mixer's diagonal exp(-i s b (t - 2k)), k = 0..t, as prepared factors in shared memory
+  // (sign applied); the caller synchronises before and after
+  __device__ __forceinline__ void load_diagonal(int layer, bool inverse, int t) {
+    if (tid <= (uint32_t)t) {
+      const longlong2 e = __ldg((const longlong2*)a.d_table + ((long long)layer * 14 + t) * 14 + tid);
+      Ds[tid] = fx::factor(e.x, inverse ? -e.y : e.y);
     }
   }
 
@@ -578,13 +625,8 @@ struct Sweeper {
       if (CF::newhi(k) <= gl || CF::lo(k) >= gh) continue;
       ks[nk++] = k;
     }
-    // this mixer's diagonal exp(-i s b (t - 2k)), k = 0..t, into shared memory (sign applied)
     __syncthreads();
-    if (tid <= (uint32_t)t) {
-      longlong2 e = __ldg((const longlong2*)a.d_table + ((long long)layer * 14 + t) * 14 + tid);
-      if (inverse) e.y = -e.y;
-      Ds[tid] = e;
-    }
+    load_diagonal(layer, inverse, t);
     for (int j = 0; j < nk; ++j) {
       go(ks[j]);
       wht_round(ks[j], on_psi, on_lam);
@@ -655,17 +697,17 @@ struct Sweeper {
       e1 = i128_to_double(sn, 2 * (a.fx_shift - in_shift) - 16);
       e0 = f64 ? ldexp(sf, 2 * in_shift) : i128_to_double(sc, 2 * (a.fx_shift - in_shift) - 32);
     } else {
-      float s0 = 0.f, s1 = 0.f;
+      float s0[4] = {0.f, 0.f, 0.f, 0.f}, s1[4] = {0.f, 0.f, 0.f, 0.f};  // independent partial sums
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const uint32_t i = idx(r);
         if (i >= evalid) continue;
         const float p2 = v[r].x * v[r].x + v[r].y * v[r].y;
-        s0 += (float)cost_f(Cs, f64, i) * p2;
-        s1 += p2;
+        s0[r & 3] += (float)cost_f(Cs, f64, i) * p2;
+        s1[r & 3] += p2;
       }
-      e0 = s0;
-      e1 = s1;
+      e0 = (double)((s0[0] + s0[1]) + (s0[2] + s0[3]));
+      e1 = (double)((s1[0] + s1[1]) + (s1[2] + s1[3]));
     }
     block_add(acc, e0, e1, true);
   }
@@ -686,14 +728,14 @@ struct Sweeper {
       }
       e0 = f64 ? sf : i128_to_double(sc, 2 * a.fx_shift - 32 - lam_shift);
     } else {
-      float s = 0.f;
+      float s[4] = {0.f, 0.f, 0.f, 0.f};  // independent partial sums
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const uint32_t i = idx(r);
         if (i >= evalid) continue;
-        s += (float)cost_f(Cs, f64, i) * (w[r].x * v[r].y - w[r].y * v[r].x);
+        s[r & 3] += (float)cost_f(Cs, f64, i) * (w[r].x * v[r].y - w[r].y * v[r].x);
       }
-      e0 = s;
+      e0 = (double)((s[0] + s[1]) + (s[2] + s[3]));
     }
     block_add(acc, 2.0 * e0, 0.0, false);
   }
@@ -888,8 +930,8 @@ struct Lean : Sweeper<CF, FX, TWO> {
   }
   template <int F, int T>
   __device__ __forceinline__ void exb() {
-    this->template ex<F, T>(this->v);
-    if constexpr (TWO) this->template ex<F, T>(this->w);
+    if constexpr (TWO) this->template ex2<F, T>();
+    else this->template ex<F, T>(this->v);
     this->cur = T;
   }
   template <int K>
@@ -958,16 +1000,8 @@ struct Lean : Sweeper<CF, FX, TWO> {
   __device__ __forceinline__ void dmul_l(V (&u)[R], int gl, int t) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const longlong2 e = this->Ds[__popc((ix<L>(r) >> gl) & ((1u << t) - 1))];
-      fx::C64 o;
-      if constexpr (BIG) {
-        const fx::Limbs xr = fx::split(u[r].x), xi = fx::split(u[r].y), nxi = fx::split(-u[r].y);
-        const fx::Limbs er = fx::split(e.x), ei = fx::split(e.y);
-        o.x = fx::dot2_q62_hi(xr, er, nxi, ei, t);
-        o.y = fx::dot2_q62_hi(xr, ei, xi, er, t);
-      } else {
-        o = fx::cmul_q62(u[r].x, u[r].y, e.x, e.y, t);
-      }
+      const fx::Factor& f = this->Ds[__popc((ix<L>(r) >> gl) & ((1u << t) - 1))];
+      const fx::C64 o = fx::cmul_factor<!BIG, false>(u[r].x, u[r].y, f, t);
       u[r] = make_longlong2(o.x, o.y);
     }
   }
@@ -976,23 +1010,20 @@ struct Lean : Sweeper<CF, FX, TWO> {
   __device__ __forceinline__ void fx_mixer(int layer, bool inverse, bool lam, int xacc) {
     const int gl = this->a.g.c, t = this->a.g.t;
     __syncthreads();
-    if (this->tid <= (uint32_t)t) {
-      longlong2 e = __ldg((const longlong2*)this->a.d_table + ((long long)layer * 14 + t) * 14 + this->tid);
-      if (inverse) e.y = -e.y;
-      this->Ds[this->tid] = e;
-    }
+    this->load_diagonal(layer, inverse, t);
     fx_fwd<0, L>(lam);
     __syncthreads();
     if constexpr (TWO) {
       if (xacc >= 0) {
-        i128 xs = 0;
+        i128 xs[2] = {0, 0};  // two independent exact sums (shorter carry chains)
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int pc = __popc((ix<L>(r) >> gl) & ((1u << t) - 1));
           const i128 pr = (i128)this->w[r].x * this->v[r].y - (i128)this->w[r].y * this->v[r].x;
-          xs += (pr >> 32) * (t - 2 * pc);
+          xs[r & 1] += (pr >> 32) * (t - 2 * pc);
         }
-        this->block_add(xacc, 2.0 * i128_to_double(xs, 2 * this->a.fx_shift + t - 32 - this->lam_shift), 0.0, false);
+        this->block_add(xacc, 2.0 * i128_to_double(xs[0] + xs[1], 2 * this->a.fx_shift + t - 32 - this->lam_shift),
+                        0.0, false);
       }
     }
     // lean sweeps run only on groups of >= 3 qubits, so the shift form of the multiply
@@ -1023,7 +1054,8 @@ struct Lean : Sweeper<CF, FX, TWO> {
     if constexpr (!FX) {
       const unsigned msk = gmask<K>();
       if (xt) {
-        float part = 0.f;
+        // four independent partial sums (pairs by r mod 4) keep the FMA chains short
+        float pa[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int rb = 0; rb < CF::RB; ++rb) {
           if (!((msk >> rb) & 1u)) continue;
@@ -1031,11 +1063,11 @@ struct Lean : Sweeper<CF, FX, TWO> {
           for (int r = 0; r < R; ++r) {
             if (r & (1 << rb)) continue;
             const int q = r | (1 << rb);
-            part += this->w[r].x * this->v[q].y - this->w[r].y * this->v[q].x + this->w[q].x * this->v[r].y -
-                    this->w[q].y * this->v[r].x;
+            pa[r & 3] += this->w[r].x * this->v[q].y - this->w[r].y * this->v[q].x + this->w[q].x * this->v[r].y -
+                         this->w[q].y * this->v[r].x;
           }
         }
-        xs = fmaf(part, w2, xs);
+        xs = fmaf((pa[0] + pa[1]) + (pa[2] + pa[3]), w2, xs);
         for (unsigned b = msk; b; b &= b - 1) w2 *= m2;
       }
       if (tanf) {

@@ -27,6 +27,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -208,6 +209,161 @@ __global__ void xy_phase_kernel(T* __restrict__ psi, const void* __restrict__ C,
     y.y = x.x * f.y + x.y * f.x;
     psi[r] = y;
   }
+}
+
+// ------------------------------------------------------------------ adjoint gradient on F_k
+//
+// The circuit is a sequence of gates exp(-i theta H_g): per layer the cost unitary
+// (H = diag(C), theta = gamma_l), then the ring pair gates (H = K_ab, the swap of a state
+// with z_a = 1, z_b = 0 and its partner; theta = beta_l).  With psi_g the state right after
+// gate g and lambda_g = (gates after g)^dagger C psi_final, dE/dtheta_g = 2 Im <lambda_g|H_g|psi_g>
+// (Sec. II-B, IV-C); a parameter's derivative is the sum over its gates.  The pass walks the
+// gates backwards from lambda = C psi_final, undoing each on psi and lambda after taking its
+// term, so it needs the two subspace buffers only.  Every term is summed in float64 per
+// thread and per block, one partial per block in a fixed grid (deterministic).
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kXYThreads / 32; ++w) t += red[w];
+  return t;  // valid in thread 0
+}
+
+// lambda = C psi, with block partials of [sum C |psi|^2, sum |psi|^2] (E = Re <psi|lambda>)
+template <typename T>
+__global__ void __launch_bounds__(kXYThreads)
+    xy_lambda_kernel(const T* __restrict__ psi, T* __restrict__ lam, const void* __restrict__ C, int cost_dtype,
+                     unsigned long long D, double* __restrict__ pe, double* __restrict__ pn) {
+  __shared__ double red[kXYThreads / 32];
+  double e = 0.0, nn = 0.0;
+  for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < D;
+       r += (unsigned long long)gridDim.x * blockDim.x) {
+    const T x = psi[r];
+    const double c = cost_dtype == QAOA_COST_I32 ? (double)((const int*)C)[r] : ((const double*)C)[r];
+    T y;
+    y.x = (typename Real<T>::type)c * x.x;
+    y.y = (typename Real<T>::type)c * x.y;
+    lam[r] = y;
+    const double pr = (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+    e += c * pr;
+    nn += pr;
+  }
+  const double se = block_sum(e, red);
+  __syncthreads();
+  const double sn = block_sum(nn, red);
+  if (threadIdx.x == 0) {
+    pe[blockIdx.x] = se;
+    pn[blockIdx.x] = sn;
+  }
+}
+
+// one pair gate backwards: the block partial of 2 Im <lambda|K_ab|psi>, then G_ab(-beta) on
+// both buffers (cb = cos beta, sb = -sin beta in the forward gate's formula)
+template <typename T>
+__global__ void __launch_bounds__(kXYThreads)
+    xy_gate_adjoint_kernel(const __grid_constant__ XYShape s, T* __restrict__ psi, T* __restrict__ lam, int qa,
+                           int qb, typename Real<T>::type cb, typename Real<T>::type sb, double* __restrict__ part) {
+  __shared__ unsigned long long B[kBN][kBN];
+  __shared__ double red[kXYThreads / 32];
+  load_binom(B, s);
+  const unsigned long long D = s.D, nch = (D + kXYChunk - 1) / kXYChunk;
+  const unsigned long long ma = 1ull << qa, mb = 1ull << qb, below = ma - 1;
+  const bool adjacent = qb == qa + 1;
+  double acc = 0.0;
+  for (unsigned long long ch = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; ch < nch;
+       ch += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long r0 = ch * kXYChunk, r1 = r0 + kXYChunk < D ? r0 + kXYChunk : D;
+    unsigned long long z = xy_unrank(r0, s.n, s.k, B);
+    for (unsigned long long r = r0; r < r1; ++r) {
+      if ((z & ma) && !(z & mb)) {
+        const unsigned long long rp = adjacent ? r + B[qa][__popcll(z & below)] : xy_rank(z ^ ma ^ mb, B);
+        if (rp < D) {
+          const T x = psi[r], y = psi[rp], lx = lam[r], ly = lam[rp];
+          // Im(conj(lam_z) psi_z' + conj(lam_z') psi_z)
+          acc += (double)lx.x * y.y - (double)lx.y * y.x + (double)ly.x * x.y - (double)ly.y * x.x;
+          T u, v;
+          u.x = cb * x.x + sb * y.y;
+          u.y = cb * x.y - sb * y.x;
+          v.x = cb * y.x + sb * x.y;
+          v.y = cb * y.y - sb * x.x;
+          psi[r] = u;
+          psi[rp] = v;
+          u.x = cb * lx.x + sb * ly.y;
+          u.y = cb * lx.y - sb * ly.x;
+          v.x = cb * ly.x + sb * lx.y;
+          v.y = cb * ly.y - sb * lx.x;
+          lam[r] = u;
+          lam[rp] = v;
+        }
+      }
+      if (r + 1 < r1) z = xy_next(z);
+    }
+  }
+  const double t = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = 2.0 * t;
+}
+
+// the cost unitary backwards: the block partial of 2 Im <lambda|C|psi>, then both buffers
+// times exp(+i gamma C) (the conjugate of the forward table entry, or computed directly)
+template <typename T>
+__global__ void __launch_bounds__(kXYThreads)
+    xy_cost_adjoint_kernel(T* __restrict__ psi, T* __restrict__ lam, const void* __restrict__ C, int cost_dtype,
+                           unsigned long long D, const T* __restrict__ tab, long long cmin, long long span,
+                           double gamma, double* __restrict__ part) {
+  __shared__ double red[kXYThreads / 32];
+  double acc = 0.0;
+  for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < D;
+       r += (unsigned long long)gridDim.x * blockDim.x) {
+    T f;
+    double c;
+    if (cost_dtype == QAOA_COST_I32) {
+      const long long ci = ((const int*)C)[r];
+      const long long i = ci - cmin;
+      c = (double)ci;
+      f = (tab != nullptr && i >= 0 && i < span) ? tab[i] : phase_of(gamma * c, (T*)nullptr);
+    } else {
+      c = ((const double*)C)[r];
+      f = phase_of(gamma * c, (T*)nullptr);
+    }
+    f.y = -f.y;  // exp(+i gamma c)
+    const T x = psi[r], l = lam[r];
+    acc += c * ((double)l.x * x.y - (double)l.y * x.x);
+    T y;
+    y.x = x.x * f.x - x.y * f.y;
+    y.y = x.x * f.y + x.y * f.x;
+    psi[r] = y;
+    y.x = l.x * f.x - l.y * f.y;
+    y.y = l.x * f.y + l.y * f.x;
+    lam[r] = y;
+  }
+  const double t = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = 2.0 * t;
+}
+
+// out[o] = sum of nparts[o] consecutive partial rows (stride kXYPartStride) from row first[o]
+struct XYReducePlan {
+  int nout;
+  int first[2 * QAOA_MAX_P + 2];
+  int rows[2 * QAOA_MAX_P + 2];
+  int cols[2 * QAOA_MAX_P + 2];  // blocks per row
+};
+constexpr int kXYPartStride = 2048;  // partial slots per launch (>= any grid used here)
+
+__global__ void __launch_bounds__(kXYThreads) xy_grad_reduce_kernel(const __grid_constant__ XYReducePlan rp,
+                                                                    const double* __restrict__ part,
+                                                                    double* __restrict__ out) {
+  __shared__ double red[kXYThreads / 32];
+  const int o = blockIdx.x;
+  double acc = 0.0;
+  for (int row = 0; row < rp.rows[o]; ++row) {
+    const double* src = part + (size_t)(rp.first[o] + row) * kXYPartStride;
+    for (int b = threadIdx.x; b < rp.cols[o]; b += kXYThreads) acc += src[b];
+  }
+  const double t = block_sum(acc, red);
+  if (threadIdx.x == 0) out[o] = t;
 }
 
 // block partials of [sum C |psi|^2, sum |psi|^2] in float64, fixed order for a fixed grid
@@ -436,6 +592,64 @@ int layers_t(const XYShape& s, T* psi, const qaoa_cost_t* cost, const double* ga
   return status_of(cudaGetLastError());
 }
 
+// partial rows of the gradient: E, norm, dE/dgamma_l (p rows), dE/dbeta_l (p x pairs rows)
+size_t xy_grad_part_bytes(int n, int k, int p) {
+  int pr[QAOA_XY_MAX_N][2];
+  const int np = (k > 0 && k < n) ? ring_pairs(n, pr) : 0;
+  return round256((size_t)(2 + p + (size_t)p * np) * kXYPartStride * sizeof(double));
+}
+
+template <typename T>
+int gradient_t(const XYShape& s, T* psi, T* lam, const qaoa_cost_t* cost, const double* gamma, const double* beta,
+               int p, double* out, char* ws, cudaStream_t st) {
+  using R = typename Real<T>::type;
+  const int sms = sm_count();
+  const size_t sb = sizeof(T);
+  // forward pass (Dicke start, p layers) with the layer workspace at the front
+  int rc = layers_t<T>(s, psi, cost, gamma, beta, p, 1, nullptr, ws, st);
+  if (rc) return rc;
+  const long long span = p > 0 ? table_span(cost) : 0;
+  const T* tab = span > 0 ? (const T*)(ws + round256(2 * (size_t)kXYRedBlocks * sizeof(double))) : nullptr;
+  double* part = (double*)(ws + ws_bytes_for(sizeof(T) == 16 ? QAOA_C128 : QAOA_C64, p, span));
+  int pr[QAOA_XY_MAX_N][2];
+  const int np = (s.k > 0 && s.k < s.n) ? ring_pairs(s.n, pr) : 0;
+  const unsigned gr = std::min<unsigned>(grid_for(s.D, sms), kXYPartStride);  // one partial slot per block
+  const unsigned long long nch = (s.D + kXYChunk - 1) / kXYChunk;
+  const unsigned gg = std::min<unsigned>(grid_for(nch, sms), kXYPartStride);
+  const unsigned long long moved = s.n >= 2 && s.k >= 1 && s.k <= s.n - 1 ? 2 * s.binom[s.n - 2][s.k - 1] : 0;
+  note_launch(0, st, true);
+  xy_lambda_kernel<T><<<gr, kXYThreads, 0, st>>>(psi, lam, cost->C_dev, cost->dtype, s.D, part, part + kXYPartStride);
+  note_launch(0, st, false, (double)s.D * (2 * sb + cost_bytes(cost->dtype)));
+  for (int l = p - 1; l >= 0; --l) {
+    const R cb = (R)std::cos(beta[l]), snb = (R)(-std::sin(beta[l]));
+    for (int q = np - 1; q >= 0; --q) {
+      double* dst = part + (size_t)(2 + p + (size_t)l * np + q) * kXYPartStride;
+      note_launch(0, st, true);
+      xy_gate_adjoint_kernel<T><<<gg, kXYThreads, 0, st>>>(s, psi, lam, pr[q][0], pr[q][1], cb, snb, dst);
+      note_launch(0, st, false, (double)moved * 4 * sb);
+    }
+    note_launch(0, st, true);
+    xy_cost_adjoint_kernel<T><<<gr, kXYThreads, 0, st>>>(psi, lam, cost->C_dev, cost->dtype, s.D,
+                                                         tab ? tab + (size_t)l * span : nullptr, cost->cmin, span,
+                                                         gamma[l], part + (size_t)(2 + l) * kXYPartStride);
+    note_launch(0, st, false, (double)s.D * (4 * sb + cost_bytes(cost->dtype)));
+    rc = status_of(cudaGetLastError());
+    if (rc) return rc;
+  }
+  XYReducePlan rp;
+  std::memset(&rp, 0, sizeof(rp));
+  rp.nout = 2 + 2 * p;
+  for (int o = 0; o < 2; ++o) rp.first[o] = o, rp.rows[o] = 1, rp.cols[o] = (int)gr;
+  for (int l = 0; l < p; ++l) {
+    rp.first[2 + l] = 2 + l, rp.rows[2 + l] = 1, rp.cols[2 + l] = (int)gr;
+    rp.first[2 + p + l] = 2 + p + l * np, rp.rows[2 + p + l] = np, rp.cols[2 + p + l] = (int)gg;
+  }
+  note_launch(3, st, true);
+  xy_grad_reduce_kernel<<<rp.nout, kXYThreads, 0, st>>>(rp, part, out);
+  note_launch(3, st, false);
+  return status_of(cudaGetLastError());
+}
+
 }  // namespace
 }  // namespace qaoa
 
@@ -517,6 +731,38 @@ int qaoa_xy_apply_layers(int n, int k, int dtype, void* psi_dev, const qaoa_cost
   const int rc = dtype == QAOA_C128
                      ? layers_t<double2>(*s, (double2*)psi_dev, cost, gamma, beta, p, init, expect_dev, (char*)ws_dev, st)
                      : layers_t<float2>(*s, (float2*)psi_dev, cost, gamma, beta, p, init, expect_dev, (char*)ws_dev, st);
+  delete s;
+  return rc;
+}
+
+int qaoa_xy_gradient_workspace_size(int n, int k, int dtype, int p, int64_t cost_span, size_t* bytes) {
+  if (bytes == nullptr || !shape_ok(n, k) || !dtype_ok(dtype) || p < 0 || p > QAOA_MAX_P || cost_span < 0)
+    return QAOA_ERR_INVALID_ARG;
+  *bytes = ws_bytes_for(dtype, p, cost_span <= QAOA_MAX_TABLE_SPAN ? cost_span : 0) + xy_grad_part_bytes(n, k, p);
+  return QAOA_OK;
+}
+
+int qaoa_xy_gradient(int n, int k, int dtype, void* psi_dev, void* lam_dev, const qaoa_cost_t* cost,
+                     const double* gamma, const double* beta, int p, double* out_dev, void* ws_dev, size_t ws_bytes,
+                     void* stream) {
+  if (!shape_ok(n, k) || !dtype_ok(dtype) || psi_dev == nullptr || lam_dev == nullptr || psi_dev == lam_dev ||
+      out_dev == nullptr || p < 0 || p > QAOA_MAX_P || !cost_ok(cost))
+    return QAOA_ERR_INVALID_ARG;
+  if (p > 0 && (gamma == nullptr || beta == nullptr)) return QAOA_ERR_INVALID_ARG;
+  for (int l = 0; l < p; ++l)
+    if (!std::isfinite(gamma[l]) || !std::isfinite(beta[l])) return QAOA_ERR_INVALID_ARG;
+  if (ws_dev == nullptr || ((uintptr_t)ws_dev & 255) != 0) return QAOA_ERR_INVALID_ARG;
+  size_t need = 0;
+  qaoa_xy_gradient_workspace_size(n, k, dtype, p, p > 0 ? table_span(cost) : 0, &need);
+  if (ws_bytes < need) return QAOA_ERR_WORKSPACE;
+  XYShape* s = new XYShape;
+  fill_shape(*s, n, k);
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int rc = dtype == QAOA_C128
+                     ? gradient_t<double2>(*s, (double2*)psi_dev, (double2*)lam_dev, cost, gamma, beta, p, out_dev,
+                                           (char*)ws_dev, st)
+                     : gradient_t<float2>(*s, (float2*)psi_dev, (float2*)lam_dev, cost, gamma, beta, p, out_dev,
+                                          (char*)ws_dev, st);
   delete s;
   return rc;
 }

@@ -56,6 +56,33 @@ int main() {
       if (fails++ < 10) printf("cmul_hi mismatch e=%d: %lld %lld vs %lld %lld\n", e, a.x, a.y, b.x, b.y);
     }
   }
+  // prepared factors (and their conjugates): full form within one unit; without the low
+  // products within one unit for e >= 3 and within three units for e = 0
+  for (int it = 0; it < 1000000; ++it) {
+    const int bits = 1 + (int)(rng() % 61);
+    const long long lim = (1ll << bits) - 1;
+    const long long xr = (long long)(rng() % (2 * (unsigned long long)lim + 1)) - lim;
+    const long long xi = (long long)(rng() % (2 * (unsigned long long)lim + 1)) - lim;
+    const double th = ang(rng);
+    long long ur = q62(std::cos(th)), ui = q62(std::sin(th));
+    if (it % 97 == 0) { ur = 1ll << 62; ui = 0; }
+    if (it % 89 == 0) { ur = 0; ui = -(1ll << 62); }
+    const Factor f = factor(ur, ui);
+    const int e = (it & 1) ? 0 : 3 + (int)(rng() % 11);
+    const long long tol_hi = e == 0 ? 3 : 1;
+    const C64 b = cmul_q62_exact(xr, xi, ur, ui, e), bc = cmul_q62_exact(xr, xi, ur, -ui, e);
+    const C64 a[4] = {cmul_factor<true, false>(xr, xi, f, e), cmul_factor<true, true>(xr, xi, f, e),
+                      cmul_factor<false, false>(xr, xi, f, e), cmul_factor<false, true>(xr, xi, f, e)};
+    for (int k = 0; k < 4; ++k) {
+      const C64& want = (k & 1) ? bc : b;
+      const long long tol = k < 2 ? 1 : tol_hi;
+      const long long dx = a[k].x - want.x, dy = a[k].y - want.y;
+      if (dx > tol || dx < -tol || dy > tol || dy < -tol) {
+        if (fails++ < 10) printf("cmul_factor<%d> mismatch e=%d: %lld %lld vs %lld %lld\n", k, e, a[k].x, a[k].y,
+                                 want.x, want.y);
+      }
+    }
+  }
   for (int it = 0; it < 1000000; ++it) {
     const long long x = (long long)(rng() >> (rng() % 63)) * ((rng() & 1) ? 1 : -1);
     const int s = (int)(rng() % 120);

@@ -263,6 +263,29 @@ def test_xy_calls_reject_bad_arguments_before_launch():
     assert q.lib.qaoa_xy_expectation(10, 5, q.C64, fake, ct.byref(cost), None, fake, 1 << 20, None) == E
 
 
+def test_xy_gradient_rejects_bad_arguments_before_launch():
+    fake, other = ct.c_void_p(1 << 20), ct.c_void_p(1 << 24)  # never dereferenced
+    cost = q.CostT(1 << 21, q.COST_I32, 0, 10)
+    gm = (ct.c_double * 2)(0.1, 0.2)
+    ok_b = (ct.c_double * 2)(0.3, 0.4)
+    bad_b = (ct.c_double * 2)(0.3, float("inf"))
+    out = ct.c_void_p(1 << 22)
+    need = ct.c_size_t()
+    assert q.lib.qaoa_xy_gradient_workspace_size(10, 5, q.C128, 2, 11, ct.byref(need)) == q.QAOA_OK
+    assert need.value > 0
+    E = q.QAOA_ERR_INVALID_ARG
+    call = lambda n, k, psi, lam, c, b, o, ws, wsb: q.lib.qaoa_xy_gradient(n, k, q.C128, psi, lam, c, gm, b, 2, o, ws,
+                                                                           wsb, None)
+    assert call(10, 5, fake, fake, ct.byref(cost), ok_b, out, fake, need.value) == E       # psi == lambda
+    assert call(10, 5, fake, None, ct.byref(cost), ok_b, out, fake, need.value) == E       # no lambda
+    assert call(10, 5, fake, other, ct.byref(cost), ok_b, None, fake, need.value) == E     # no output
+    assert call(10, 5, fake, other, None, ok_b, out, fake, need.value) == E                # no cost
+    assert call(10, 11, fake, other, ct.byref(cost), ok_b, out, fake, need.value) == E     # k > n
+    assert call(10, 5, fake, other, ct.byref(cost), bad_b, out, fake, need.value) == E     # non-finite angle
+    assert call(10, 5, fake, other, ct.byref(cost), ok_b, out, ct.c_void_p((1 << 20) + 8), need.value) == E
+    assert call(10, 5, fake, other, ct.byref(cost), ok_b, out, fake, need.value - 1) == q.QAOA_ERR_WORKSPACE
+
+
 def test_xy_binding_checks_buffer_sizes_first():
     torch = pytest.importorskip("torch")
     cv = q.CostVector(torch.zeros(q.xy_dim(10, 5), dtype=torch.int32), 10)

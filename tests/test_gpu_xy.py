@@ -103,6 +103,61 @@ def test_xy_layers_match_oracle(n, k, dtype, integer):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,k", CASES)
+@pytest.mark.parametrize("integer", [True, False])
+def test_xy_gradient_matches_oracle(n, k, dtype, integer):
+    """The subspace adjoint gradient against oracle/xy.py's (one 2 Im <lambda|H_g|psi_g> term
+    per gate, pinned to central differences); complex128 within 1e-10 max(1, sum|w|),
+    complex64 within 1e-4 max(1, |value|) per entry."""
+    q, g, cv, C, rng = make(n, k, 0.5, seed=2000 + 37 * n + k + (0 if integer else 5), integer=integer)
+    p = 3
+    gammas, betas = rng.uniform(-1.2, 1.2, p), rng.uniform(-1.2, 1.2, p)
+    psi, lam = q.xy_new_state(n, k, dtype), q.xy_new_state(n, k, dtype)
+    out = q.xy_gradient(psi, lam, n, k, cv, gammas, betas).cpu().numpy()
+    E, dg, db = ox.xy_adjoint_gradient(n, k, C, gammas, betas)
+    ref = np.concatenate([[E], dg, db])
+    got = np.concatenate([out[:1], out[2:]])
+    if dtype == "c128":
+        scale = max(1.0, float(np.abs(g.weights).sum())) if g.m else 1.0
+        assert np.max(np.abs(got - ref)) <= 1e-10 * scale
+        assert abs(out[1] - 1.0) < 1e-12
+        dicke = np.full(comb(n, k), 1.0 / np.sqrt(comb(n, k)))
+        assert np.max(np.abs(psi.cpu().numpy() - dicke)) < 1e-12  # the pass undoes every gate
+    else:
+        assert np.all(np.abs(got - ref) <= 1e-4 * np.maximum(1.0, np.abs(ref)))
+        assert abs(out[1] - 1.0) < 1e-5
+
+
+def test_xy_gradient_at_bench_size_is_consistent():
+    """n = 24, k = 12 (2.7e6 amplitudes): no full-space oracle, so the complex128 gradient
+    is checked against the complex64 one and against the device's own central differences
+    of <C> (h = 1e-5) for one angle of each kind."""
+    q = _q()
+    n, k = 24, 12
+    rng = np.random.default_rng(7)
+    edges = [(j, (j + 1) % n) for j in range(n)] + [(j, (j + n // 2) % n) for j in range(n // 2)]
+    w = rng.integers(1, 11, len(edges)).astype(np.float64)
+    g = q.Graph(n, np.array(edges, dtype=np.int32), w, integer=True)
+    cv = q.xy_cost_vector(g, k, "i32")
+    gammas, betas = rng.uniform(0, np.pi, 2), rng.uniform(0, np.pi, 2)
+    psi, lam = q.xy_new_state(n, k, "c128"), q.xy_new_state(n, k, "c128")
+    out = q.xy_gradient(psi, lam, n, k, cv, gammas, betas).cpu().numpy()
+    p32, l32 = q.xy_new_state(n, k, "c64"), q.xy_new_state(n, k, "c64")
+    out32 = q.xy_gradient(p32, l32, n, k, cv, gammas, betas).cpu().numpy()
+    assert np.all(np.abs(out32 - out) <= 1e-4 * np.maximum(1.0, np.abs(out)))
+    h = 1e-5
+
+    def energy(gm, bt):
+        st = q.xy_new_state(n, k, "c128")
+        return q.xy_apply_layers(st, n, k, cv, gm, bt, init=True, expect=True).cpu().numpy()[0]
+
+    fd_g = (energy(gammas + [h, 0], betas) - energy(gammas - [h, 0], betas)) / (2 * h)
+    fd_b = (energy(gammas, betas + [0, h]) - energy(gammas, betas - [0, h])) / (2 * h)
+    scale = float(w.sum())
+    assert abs(out[2] - fd_g) <= 1e-6 * scale and abs(out[2 + 2 + 1] - fd_b) <= 1e-6 * scale
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_xy_layers_continue_from_a_given_state(dtype):
     n, k = 11, 4
     q, g, cv, C, rng = make(n, k, 0.4, seed=99)
