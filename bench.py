@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-ratio measurement")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched workload: the library's default tile per qubit count instead of the autotuner's")
     ap.add_argument("--ttr-graphs", type=int, default=256)
     ap.add_argument("--ttr-target", type=float, default=0.88)
     ap.add_argument("--jsonl", default=None, help="also append the JSON line to this file (a run log)")
@@ -330,7 +332,7 @@ BATCH_WORKLOAD = ("{g} graphs, n ~ U{{8..20}}, half random 3-regular / half G(n,
                   "p=3, own angles per graph: <C> + adjoint gradient of every graph")
 
 
-def measure_batched(q, dev, dtype: str, count: int, reps: int = 3):
+def measure_batched(q, dev, dtype: str, count: int, reps: int = 3, autotune: bool = True):
     """The batched workload: one persistent launch over all graphs against the plain path
     (cost vector + gradient per graph, one graph at a time), both timed with CUDA events."""
     import torch
@@ -339,7 +341,8 @@ def measure_batched(q, dev, dtype: str, count: int, reps: int = 3):
     insts = synth.batch_instances(count, 1, p=p)
     graphs = [q.Graph(n, e, w, True) for (n, f, e, w, g, b) in insts]
     ang = np.stack([np.concatenate([g, b]) for (*_, g, b) in insts])
-    tiles, tune_ms = q.batch_autotune(dtype, p, 8, 20, graphs_per_n=152, device=dev)
+    # tile size per qubit count from the autotuner, or the library's default choice
+    tiles = q.batch_autotune(dtype, p, 8, 20, graphs_per_n=152, device=dev)[0] if autotune else None
     q.batch_gradient(graphs, ang, dtype, tiles=tiles, device=dev)
     torch.cuda.synchronize()
     ts = []
@@ -373,7 +376,8 @@ def measure_batched(q, dev, dtype: str, count: int, reps: int = 3):
     return {"workload": BATCH_WORKLOAD.format(g=count), "state_dtype": dtype,
             "graph_grads_per_s": count / (batched_ms / 1e3), "batched_ms": batched_ms, "plain_ms": plain_ms,
             "speedup": plain_ms / batched_ms, "max_abs_diff_vs_plain": agree,
-            "tiles": {int(n): int(tiles[n]) for n in range(8, 21)}, "launches": "1 prep + 1 persistent per tile size",
+            "tiles": {int(n): int(tiles[n]) for n in range(8, 21)} if tiles is not None else "library default",
+            "launches": "1 prep + 1 persistent per tile size",
             "timing": "CUDA events, median of %d batched runs; plain: one run over all graphs" % reps}
 
 
@@ -682,7 +686,7 @@ def run_batched(a):
     torch.cuda.set_device(local)
     import paper_2407_13012_gb300 as q
     dev = torch.device("cuda", local)
-    res = measure_batched(q, dev, a.dtype, a.batch_graphs, reps=a.steps)
+    res = measure_batched(q, dev, a.dtype, a.batch_graphs, reps=a.steps, autotune=not a.no_autotune)
     if rank == 0:
         emit({"metric": "batched adjoint gradients (graph gradients/s)", "value": res["graph_grads_per_s"],
               "unit": "graph gradients/s", "n_gpus": 1, "steps": a.steps, "warmup": 1,
