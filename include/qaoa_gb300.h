@@ -492,6 +492,23 @@ int qaoa_xy_apply_layers(int n, int k, int dtype, void* psi_dev, const qaoa_cost
 int qaoa_xy_expectation(int n, int k, int dtype, const void* psi_dev, const qaoa_cost_t* cost, double* out_dev,
                         void* ws_dev, size_t ws_bytes, void* stream);
 
+/* Bytes of device scratch for qaoa_xy_sample.  Host-only. */
+int qaoa_xy_sample_workspace_size(int n, int k, size_t* bytes);
+
+/*
+ * Bitstring samples of a subspace state (the sampling of Sec. IV-D over F_k): with
+ * P the running sum of |psi_r|^2 in rank order, shot i draws u_i from the same
+ * SplitMix64 stream as qaoa_sample (seed, i) and takes the rank
+ * r_i = min{r : P(r) > u_i P_total} (the last rank with nonzero probability when
+ * rounding puts the target past the end); z_dev[i] receives the state of F_k with
+ * that rank (a bitstring with k ones) and cost_dev[i] = C(z_i) from the subspace
+ * cost vector.  Rank order is increasing z, so this equals qaoa_sample on the state
+ * embedded in 2^n amplitudes.  Errors as for qaoa_sample; QAOA_ERR_WORKSPACE below
+ * qaoa_xy_sample_workspace_size.
+ */
+int qaoa_xy_sample(int n, int k, int dtype, const void* psi_dev, const qaoa_cost_t* cost, int64_t shots,
+                   uint64_t seed, uint64_t* z_dev, double* cost_dev, void* ws_dev, size_t ws_bytes, void* stream);
+
 /* Bytes of device scratch for qaoa_xy_gradient (depth p, integer cost span as
  * for qaoa_xy_workspace_size).  Host-only. */
 int qaoa_xy_gradient_workspace_size(int n, int k, int dtype, int p, int64_t cost_span, size_t* bytes);

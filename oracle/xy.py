@@ -134,6 +134,23 @@ def xy_expectation(psi_sub: np.ndarray, C_sub: np.ndarray):
     return float(np.sum(np.asarray(C_sub, dtype=np.float64) * pr)), float(np.sum(pr))
 
 
+def xy_sample(psi_sub: np.ndarray, n: int, k: int, C_sub: np.ndarray, u: np.ndarray):
+    """Inverse-CDF sampling (Sec. IV-D) of a subspace state: r_i = min{r : P(r) > u_i P_total}
+    with P the inclusive running sum of |psi_r|**2 in rank order, the last rank with nonzero
+    probability when rounding puts the target at or past the end.  Rank order is increasing
+    z, so this is the full-space rule applied to the state embedded in 2**n amplitudes (the
+    zeros off F_k add nothing to the running sum).  Returns (z uint64 of rank r_i, C_sub[r_i])."""
+    prob = psi_sub.real ** 2 + psi_sub.imag ** 2
+    P = np.cumsum(prob)
+    total = P[-1]
+    r = np.searchsorted(P, np.asarray(u, dtype=np.float64) * total, side="right")
+    nz = np.nonzero(prob > 0)[0]
+    last = nz[-1] if len(nz) else len(prob) - 1
+    r = np.minimum(r, last)
+    states = feasible_states(n, k)
+    return states[r].astype(np.uint64), np.asarray(C_sub, dtype=np.float64)[r]
+
+
 def xy_adjoint_gradient(n: int, k: int, C: np.ndarray, gammas, betas):
     """[E, dE/dgamma_1..p, dE/dbeta_1..p] of E = <psi|C|psi> for the subspace QAOA above.
 

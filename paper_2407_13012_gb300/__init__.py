@@ -96,6 +96,8 @@ def _load() -> ct.CDLL:
         "qaoa_xy_apply_layers": ([i32, i32, i32, vp, ct.POINTER(CostT), dp, dp, i32, i32, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_xy_expectation": ([i32, i32, i32, vp, ct.POINTER(CostT), vp, vp, ct.c_size_t, vp], i32),
         "qaoa_xy_gradient_workspace_size": ([i32, i32, i32, i32, i64, szp], i32),
+        "qaoa_xy_sample_workspace_size": ([i32, i32, szp], i32),
+        "qaoa_xy_sample": ([i32, i32, i32, vp, ct.POINTER(CostT), i64, u64, vp, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_xy_gradient": ([i32, i32, i32, vp, vp, ct.POINTER(CostT), dp, dp, i32, vp, vp, ct.c_size_t, vp], i32),
         "qaoa_launch_count": ([], i64),
         "qaoa_launch_count_reset": ([], None),
@@ -683,6 +685,25 @@ def xy_gradient(psi, lam, n: int, k: int, cost: CostVector, gammas, betas):
                                  gp, bp, len(g), ct.c_void_p(out.data_ptr()), ct.c_void_p(ws.data_ptr()), ws.numel(),
                                  ct.c_void_p(_stream(psi.device))), "xy_gradient")
     return out
+
+
+def xy_sample(psi, n: int, k: int, cost: CostVector, shots: int, seed: int):
+    """Samples of a subspace state: (z bitstrings with k ones as an int64 tensor, cost float64
+    tensor) on the device, in draw order."""
+    torch = _torch()
+    _xy_sizes(n, k, psi, cost)
+    _require_cuda(psi)
+    dt = _dtype_code(psi)
+    nb = ct.c_size_t()
+    _check(_lib.qaoa_xy_sample_workspace_size(n, k, ct.byref(nb)), "xy_sample_workspace_size")
+    ws = _workspace(nb.value, psi.device)
+    z = torch.empty(max(shots, 1), dtype=torch.int64, device=psi.device)
+    cz = torch.empty(max(shots, 1), dtype=torch.float64, device=psi.device)
+    cs = cost.struct()
+    _check(_lib.qaoa_xy_sample(n, k, dt, ct.c_void_p(psi.data_ptr()), ct.byref(cs), shots,
+                               ct.c_uint64(seed & (2**64 - 1)), ct.c_void_p(z.data_ptr()), ct.c_void_p(cz.data_ptr()),
+                               ct.c_void_p(ws.data_ptr()), ws.numel(), ct.c_void_p(_stream(psi.device))), "xy_sample")
+    return z[:shots], cz[:shots]
 
 
 def launch_count() -> int:

@@ -170,6 +170,7 @@ cudaError_t launch_pubo(const PuboArgs& a, cudaStream_t s);
 // sampling
 struct SampleArgs {
   int n;
+  uint64_t len;     // entries of the sampled vector (0: 2^n); the returned z are indices into it
   int dtype;
   const void* psi;
   const void* C;
@@ -184,6 +185,7 @@ struct SampleArgs {
 };
 cudaError_t launch_sample(const SampleArgs& a, cudaStream_t s);
 size_t sample_ws_bytes(int n, int dtype);
+size_t sample_ws_bytes_len(uint64_t len);  // workspace for a vector of len entries
 
 // bookkeeping for benchmarks: call with begin = true before a launch and begin = false
 // after it; `bytes` (algorithmic HBM bytes of the launch) is read on the second call

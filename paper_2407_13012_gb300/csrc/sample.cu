@@ -37,17 +37,17 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// (1) one warp per leaf
+// (1) one warp per leaf; a.len entries (the last leaf may be partly past the end)
 __global__ void leaf_sum_kernel(const __grid_constant__ SampleArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t nleaf = 1ll << (a.n - a.leaf_bits);
   const uint32_t L = 1u << a.leaf_bits;
+  const int64_t nleaf = (int64_t)((a.len + L - 1) >> a.leaf_bits);
   for (int64_t li = warp; li < nleaf; li += nwarps) {
     const uint64_t base = (uint64_t)li << a.leaf_bits;
     double s = 0.0;
-    for (uint32_t k = lane; k < L; k += 32) s += prob_at(a.psi, a.dtype, base + k);
+    for (uint32_t k = lane; k < L && base + k < a.len; k += 32) s += prob_at(a.psi, a.dtype, base + k);
     s = warp_sum(s);
     if (lane == 0) a.leaf[li] = s;
   }
@@ -119,8 +119,8 @@ __global__ void draw_kernel(const __grid_constant__ SampleArgs a, const double* 
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t nleaf = 1ll << (a.n - a.leaf_bits);
   const uint32_t L = 1u << a.leaf_bits;
+  const int64_t nleaf = (int64_t)((a.len + L - 1) >> a.leaf_bits);
   const double total = prefix[nleaf];
   const uint64_t sbase = mix64(mix64(a.seed) ^ 0x5f5f656c706d6173ull);
   for (int64_t i = warp; i < a.shots; i += nwarps) {
@@ -141,12 +141,13 @@ __global__ void draw_kernel(const __grid_constant__ SampleArgs a, const double* 
         while (li > 0 && !(prefix[li + 1] > prefix[li])) --li;
     }
     const uint64_t base = (uint64_t)li << a.leaf_bits;
+    const uint32_t Lh = a.len - base < L ? (uint32_t)(a.len - base) : L;  // entries in this leaf
     const double rem = target - prefix[li];
     double run = 0.0;
     int64_t found = -1, last_nz = -1;
-    for (uint32_t k0 = 0; k0 < L && found < 0; k0 += 32) {
+    for (uint32_t k0 = 0; k0 < Lh && found < 0; k0 += 32) {
       const uint32_t k = k0 + lane;
-      const double pk = (k < L) ? prob_at(a.psi, a.dtype, base + k) : 0.0;
+      const double pk = (k < Lh) ? prob_at(a.psi, a.dtype, base + k) : 0.0;
       double incl = pk;
       for (int o = 1; o < 32; o <<= 1) {
         const double y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -158,7 +159,7 @@ __global__ void draw_kernel(const __grid_constant__ SampleArgs a, const double* 
       if (hit) found = k0 + __ffs(hit) - 1;
       run += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (found < 0) found = (last_nz >= 0 && total > 0.0) ? last_nz : (int64_t)L - 1;
+    if (found < 0) found = (last_nz >= 0 && total > 0.0) ? last_nz : (int64_t)Lh - 1;
     if (lane == 0) {
       const uint64_t z = base + (uint64_t)found;
       a.z[i] = z;
@@ -167,21 +168,29 @@ __global__ void draw_kernel(const __grid_constant__ SampleArgs a, const double* 
   }
 }
 
-int leaf_bits_for(int n) { return n < 10 ? n : 10; }
+// leaves of 2^10 entries, or one leaf of 2^ceil(log2 len) for shorter vectors (2^n: min(n, 10))
+int leaf_bits_for_len(uint64_t len) {
+  int lb = 0;
+  while (lb < 10 && (1ull << lb) < len) ++lb;
+  return lb;
+}
 
 }  // namespace
 
-size_t sample_ws_bytes(int n, int /*dtype*/) {
-  const int lb = leaf_bits_for(n);
-  const int64_t nleaf = 1ll << (n - lb);
+size_t sample_ws_bytes_len(uint64_t len) {
+  const int lb = leaf_bits_for_len(len);
+  const int64_t nleaf = (int64_t)((len + (1ull << lb) - 1) >> lb);
   const int64_t nchunks = (nleaf + kChunk - 1) / kChunk;
   return (size_t)(nleaf + (nleaf + 1) + (nchunks + 1)) * sizeof(double) + 3 * 256;
 }
 
+size_t sample_ws_bytes(int n, int /*dtype*/) { return sample_ws_bytes_len(1ull << n); }
+
 cudaError_t launch_sample(const SampleArgs& a0, cudaStream_t s) {
   SampleArgs a = a0;
-  a.leaf_bits = leaf_bits_for(a.n);
-  const int64_t nleaf = 1ll << (a.n - a.leaf_bits);
+  if (a.len == 0) a.len = 1ull << a.n;
+  a.leaf_bits = leaf_bits_for_len(a.len);
+  const int64_t nleaf = (int64_t)((a.len + (1ull << a.leaf_bits) - 1) >> a.leaf_bits);
   const int64_t nchunks = (nleaf + kChunk - 1) / kChunk;
   // carve the workspace: leaf sums, prefix, chunk sums (256-byte aligned pieces)
   char* p = (char*)a.leaf;
@@ -205,7 +214,7 @@ cudaError_t launch_sample(const SampleArgs& a0, cudaStream_t s) {
     if (blocks > (int64_t)sms * 16) blocks = (int64_t)sms * 16;
     leaf_sum_kernel<<<(int)blocks, kThreads, 0, s>>>(a);
   }
-  note_launch(2, s, false, (double)(1ull << a.n) * (a.dtype == QAOA_C128 ? 16.0 : 8.0));
+  note_launch(2, s, false, (double)a.len * (a.dtype == QAOA_C128 ? 16.0 : 8.0));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   note_launch(3, s, true);

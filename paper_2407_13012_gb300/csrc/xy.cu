@@ -211,6 +211,15 @@ __global__ void xy_phase_kernel(T* __restrict__ psi, const void* __restrict__ C,
   }
 }
 
+// sampled ranks -> the states of F_k they index (in place)
+__global__ void __launch_bounds__(kXYThreads) xy_unrank_kernel(const __grid_constant__ XYShape s,
+                                                                unsigned long long* __restrict__ z, long long shots) {
+  __shared__ unsigned long long B[kBN][kBN];
+  load_binom(B, s);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < shots; i += (long long)gridDim.x * blockDim.x)
+    z[i] = xy_unrank(z[i], s.n, s.k, B);
+}
+
 // ------------------------------------------------------------------ adjoint gradient on F_k
 //
 // The circuit is a sequence of gates exp(-i theta H_g): per layer the cost unitary
@@ -763,6 +772,51 @@ int qaoa_xy_gradient(int n, int k, int dtype, void* psi_dev, void* lam_dev, cons
                                            (char*)ws_dev, st)
                      : gradient_t<float2>(*s, (float2*)psi_dev, (float2*)lam_dev, cost, gamma, beta, p, out_dev,
                                           (char*)ws_dev, st);
+  delete s;
+  return rc;
+}
+
+int qaoa_xy_sample_workspace_size(int n, int k, size_t* bytes) {
+  if (bytes == nullptr || !shape_ok(n, k)) return QAOA_ERR_INVALID_ARG;
+  XYShape s;
+  fill_shape(s, n, k);
+  *bytes = round256(sample_ws_bytes_len(s.D));
+  return QAOA_OK;
+}
+
+int qaoa_xy_sample(int n, int k, int dtype, const void* psi_dev, const qaoa_cost_t* cost, int64_t shots,
+                   uint64_t seed, uint64_t* z_dev, double* cost_dev, void* ws_dev, size_t ws_bytes, void* stream) {
+  if (!shape_ok(n, k) || !dtype_ok(dtype) || psi_dev == nullptr || !cost_ok(cost) || shots < 0)
+    return QAOA_ERR_INVALID_ARG;
+  if (shots > 0 && (z_dev == nullptr || cost_dev == nullptr)) return QAOA_ERR_INVALID_ARG;
+  if (ws_dev == nullptr || ((uintptr_t)ws_dev & 255) != 0) return QAOA_ERR_INVALID_ARG;
+  size_t need = 0;
+  qaoa_xy_sample_workspace_size(n, k, &need);
+  if (ws_bytes < need) return QAOA_ERR_WORKSPACE;
+  XYShape* s = new XYShape;
+  fill_shape(*s, n, k);
+  SampleArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n;
+  a.len = s->D;  // the sampler walks the subspace vector in rank order and returns ranks
+  a.dtype = dtype;
+  a.psi = psi_dev;
+  a.C = cost->C_dev;
+  a.cost_dtype = cost->dtype;
+  a.shots = shots;
+  a.seed = seed;
+  a.z = z_dev;
+  a.cost = cost_dev;
+  a.leaf = (double*)ws_dev;
+  const cudaStream_t st = (cudaStream_t)stream;
+  int rc = status_of(launch_sample(a, st));
+  if (rc == QAOA_OK && shots > 0) {
+    note_launch(3, st, true);
+    xy_unrank_kernel<<<grid_for((unsigned long long)shots, sm_count()), kXYThreads, 0, st>>>(
+        *s, (unsigned long long*)z_dev, shots);
+    note_launch(3, st, false);
+    rc = status_of(cudaGetLastError());
+  }
   delete s;
   return rc;
 }

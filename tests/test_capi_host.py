@@ -286,6 +286,23 @@ def test_xy_gradient_rejects_bad_arguments_before_launch():
     assert call(10, 5, fake, other, ct.byref(cost), ok_b, out, fake, need.value - 1) == q.QAOA_ERR_WORKSPACE
 
 
+def test_xy_sample_rejects_bad_arguments_before_launch():
+    fake = ct.c_void_p(1 << 20)
+    cost = q.CostT(1 << 21, q.COST_I32, 0, 10)
+    need = ct.c_size_t()
+    assert q.lib.qaoa_xy_sample_workspace_size(10, 5, ct.byref(need)) == q.QAOA_OK and need.value > 0
+    assert q.lib.qaoa_xy_sample_workspace_size(10, 11, ct.byref(need)) == q.QAOA_ERR_INVALID_ARG
+    E = q.QAOA_ERR_INVALID_ARG
+    s = lambda n, k, dt, psi, c, shots, z, ws, wsb: q.lib.qaoa_xy_sample(n, k, dt, psi, c, shots, 1, z, z, ws, wsb, None)
+    assert s(10, 5, q.C128, None, ct.byref(cost), 10, fake, fake, 1 << 20) == E           # no state
+    assert s(10, 5, q.C128, fake, None, 10, fake, fake, 1 << 20) == E                     # no cost
+    assert s(10, 5, q.C128, fake, ct.byref(cost), -1, fake, fake, 1 << 20) == E           # negative shots
+    assert s(10, 5, q.C128, fake, ct.byref(cost), 10, None, fake, 1 << 20) == E           # no output
+    assert s(10, 5, 7, fake, ct.byref(cost), 10, fake, fake, 1 << 20) == E                # dtype
+    assert s(10, 5, q.C128, fake, ct.byref(cost), 10, fake, ct.c_void_p((1 << 20) + 8), 1 << 20) == E
+    assert s(10, 5, q.C128, fake, ct.byref(cost), 10, fake, fake, 16) == q.QAOA_ERR_WORKSPACE
+
+
 def test_xy_binding_checks_buffer_sizes_first():
     torch = pytest.importorskip("torch")
     cv = q.CostVector(torch.zeros(q.xy_dim(10, 5), dtype=torch.int32), 10)

@@ -158,6 +158,59 @@ def test_xy_gradient_at_bench_size_is_consistent():
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n,k", CASES)
+def test_xy_sample_matches_oracle(n, k, dtype):
+    """Sampling on F_k (Sec. IV-D over the subspace) against oracle/xy.py's xy_sample under
+    the same uniforms: mismatches only where a target lies within rounding of a CDF step
+    (<= 1e-5 of the shots), every bitstring has k ones and its cost is C(z) exactly."""
+    import synth
+    q, g, cv, C, rng = make(n, k, 0.5, seed=3000 + 37 * n + k)
+    gammas, betas = rng.uniform(-1.2, 1.2, 2), rng.uniform(-1.2, 1.2, 2)
+    psi = q.xy_new_state(n, k, dtype)
+    q.xy_apply_layers(psi, n, k, cv, gammas, betas)
+    ref_in = psi.cpu().numpy().astype(np.complex128)  # exactly the values the sampler reads
+    shots, seed = 20000, 77 + n
+    z, cz = q.xy_sample(psi, n, k, cv, shots, seed)
+    z, cz = z.cpu().numpy().astype(np.uint64), cz.cpu().numpy()
+    zr, cr = ox.xy_sample(ref_in, n, k, ox.subspace_costs(C, n, k), synth.sample_uniforms(seed, shots))
+    assert np.mean(z != zr) <= 1e-5
+    assert all(bin(int(x)).count("1") == k for x in z[:2000])
+    assert np.array_equal(cz, C[z.astype(np.int64)].astype(np.float64))
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_xy_sample_ragged_multichunk(dtype):
+    """n = 26, k = 13: binom(26, 13) = 10,400,600 amplitudes, a ragged last leaf and three
+    scan chunks (4096 leaves of 1024 each); mass in the last entries of the last leaf too."""
+    import synth
+    q = _q()
+    n, k = 26, 13
+    D = comb(n, k)
+    rng = np.random.default_rng(11)
+    edges, w = random_graph(rng, n, 0.15, integer=True)
+    g = q.Graph(n, np.array(edges, dtype=np.int32).reshape(-1, 2), w, integer=True)
+    cv = q.xy_cost_vector(g, k, "i32")
+    Csub = cv.C.cpu().numpy().astype(np.int64)
+    u = synth.uniforms(5, "state", 2 * D).reshape(-1, 2) - 0.5
+    amp = u[:, 0] + 1j * u[:, 1]
+    amp[-40:] *= 30.0  # weight on the ragged end
+    amp /= np.linalg.norm(amp)
+    tdt = torch.complex128 if dtype == "c128" else torch.complex64
+    psi = torch.as_tensor(amp).to(tdt).cuda()
+    ref_in = psi.cpu().numpy().astype(np.complex128)
+    shots, seed = 100000, 123
+    z, cz = q.xy_sample(psi, n, k, cv, shots, seed)
+    z, cz = z.cpu().numpy().astype(np.uint64), cz.cpu().numpy()
+    zr, cr = ox.xy_sample(ref_in, n, k, Csub, synth.sample_uniforms(seed, shots))
+    assert np.mean(z != zr) <= 1e-5
+    assert np.array_equal(cz, cr)
+    states = ox.feasible_states(n, k)
+    assert np.sum(z >= np.uint64(states[-40])) > 0  # the ragged end is reached
+    del psi
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_xy_layers_continue_from_a_given_state(dtype):
     n, k = 11, 4
     q, g, cv, C, rng = make(n, k, 0.4, seed=99)

@@ -14,6 +14,8 @@ from scipy.linalg import expm
 from oracle import qaoa as oq
 from oracle import xy as ox
 
+import synth
+
 _I = np.eye(2, dtype=np.complex128)
 _X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
 _Y = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
@@ -189,3 +191,36 @@ def test_adjoint_gradient_vanishes_where_the_mixer_cannot_act():
     C = oq.cut_values(n, [(0, 1), (1, 2), (2, 4)], [1.0, 2.0, 3.0])
     E, dg, db = ox.xy_adjoint_gradient(n, 0, C, [0.3, 0.5], [0.2, -0.4])
     assert E == 0.0 and np.all(dg == 0) and np.all(db == 0)
+
+
+@pytest.mark.parametrize("n,k", [(1, 0), (1, 1), (4, 2), (7, 3), (10, 5), (12, 4)])
+def test_subspace_sampling_equals_full_space_sampling(n, k):
+    """Rank order is increasing z, so sampling the subspace vector must give exactly the
+    full-space sampler's bitstrings for the same state embedded in 2**n amplitudes."""
+    rng = np.random.default_rng(31 * n + k)
+    edges = [(u, v) for u in range(n) for v in range(u + 1, n) if rng.random() < 0.5]
+    w = rng.integers(1, 11, len(edges)).astype(np.float64)
+    C = oq.cut_values(n, edges, w) if edges else np.zeros(1 << n, dtype=np.int64)
+    psi = ox.xy_state(n, k, C, rng.uniform(0, 1, 2), rng.uniform(0, 1, 2))
+    u = synth.sample_uniforms(5 + n, 5000)
+    z_full, c_full = oq.sample(psi, C, u)
+    z_sub, c_sub = ox.xy_sample(ox.restrict(psi, n, k), n, k, ox.subspace_costs(C, n, k), u)
+    assert np.array_equal(z_full, z_sub) and np.array_equal(c_full, c_sub)
+    assert all(bin(int(z)).count("1") == k for z in z_sub[:200])
+
+
+def test_subspace_sampling_chi_square():
+    n, k = 10, 4
+    rng = np.random.default_rng(3)
+    psi = rng.normal(size=comb(n, k)) + 1j * rng.normal(size=comb(n, k))
+    psi /= np.linalg.norm(psi)
+    shots = 100000
+    z, _ = ox.xy_sample(psi, n, k, np.zeros(comb(n, k)), synth.sample_uniforms(9, shots))
+    states = ox.feasible_states(n, k)
+    idx = np.searchsorted(states, z.astype(np.int64))
+    assert np.array_equal(states[idx], z.astype(np.int64))
+    obs = np.bincount(idx, minlength=len(states))
+    prob = np.abs(psi) ** 2
+    chi2 = np.sum((obs - shots * prob) ** 2 / (shots * prob))
+    dof = len(states) - 1
+    assert chi2 < dof + 6 * np.sqrt(2 * dof)
