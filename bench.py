@@ -11,6 +11,13 @@ cost vector C(z), p layers with fused <C>, sampling, and the adjoint gradient
 Under torchrun every rank runs an independent replica (the simulation does not
 shard); timing is the max over ranks.  ``--impl reference`` times the FP64 CPU
 oracle on a bounded sample of the same workload on the host cores.
+
+Outside the timed step the line also carries: ``gradient`` (gradient evaluations per
+second), ``batched`` (4096 small graphs in one persistent launch against one at a time),
+``time_to_ratio`` (time for 256 graphs to reach an approximation ratio: batched or plain
+optimiser, from the linear ramp or the learned proposer) and ``cpu_baseline`` (the oracle
+on one core and on all host cores).  ``--workload batched|xy|ttr`` prints one of those
+measurements, or the Hamming-weight-subspace workload, as a line of its own.
 """
 from __future__ import annotations
 

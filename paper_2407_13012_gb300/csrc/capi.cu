@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -215,7 +216,10 @@ static int run_sweeps(const Ctx& c, std::vector<Sweep>& sw, const std::vector<Gr
   p_ws += partial_bytes(nout);
   const bool int_cost = c.cost->dtype == QAOA_COST_I32;
   int64_t cmin = 0, span = 0;
-  if (int_cost && c.cost->cmax >= c.cost->cmin && p > 0 && c.cost->cmax - c.cost->cmin + 1 <= QAOA_MAX_TABLE_SPAN) {
+  // a phase table over [cmin, cmax]: only for bounds inside int32 (the kernels index it in 32-bit
+  // arithmetic; int32 costs outside such bounds take the direct phase)
+  if (int_cost && c.cost->cmax >= c.cost->cmin && p > 0 && c.cost->cmax - c.cost->cmin + 1 <= QAOA_MAX_TABLE_SPAN &&
+      c.cost->cmin >= INT32_MIN && c.cost->cmax <= INT32_MAX) {
     span = c.cost->cmax - c.cost->cmin + 1;
     cmin = c.cost->cmin;
   }

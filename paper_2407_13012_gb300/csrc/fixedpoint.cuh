@@ -58,8 +58,9 @@ QAOA_HD long long round_shift(i128 v, int s) {
   return s > 0 ? (long long)((v + ((i128)1 << (s - 1))) >> s) : (long long)v;
 }
 
-// A value split into 32-bit limbs x = h * 2^32 + l with l signed, |l| <= 2^31.
-struct Limbs {
+// A value split into 32-bit limbs x = h * 2^32 + l with l signed, |l| <= 2^31 (8-byte
+// aligned, so a prepared factor in shared memory loads as three 64-bit words).
+struct alignas(8) Limbs {
   int h;
   int l;
 };

@@ -340,8 +340,10 @@ struct Sweeper {
     if (FX && !f64 && layer == ts_layer && Tf != nullptr) {  // prepared factors in shared memory
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const long long k = (long long)cost_i(Cs, idx(r)) - a.cmin;
-        if (k >= 0 && k < a.span) {
+        // table index in 32-bit arithmetic (the host keeps table bounds inside int32, so an
+        // entry outside [cmin, cmax] can never wrap into the table)
+        const uint32_t k = (uint32_t)cost_i(Cs, idx(r)) - (uint32_t)a.cmin;
+        if (k < (uint32_t)a.span) {
           if constexpr (FX) {
             const fx::C64 o = fx::cmul_factor<false, INV>(u[r].x, u[r].y, Tf[k], 0);
             u[r] = make_longlong2(o.x, o.y);
@@ -354,8 +356,10 @@ struct Sweeper {
       const V* tab = (layer == ts_layer && Ts != nullptr) ? Ts : (const V*)a.phase_table + (long long)layer * a.span;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const long long k = (long long)cost_i(Cs, idx(r)) - a.cmin;
-        if (k >= 0 && k < a.span) {
+        // table index in 32-bit arithmetic (the host keeps table bounds inside int32, so an
+        // entry outside [cmin, cmax] can never wrap into the table)
+        const uint32_t k = (uint32_t)cost_i(Cs, idx(r)) - (uint32_t)a.cmin;
+        if (k < (uint32_t)a.span) {
           V e = tab[k];
           if constexpr (INV) e.y = -e.y;
           u[r] = vmul(u[r], e);
@@ -385,8 +389,10 @@ struct Sweeper {
     if (FX && !f64 && layer == ts_layer && Tf != nullptr) {  // prepared factors in shared memory
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const long long k = (long long)cost_i(Cs, idx(r)) - a.cmin;
-        if (k >= 0 && k < a.span) {
+        // table index in 32-bit arithmetic (the host keeps table bounds inside int32, so an
+        // entry outside [cmin, cmax] can never wrap into the table)
+        const uint32_t k = (uint32_t)cost_i(Cs, idx(r)) - (uint32_t)a.cmin;
+        if (k < (uint32_t)a.span) {
           if constexpr (FX) {
             const fx::Factor& f = Tf[k];
             const fx::C64 o = fx::cmul_factor<false, INV>(v[r].x, v[r].y, f, 0);
@@ -402,8 +408,10 @@ struct Sweeper {
       const V* tab = (layer == ts_layer && Ts != nullptr) ? Ts : (const V*)a.phase_table + (long long)layer * a.span;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const long long k = (long long)cost_i(Cs, idx(r)) - a.cmin;
-        if (k >= 0 && k < a.span) {
+        // table index in 32-bit arithmetic (the host keeps table bounds inside int32, so an
+        // entry outside [cmin, cmax] can never wrap into the table)
+        const uint32_t k = (uint32_t)cost_i(Cs, idx(r)) - (uint32_t)a.cmin;
+        if (k < (uint32_t)a.span) {
           V e = tab[k];
           if constexpr (INV) e.y = -e.y;
           v[r] = vmul(v[r], e);
@@ -1128,15 +1136,21 @@ struct Lean : Sweeper<CF, FX, TWO> {
         const uint32_t kind = op & 0xff;
         const int layer = (op >> 16) & 0xff, acc = (int)((op >> 24) & 0xff);
         const bool inv = op & F_SIGN;
+        // every mixer returns to layout 0, where the elementwise ops run: restating cur = 0
+        // before each lets the compiler fold their register-to-index maps to constants
         if (kind == OP_MIX) {
           mixer<L>(layer, inv, (op & F_XTERM) ? acc : -1);
         } else if (kind == OP_PHASE) {
+          this->cur = 0;
           this->op_phase(layer, inv, true, TWO);
         } else if (kind == OP_LAMBDA) {
+          this->cur = 0;
           if constexpr (TWO) this->op_lambda();
         } else if (kind == OP_RED_EXPECT) {
+          this->cur = 0;
           this->op_expect(acc);
         } else if (kind == OP_RED_CTERM) {
+          this->cur = 0;
           if constexpr (TWO) this->op_cterm(acc);
         }
       }

@@ -182,6 +182,21 @@ def test_table_bounds_wrong_still_correct():
     assert np.linalg.norm(state_np(psi) - qaoa.qaoa_state(n, C, gam, bet)) <= 1e-11
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_table_bounds_outside_int32_still_correct(dtype):
+    # bounds no int32 cost can reach: the kernels skip the table and compute every phase
+    n = 10
+    g, e, w, integer = instance("gnp", n, 4, "int", prob=0.5)
+    C = qaoa.cut_values(n, e, w)
+    cv = q.cost_vector(g, "i32")
+    cv.cmin, cv.cmax = (1 << 40) - 3, (1 << 40) + 50
+    gam, bet = synth.angles(2, 5)
+    psi = q.new_state(n, dtype)
+    q.apply_layers(psi, cv, gam, bet)
+    err = np.linalg.norm(state_np(psi) - qaoa.qaoa_state(n, C, gam, bet))
+    assert err <= (1e-11 if dtype == "c128" else 1e-5)
+
+
 def test_empty_graph_and_zero_angles():
     n = 9
     g = q.Graph(n, np.zeros((0, 2), np.int32), None, True)
