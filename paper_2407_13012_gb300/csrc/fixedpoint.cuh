@@ -74,14 +74,27 @@ QAOA_HD Limbs split(long long x) {
   return r;
 }
 
+// a * b + c for 32-bit a, b and a 64-bit c.  On the device this is one multiply-add-wide
+// instruction; written as (long long)a * b + c the compiler emits a 64 x 64-bit multiply
+// (measured: 8 instead of 3 instructions per product, 74 instead of 42 per complex multiply).
+QAOA_HD long long madw(int a, int b, long long c) {
+#ifdef __CUDA_ARCH__
+  long long d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+#else
+  return (long long)a * b + c;
+#endif
+}
+
 // round((a b + c d) / 2^(62 + e)) for a, c with |.| < 2^61 and b, d Q62 with |.| <= 2^62,
 // 0 <= e <= 30, from eight 32x32 -> 64-bit products.  x y = xh yh 2^64 + (xh yl + xl yh) 2^32
 // + xl yl; the low products enter only through their high words, so the result can differ
 // from exact rounding by one unit when the exact value lies within 2^-29 units of a tie.
 QAOA_HD long long dot2_q62(Limbs a, Limbs b, Limbs c, Limbs d, int e) {
-  const long long P = (long long)a.h * b.h + (long long)c.h * d.h;
-  const long long M = (long long)a.h * b.l + (long long)a.l * b.h + (long long)c.h * d.l + (long long)c.l * d.h;
-  const long long Lh = (((long long)a.l * b.l) >> 32) + (((long long)c.l * d.l) >> 32);
+  const long long P = madw(c.h, d.h, madw(a.h, b.h, 0));
+  const long long M = madw(c.l, d.h, madw(c.h, d.l, madw(a.l, b.h, madw(a.h, b.l, 0))));
+  const long long Lh = (madw(a.l, b.l, 0) >> 32) + (madw(c.l, d.l, 0) >> 32);
   const long long T = M + Lh;  // value = P 2^64 + T 2^32 (up to the dropped low words)
   if (e <= 2) return (long long)((unsigned long long)P << (2 - e)) + ((T + (1ll << (29 + e))) >> (30 + e));
   return (P + ((T + (1ll << (29 + e))) >> 32)) >> (e - 2);
@@ -91,10 +104,28 @@ QAOA_HD long long dot2_q62(Limbs a, Limbs b, Limbs c, Limbs d, int e) {
 // so for e >= 3 the result is within one unit of exact rounding (two fewer 32 x 32-bit
 // products per call)
 QAOA_HD long long dot2_q62_hi(Limbs a, Limbs b, Limbs c, Limbs d, int e) {
-  const long long P = (long long)a.h * b.h + (long long)c.h * d.h;
-  const long long T = (long long)a.h * b.l + (long long)a.l * b.h + (long long)c.h * d.l + (long long)c.l * d.h;
+  const long long P = madw(c.h, d.h, madw(a.h, b.h, 0));
+  const long long T = madw(c.l, d.h, madw(c.h, d.l, madw(a.l, b.h, madw(a.h, b.l, 0))));
   if (e <= 2) return (long long)((unsigned long long)P << (2 - e)) + ((T + (1ll << (29 + e))) >> (30 + e));
   return (P + ((T + (1ll << (29 + e))) >> 32)) >> (e - 2);
+}
+
+// Exact 128-bit products from four 32 x 32-bit limb products each (fused multiply-add-wide
+// on the device).  Operands |.| < 2^61: the high limbs are below 2^29 in magnitude, so the
+// middle sums stay inside int64; the low-limb difference (two products of magnitude <= 2^62)
+// does too.
+// a b - c d
+QAOA_HD i128 dot2_exact(long long a, long long b, long long c, long long d) {
+  const Limbs A = split(a), B = split(b), C = split(c), D = split(d);
+  const long long P = madw(-C.h, D.h, madw(A.h, B.h, 0));
+  const long long M = madw(A.h, B.l, madw(A.l, B.h, 0)) - madw(C.h, D.l, madw(C.l, D.h, 0));
+  const long long L = madw(A.l, B.l, 0) - madw(C.l, D.l, 0);
+  return ((i128)P << 64) + ((i128)M << 32) + (i128)L;
+}
+// a c for a 64-bit a (|a| < 2^62) and a 32-bit c
+QAOA_HD i128 mul_wide32(long long a, int c) {
+  const Limbs A = split(a);
+  return ((i128)madw(A.h, c, 0) << 32) + (i128)madw(A.l, c, 0);
 }
 
 // x * u / 2^(62 + e) for complex x (|re|, |im| < 2^61) and a Q62 unit complex u

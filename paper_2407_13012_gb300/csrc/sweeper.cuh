@@ -645,7 +645,7 @@ struct Sweeper {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int pc = __popc((idx(r) >> gl) & ((1u << t) - 1));
-        const i128 pr = (i128)w[r].x * v[r].y - (i128)w[r].y * v[r].x;  // Im(conj(lam~) psi~)
+        const i128 pr = fx::dot2_exact(w[r].x, v[r].y, w[r].y, v[r].x);  // Im(conj(lam~) psi~)
         xs += (pr >> 32) * (t - 2 * pc);
       }
       // value = 2 * xs * 2^32 * 2^-t * 2^-2S (lambda carries the scale 2^lam_shift)
@@ -675,7 +675,8 @@ struct Sweeper {
       if constexpr (FX) {
         if (!f64) {
           const long long c = cost_i(Cs, i);
-          w[r] = make_longlong2(round_shift((i128)v[r].x * c, lam_shift), round_shift((i128)v[r].y * c, lam_shift));
+          w[r] = make_longlong2(round_shift(fx::mul_wide32(v[r].x, (int)c), lam_shift),
+                                round_shift(fx::mul_wide32(v[r].y, (int)c), lam_shift));
         } else {
           const long long cq = double_to_fx(cost_f(Cs, true, i), 62 - lam_shift);
           w[r] = make_longlong2(round_shift((i128)v[r].x * cq, 62), round_shift((i128)v[r].y * cq, 62));
@@ -697,7 +698,7 @@ struct Sweeper {
       for (int r = 0; r < R; ++r) {
         const uint32_t i = idx(r);
         if (i >= evalid) continue;
-        const i128 p2 = (i128)v[r].x * v[r].x + (i128)v[r].y * v[r].y;
+        const i128 p2 = fx::dot2_exact(v[r].x, v[r].x, -v[r].y, v[r].y);  // |psi|^2, exact
         sn += p2 >> 16;
         if (!f64) sc += (p2 >> 32) * cost_i(Cs, i);
         else sf += cost_f(Cs, true, i) * i128_to_double(p2, 2 * a.fx_shift);
@@ -730,7 +731,7 @@ struct Sweeper {
       for (int r = 0; r < R; ++r) {
         const uint32_t i = idx(r);
         if (i >= evalid) continue;
-        const i128 pr = (i128)w[r].x * v[r].y - (i128)w[r].y * v[r].x;
+        const i128 pr = fx::dot2_exact(w[r].x, v[r].y, w[r].y, v[r].x);
         if (!f64) sc += (pr >> 32) * cost_i(Cs, i);
         else sf += cost_f(Cs, true, i) * i128_to_double(pr, 2 * a.fx_shift - lam_shift);
       }
@@ -1027,7 +1028,7 @@ struct Lean : Sweeper<CF, FX, TWO> {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int pc = __popc((ix<L>(r) >> gl) & ((1u << t) - 1));
-          const i128 pr = (i128)this->w[r].x * this->v[r].y - (i128)this->w[r].y * this->v[r].x;
+          const i128 pr = fx::dot2_exact(this->w[r].x, this->v[r].y, this->w[r].y, this->v[r].x);
           xs[r & 1] += (pr >> 32) * (t - 2 * pc);
         }
         this->block_add(xacc, 2.0 * i128_to_double(xs[0] + xs[1], 2 * this->a.fx_shift + t - 32 - this->lam_shift),

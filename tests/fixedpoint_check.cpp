@@ -83,6 +83,22 @@ int main() {
       }
     }
   }
+  // exact limb products against plain 128-bit arithmetic
+  for (int it = 0; it < 1000000; ++it) {
+    long long v[4];
+    for (int k = 0; k < 4; ++k) {
+      const int bits = 1 + (int)(rng() % 60);  // |v| < 2^61
+      const long long lim = (1ll << bits) - 1;
+      v[k] = (long long)(rng() % (2 * (unsigned long long)lim + 1)) - lim;
+    }
+    if (it % 101 == 0) { v[0] = (1ll << 61) - 1; v[1] = -(1ll << 61) + 1; v[2] = -(1ll << 61) + 1; v[3] = -(1ll << 61) + 1; }
+    const __int128 want = (__int128)v[0] * v[1] - (__int128)v[2] * v[3];
+    const int c = (int)(unsigned)rng();
+    const __int128 want2 = (__int128)v[0] * c;
+    if (dot2_exact(v[0], v[1], v[2], v[3]) != want || mul_wide32(v[0], c) != want2) {
+      if (fails++ < 10) printf("exact limb product mismatch\n");
+    }
+  }
   for (int it = 0; it < 1000000; ++it) {
     const long long x = (long long)(rng() >> (rng() % 63)) * ((rng() & 1) ? 1 : -1);
     const int s = (int)(rng() % 120);
