@@ -195,7 +195,7 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-SWEEP_SOURCES = ("sweep.cu", "sweeper.cuh", "fixedpoint.cuh", "internal.h", "capi.cu")
+SWEEP_SOURCES = ("sweep.cu", "sweeper.cuh", "tile_layout.cuh", "fixedpoint.cuh", "internal.h", "capi.cu")
 
 
 def sweep_source_hash() -> str:

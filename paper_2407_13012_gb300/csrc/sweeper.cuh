@@ -36,6 +36,7 @@
 #include <type_traits>
 
 #include "fixedpoint.cuh"
+#include "tile_layout.cuh"
 
 namespace qaoa {
 namespace {
@@ -54,31 +55,6 @@ inline void once_per_device(std::mutex& mu, uint64_t& done, F&& setup) {
     done |= bit;
   }
 }
-
-// ------------------------------------------------------------------ tile layouts
-
-template <int B_, int RB_, int SW_, int SWW_, int MINB_>
-struct Cfg {
-  static constexpr int MINB = MINB_;        // blocks per SM the register budget is sized for
-  static constexpr int B = B_;              // tile bits
-  static constexpr int RB = RB_;            // register bits per layout
-  static constexpr int R = 1 << RB_;        // amplitudes per thread (per buffer)
-  static constexpr int NT = 1 << (B_ - RB_);  // threads per block
-  static constexpr int NR = (B_ + RB_ - 1) / RB_;  // layouts (rounds)
-  __host__ __device__ static constexpr int lo(int k) {
-    const int v = B - RB * (k + 1);
-    return v < 0 ? 0 : v;
-  }
-  // first local bit of round k that no earlier round covers: round k processes
-  // [lo(k), newhi(k)) where newhi(0) = B and newhi(k) = lo(k - 1)
-  __host__ __device__ static constexpr int newhi(int k) { return k == 0 ? B : lo(k - 1); }
-  __host__ __device__ static constexpr uint32_t idx(int k, uint32_t tid, int r) {
-    const int l = lo(k);
-    return (tid & ((1u << l) - 1)) | ((uint32_t)r << l) | ((tid >> l) << (l + RB));
-  }
-  // shared-memory slot of local index i: XOR-fold higher bits into the bank bits
-  __host__ __device__ static constexpr uint32_t phys(uint32_t i) { return i ^ ((i >> SW_) & ((1u << SWW_) - 1)); }
-};
 
 // complex64 single buffer: 8192-amplitude tiles, 32 per thread, 256 threads
 using CfgF1 = Cfg<13, 5, 5, 4, 2>;
@@ -218,6 +194,23 @@ struct Sweeper {
 
   __device__ __forceinline__ uint32_t idx(int r) const { return CF::idx(cur, tid, r); }
 
+  // barrier over the exchange group of a move between layouts F and T (Cfg: exchange groups).
+  // Only exchanges use the exchange area, every tile starts and ends in layout 0, and each
+  // move starts in the layout the previous one ended in: the slots a thread writes are the
+  // slots of its own local indices, which it alone read in the previous move.  So a move
+  // needs one barrier, between its writes and its reads, over its exchange group.
+  template <int F, int T>
+  __device__ __forceinline__ void xsync() const {
+    constexpr int kind = CF::move_sync(F, T);
+    if constexpr (kind == 0) {
+      __syncwarp();
+    } else if constexpr (kind == 1) {
+      __syncthreads();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(CF::bar_id(F, T, tid >> 5)), "r"(CF::bar_count(F, T)) : "memory");
+    }
+  }
+
   // move u from layout F to layout T through the shared exchange buffer; layouts known at
   // compile time so each slot address is one base plus an immediate
   // The swizzle is linear over GF(2) and idx(k, tid, r) = idx(k, tid, 0) | (r << lo(k)) with
@@ -225,10 +218,9 @@ struct Sweeper {
   template <int F, int T>
   __device__ __forceinline__ void ex(V (&u)[R]) {
     const uint32_t pf = CF::phys(CF::idx(F, tid, 0)), pt = CF::phys(CF::idx(T, tid, 0));
-    __syncthreads();
 #pragma unroll
     for (int r = 0; r < R; ++r) X[pf ^ CF::phys((uint32_t)r << CF::lo(F))] = u[r];
-    __syncthreads();
+    xsync<F, T>();
 #pragma unroll
     for (int r = 0; r < R; ++r) u[r] = X[pt ^ CF::phys((uint32_t)r << CF::lo(T))];
   }
@@ -249,19 +241,17 @@ struct Sweeper {
       default: if constexpr (CF::NR > 3) ex_from<(CF::NR > 3 ? 3 : 0)>(u, to); break;
     }
   }
-  // both buffers always share one layout
   // both buffers at once: psi through X, lambda through the second half X + 2^B, so one
-  // pair of barriers serves the two
+  // barrier serves the two
   template <int F, int T>
   __device__ __forceinline__ void ex2() {
     const uint32_t pf = CF::phys(CF::idx(F, tid, 0)), pt = CF::phys(CF::idx(T, tid, 0));
     V* X2 = X + (1u << CF::B);
-    __syncthreads();
 #pragma unroll
     for (int r = 0; r < R; ++r) X[pf ^ CF::phys((uint32_t)r << CF::lo(F))] = v[r];
 #pragma unroll
     for (int r = 0; r < R; ++r) X2[pf ^ CF::phys((uint32_t)r << CF::lo(F))] = w[r];
-    __syncthreads();
+    xsync<F, T>();
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = X[pt ^ CF::phys((uint32_t)r << CF::lo(T))];
 #pragma unroll
