@@ -161,6 +161,10 @@ static int lean_kind(const Sweep& s, const Group& g, int tile_bits, int dtype, b
   const int rb = fx ? (s.two ? 3 : 4) : 5;
   if (g.t + g.c != tile_bits || g.c > tile_bits - rb || g.t < 3) return SWEEP_GENERIC;
   if (fx && s.load_user) return SWEEP_GENERIC;
+  if ((int)s.red_slot.size() > kLeanAcc) return SWEEP_GENERIC;
+  int mixers = 0;
+  for (uint32_t op : s.ops) mixers += (op & 0xff) == OP_MIX;
+  if (mixers > kLeanMix) return SWEEP_GENERIC;
   const uint32_t want_mix = s.two ? (F_PSI | F_LAM | F_XTERM) : F_PSI;
   const std::vector<uint32_t>& o = s.ops;
   const bool plain_formats = !s.init && !s.load_user && !s.store_user && s.store_psi &&

@@ -36,6 +36,8 @@ inline uint32_t make_op(uint32_t kind, uint32_t flags, uint32_t layer, uint32_t 
 constexpr int kMaxOps = 200;
 constexpr int kMaxAcc = 2 * QAOA_MAX_P + 2;  // reduction accumulators per sweep (double each)
 constexpr int kMaxContrib = 8;               // partial slots per output
+constexpr int kLeanAcc = 8;   // reduction accumulators of a lean sweep (per-warp slots)
+constexpr int kLeanMix = 4;   // mixers of a lean sweep (diagonals staged once per launch)
 constexpr int kGridCap = 2048;               // most blocks a reduction writes partials for
 // qaoa_expectation's workspace: partials of its 2 outputs (kMaxContrib slots x kGridCap
 // blocks each); the size qaoa_workspace_size reports adds kHostResultBytes, the slot where

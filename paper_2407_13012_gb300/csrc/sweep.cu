@@ -39,12 +39,26 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
   void* Cs = smem_raw + ((sizeof(V) << CF::B) << (TWO ? 1 : 0));
   const bool cost = OPS && a.needs_cost;
   V* Tsm = (V*)((unsigned char*)Cs + (cost ? ((a.cost_dtype == QAOA_COST_F64 ? 8 : 4) << CF::B) : 0));
-  __shared__ double blk[kMaxAcc];
-  __shared__ double red[2 * (CF::NT / 32)];
-  __shared__ fx::Factor dsm[16];
-  for (int r = threadIdx.x; r < kMaxAcc; r += CF::NT) blk[r] = 0.0;
-  S s(a, X, Cs, blk, red);
-  s.Ds = dsm;
+  constexpr int NW = CF::NT / 32;
+  __shared__ double wacc[kLeanAcc * NW];
+  __shared__ fx::Factor dpre[FX ? kLeanMix * 16 : 1];
+  for (int r = threadIdx.x; r < kLeanAcc * NW; r += CF::NT) wacc[r] = 0.0;
+  S s(a, X, Cs, nullptr, nullptr);
+  s.wacc = wacc;
+  if constexpr (FX) {  // every mixer's diagonal exp(-i beta (t - 2k)), k = 0..t, as prepared factors
+    const int t = a.g.t;
+    int m = 0;
+    for (int k = 0; k < (OPS ? a.nops : 1) && m < kLeanMix; ++k) {
+      const uint32_t op = a.ops[k];
+      if ((op & 0xff) != OP_MIX) continue;
+      if (threadIdx.x <= (uint32_t)t) {
+        const longlong2 e = __ldg((const longlong2*)a.d_table + ((long long)((op >> 16) & 0xff) * 14 + t) * 14 + threadIdx.x);
+        dpre[16 * m + threadIdx.x] = fx::factor(e.x, (op & F_SIGN) ? -e.y : e.y);
+      }
+      ++m;
+    }
+    s.dpre = dpre;
+  }
   if (OPS && a.smem_table_layer >= 0) {
     stage_table<FX>(s, a, Tsm, CF::NT);
   }
@@ -61,8 +75,11 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
   for (int64_t tile = blockIdx.x; tile < a.g.tiles; tile += gridDim.x)
     lean_tile<CF, FX, TWO, OPS, LAST, false>(s, a, tile, Cs);
   __syncthreads();
-  for (int r = threadIdx.x; r < a.nred; r += CF::NT)
-    a.partials[(int64_t)a.red_slot[r] * a.grid + blockIdx.x] = blk[r];
+  for (int r = threadIdx.x; r < a.nred; r += CF::NT) {
+    double v = 0.0;
+    for (int w = 0; w < NW; ++w) v += wacc[r * NW + w];
+    a.partials[(int64_t)a.red_slot[r] * a.grid + blockIdx.x] = v;
+  }
 }
 
 template <class CF, bool FX, bool TWO>

@@ -179,6 +179,7 @@ struct Sweeper {
   fx::Factor* Ds;  // shared-memory mixer diagonal of the current fixed-point mixer (<= 14 entries)
   int ts_layer;  // layer whose table Ts holds (-1: none)
   double* blk;   // block accumulators
+  double* wacc = nullptr;  // per-warp accumulators [kLeanAcc][NT / 32], if set (lean sweeps)
   double* red;   // reduction scratch [2][NT/32]
   int cur;       // current layout
   int lam_shift;  // lambda scale exponent (fixed point)
@@ -284,12 +285,21 @@ struct Sweeper {
   }
 
   // block-reduce and add to blk[r] (and blk[r + 1])
+  // (with per-warp accumulators: lane 0 adds the warp's sum to the warp's own slot, no
+  // barrier; the slots are summed in warp order once, at the end of the launch)
   __device__ __forceinline__ void block_add(int r, double v0, double v1, bool pair) {
     const int warp = tid >> 5, lane = tid & 31;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       v0 += __shfl_down_sync(0xffffffffu, v0, o);
       v1 += __shfl_down_sync(0xffffffffu, v1, o);
+    }
+    if (wacc != nullptr) {
+      if (lane == 0) {
+        wacc[r * (CF::NT / 32) + warp] += v0;
+        if (pair) wacc[(r + 1) * (CF::NT / 32) + warp] += v1;
+      }
+      return;
     }
     __syncthreads();
     if (lane == 0) {
@@ -914,6 +924,9 @@ struct Lean : Sweeper<CF, FX, TWO> {
   using V = typename B::V;
   static constexpr int R = CF::R, NR = CF::NR;
   using B::B;
+  // mixer diagonals of the launch's mixers, staged once in shared memory ([kLeanMix][16]),
+  // or nullptr: each mixer then stages its own between block barriers
+  const fx::Factor* dpre = nullptr;
 
   // group-qubit register bits of round K (relative to lo(K)), uniform
   template <int K>
@@ -996,22 +1009,25 @@ struct Lean : Sweeper<CF, FX, TWO> {
     }
   }
   template <int L, bool BIG>
-  __device__ __forceinline__ void dmul_l(V (&u)[R], int gl, int t) {
+  __device__ __forceinline__ void dmul_l(V (&u)[R], const fx::Factor* Ds, int gl, int t) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const fx::Factor& f = this->Ds[__popc((ix<L>(r) >> gl) & ((1u << t) - 1))];
+      const fx::Factor& f = Ds[__popc((ix<L>(r) >> gl) & ((1u << t) - 1))];
       const fx::C64 o = fx::cmul_factor<!BIG, false>(u[r].x, u[r].y, f, t);
       u[r] = make_longlong2(o.x, o.y);
     }
   }
   // W D W from layout 0 back to layout 0; D at layout L (the last round with group qubits)
   template <int L>
-  __device__ __forceinline__ void fx_mixer(int layer, bool inverse, bool lam, int xacc) {
+  __device__ __forceinline__ void fx_mixer(int layer, bool inverse, bool lam, int xacc, int mix) {
     const int gl = this->a.g.c, t = this->a.g.t;
-    __syncthreads();
-    this->load_diagonal(layer, inverse, t);
+    const fx::Factor* Ds = dpre != nullptr ? dpre + 16 * mix : this->Ds;
+    if (dpre == nullptr) {
+      __syncthreads();
+      this->load_diagonal(layer, inverse, t);
+    }
     fx_fwd<0, L>(lam);
-    __syncthreads();
+    if (dpre == nullptr) __syncthreads();
     if constexpr (TWO) {
       if (xacc >= 0) {
         i128 xs[2] = {0, 0};  // two independent exact sums (shorter carry chains)
@@ -1029,14 +1045,14 @@ struct Lean : Sweeper<CF, FX, TWO> {
     // applies; the two-buffer kernels keep the branch (it schedules better there)
     if constexpr (TWO) {
       if (t >= 3) {
-        dmul_l<L, true>(this->v, gl, t);
-        if (lam) dmul_l<L, true>(this->w, gl, t);
+        dmul_l<L, true>(this->v, Ds, gl, t);
+        if (lam) dmul_l<L, true>(this->w, Ds, gl, t);
       } else {
-        dmul_l<L, false>(this->v, gl, t);
-        if (lam) dmul_l<L, false>(this->w, gl, t);
+        dmul_l<L, false>(this->v, Ds, gl, t);
+        if (lam) dmul_l<L, false>(this->w, Ds, gl, t);
       }
     } else {
-      dmul_l<L, true>(this->v, gl, t);
+      dmul_l<L, true>(this->v, Ds, gl, t);
     }
     fx_back<L>(lam);
   }
@@ -1103,8 +1119,8 @@ struct Lean : Sweeper<CF, FX, TWO> {
     }
   }
   template <int L>
-  __device__ __forceinline__ void mixer(int layer, bool inverse, int xacc) {
-    if constexpr (FX) fx_mixer<L>(layer, inverse, TWO, xacc);
+  __device__ __forceinline__ void mixer(int layer, bool inverse, int xacc, int mix) {
+    if constexpr (FX) fx_mixer<L>(layer, inverse, TWO, xacc, mix);
     else f32_mixer<L>(layer, inverse, xacc);
   }
 
@@ -1116,11 +1132,12 @@ struct Lean : Sweeper<CF, FX, TWO> {
     const uint32_t* ops = this->a.ops;
     if constexpr (!OPS) {
       const uint32_t o = ops[0];
-      mixer<L>((o >> 16) & 0xff, o & F_SIGN, (o & F_XTERM) ? (int)((o >> 24) & 0xff) : -1);
+      mixer<L>((o >> 16) & 0xff, o & F_SIGN, (o & F_XTERM) ? (int)((o >> 24) & 0xff) : -1, 0);
     } else {
       // one copy of the mixer code for every mixer of the program keeps the kernel within
       // the instruction cache.  Two-buffer kernels apply mixers and phases to both buffers:
       // an op on psi alone only occurs while lambda is still zero (the host checks that).
+      int mix = 0;
 #pragma unroll 1
       for (int k = 0; k < this->a.nops; ++k) {
         const uint32_t op = ops[k];
@@ -1130,7 +1147,7 @@ struct Lean : Sweeper<CF, FX, TWO> {
         // every mixer returns to layout 0, where the elementwise ops run: restating cur = 0
         // before each lets the compiler fold their register-to-index maps to constants
         if (kind == OP_MIX) {
-          mixer<L>(layer, inv, (op & F_XTERM) ? acc : -1);
+          mixer<L>(layer, inv, (op & F_XTERM) ? acc : -1, mix++);
         } else if (kind == OP_PHASE) {
           this->cur = 0;
           this->op_phase(layer, inv, true, TWO);
