@@ -158,7 +158,7 @@ static int cuda_status(cudaError_t e) { return e == cudaSuccess ? QAOA_OK : QAOA
 // tile by 16-byte copies, which need whole 16-byte chunks per row).
 static int lean_kind(const Sweep& s, const Group& g, int tile_bits, int dtype, bool cost_f64) {
   const bool fx = dtype == QAOA_C128;
-  const int rb = fx ? (s.two ? 3 : 4) : 5;
+  const int rb = fx ? (s.two ? 3 : 4) : (s.two ? 4 : 5);
   if (g.t + g.c != tile_bits || g.c > tile_bits - rb || g.t < 3) return SWEEP_GENERIC;
   if (fx && s.load_user) return SWEEP_GENERIC;
   if ((int)s.red_slot.size() > kLeanAcc) return SWEEP_GENERIC;

@@ -58,9 +58,10 @@ inline void once_per_device(std::mutex& mu, uint64_t& done, F&& setup) {
 
 // complex64 single buffer: 8192-amplitude tiles, 32 per thread, 256 threads
 using CfgF1 = Cfg<13, 5, 5, 4, 2>;
-// complex64 two buffers (gradient) with 8192-amplitude tiles: 32 amplitudes per thread per
-// buffer, one block per SM; at n = 32 this keeps >= 3 carried low bits (64-byte rows)
-using CfgF3 = Cfg<13, 5, 5, 4, 1>;
+// complex64 two buffers (gradient) with 8192-amplitude tiles: 16 amplitudes per thread per
+// buffer, 512 threads, one block per SM; at n = 32 this keeps >= 3 carried low bits (64-byte
+// rows)
+using CfgF3 = Cfg<13, 4, 4, 4, 1>;
 // complex128 fixed point single buffer: 4096-amplitude tiles, 16 per thread
 using CfgX1 = Cfg<12, 4, 4, 3, 2>;
 // complex128 fixed point two buffers: 4096-amplitude tiles, 8 per thread per buffer, 512 threads

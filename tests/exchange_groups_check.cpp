@@ -79,7 +79,8 @@ static void check(const char* name) {
 
 int main() {
   check<Cfg<13, 5, 5, 4, 2>>("complex64 single buffer");
-  check<Cfg<13, 5, 5, 4, 1>>("complex64 two buffers");
+  check<Cfg<13, 4, 4, 4, 1>>("complex64 two buffers");
+  check<Cfg<13, 5, 5, 4, 1>>("8192-amplitude tiles, 5 register bits, one block");
   check<Cfg<12, 4, 4, 3, 2>>("complex128 single buffer");
   check<Cfg<12, 3, 3, 3, 1>>("complex128 two buffers");
   check<Cfg<10, 3, 3, 3, 2>>("batched complex128, 2^10 tiles");
