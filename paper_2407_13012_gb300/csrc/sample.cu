@@ -37,17 +37,75 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// (1) one warp per leaf; a.len entries (the last leaf may be partly past the end)
+// Double-float accumulation in float32 (the float64 pipe retires ~1.75 FMA per SM clock, so
+// a float64 product per amplitude would bound the complex64 leaf sums): x^2 = p + e exactly
+// (one FMA gives e), and (s, c) absorbs p by Knuth's two-sum, so s + c carries the exact
+// sum to ~2^-44 relative.
+struct F2Sum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add_sq(float x) {
+    const float p = x * x;
+    const float e = fmaf(x, x, -p);
+    const float t = s + p;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (p - bp);
+    s = t;
+    c += err + e;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// (1) one warp per leaf; a.len entries (the last leaf may be partly past the end).  Full
+// leaves of an aligned vector take 16-byte loads, all issued before the sums (complex128:
+// one amplitude per load, two independent float64 FMA chains; complex64: two amplitudes
+// per load, double-float sums in float32); other leaves go amplitude by amplitude.
 __global__ void leaf_sum_kernel(const __grid_constant__ SampleArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const uint32_t L = 1u << a.leaf_bits;
   const int64_t nleaf = (int64_t)((a.len + L - 1) >> a.leaf_bits);
+  const bool vec = a.leaf_bits == 10 && ((uintptr_t)a.psi & 15) == 0;
   for (int64_t li = warp; li < nleaf; li += nwarps) {
     const uint64_t base = (uint64_t)li << a.leaf_bits;
     double s = 0.0;
-    for (uint32_t k = lane; k < L && base + k < a.len; k += 32) s += prob_at(a.psi, a.dtype, base + k);
+    if (vec && base + L <= a.len) {
+      if (a.dtype == QAOA_C128) {
+        const double2* q = (const double2*)a.psi + base + lane;
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int m0 = 0; m0 < 32; m0 += 8) {
+          double2 v[8];
+#pragma unroll
+          for (int m = 0; m < 8; ++m) v[m] = __ldg(q + 32 * (m0 + m));
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            s0 = fma(v[m].x, v[m].x, s0);
+            s1 = fma(v[m].y, v[m].y, s1);
+          }
+        }
+        s = s0 + s1;
+      } else {
+        const float4* q = (const float4*)a.psi + (base >> 1) + lane;
+        F2Sum f0, f1;
+#pragma unroll
+        for (int m0 = 0; m0 < 16; m0 += 8) {
+          float4 v[8];
+#pragma unroll
+          for (int m = 0; m < 8; ++m) v[m] = __ldg(q + 32 * (m0 + m));
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            f0.add_sq(v[m].x);
+            f1.add_sq(v[m].y);
+            f0.add_sq(v[m].z);
+            f1.add_sq(v[m].w);
+          }
+        }
+        s = f0.value() + f1.value();
+      }
+    } else {
+      for (uint32_t k = lane; k < L && base + k < a.len; k += 32) s += prob_at(a.psi, a.dtype, base + k);
+    }
     s = warp_sum(s);
     if (lane == 0) a.leaf[li] = s;
   }
