@@ -69,6 +69,7 @@ struct SweepArgs {
   // store 0 = internal, 1 = user, -1 = none.  complex64 internal == user.
   int load_fmt, store_fmt;
   int load_lam, store_lam;
+  int stage;          // lean two-buffer sweeps: psi of the block's next tile staged in shared memory
   long long init_fx;  // |+> amplitude in fixed point
   float init_f32;     // |+> amplitude in float32
   int fx_shift;       // fixed-point scale S (value = integer * 2^-S)

@@ -62,6 +62,11 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
   if (OPS && a.smem_table_layer >= 0) {
     stage_table<FX>(s, a, Tsm, CF::NT);
   }
+  if (TWO && a.stage) {  // staging area after the phase table, 16-byte aligned
+    const size_t tb = FX ? sizeof(fx::Factor) : sizeof(V);
+    const size_t off = (size_t)((unsigned char*)Tsm - smem_raw) + (OPS && a.smem_table_layer >= 0 ? tb * a.span : 0);
+    s.Ps = (V*)(smem_raw + ((off + 15) & ~(size_t)15));
+  }
   s.evalid = 1u << CF::B;
   if constexpr (FX && TWO) {
     if (a.cmax_dev != nullptr) {
@@ -72,8 +77,12 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
     }
   }
   __syncthreads();
-  for (int64_t tile = blockIdx.x; tile < a.g.tiles; tile += gridDim.x)
-    lean_tile<CF, FX, TWO, OPS, LAST, false>(s, a, tile, Cs);
+  bool have = false;  // this tile's psi is in the staging area
+  for (int64_t tile = blockIdx.x; tile < a.g.tiles; tile += gridDim.x) {
+    const int64_t next = tile + gridDim.x < a.g.tiles ? tile + gridDim.x : -1;
+    lean_tile<CF, FX, TWO, OPS, LAST, false>(s, a, tile, Cs, next, have);
+    have = s.Ps != nullptr && next >= 0;
+  }
   __syncthreads();
   for (int r = threadIdx.x; r < a.nred; r += CF::NT) {
     double v = 0.0;
@@ -286,13 +295,38 @@ int blocks_per_sm(int cost_bytes) {
   return cached[slot];
 }
 
+// dynamic shared memory a lean kernel may take on this device: the opt-in limit less its
+// static shared memory (two-buffer kernels, which may add the psi staging area), else the
+// largest exchange + cost + table layout
+template <class CF, bool FX, bool TWO>
+size_t lean_smem_cap() {
+  static size_t cached[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& c = cached[dev & 63];
+  if (c == 0) {
+    c = smem_bytes<CF, FX, TWO>(8, kSmemTable);
+    if (TWO) {
+      int optin = 0;
+      cudaFuncAttributes fa;
+      if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+          cudaFuncGetAttributes(&fa, lean_kernel<CF, FX, TWO, true, 0>) == cudaSuccess &&
+          (size_t)optin > fa.sharedSizeBytes + 1024)
+        c = std::max(c, (size_t)optin - fa.sharedSizeBytes - 1024);
+    }
+  }
+  return c;
+}
+
 template <class CF, bool FX, bool TWO, bool OPS, int LAST>
 void lean_launch_l(const SweepArgs& a, size_t sm, cudaStream_t s) {
   static std::mutex mu;
   static uint64_t done = 0;
   once_per_device(mu, done, [] {
     cudaFuncSetAttribute(lean_kernel<CF, FX, TWO, OPS, LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_bytes<CF, FX, TWO>(8, kSmemTable));
+                         (int)lean_smem_cap<CF, FX, TWO>());
   });
   lean_kernel<CF, FX, TWO, OPS, LAST><<<a.grid, CF::NT, sm, s>>>(a);
 }
@@ -319,8 +353,21 @@ void launch_t(const SweepArgs& a, cudaStream_t s) {
       const int lo = std::max(0, CF::B - CF::RB * (k + 1)), hi = k == 0 ? CF::B : std::max(0, CF::B - CF::RB * k);
       if (hi > a.g.c && lo < a.g.c + a.g.t) last = k;
     }
-    if (a.kind == SWEEP_LEAN_OPS) lean_launch<CF, FX, TWO, true>(a, last, sm, s);
-    else lean_launch<CF, FX, TWO, false>(a, last, sm, s);
+    // complex128 two-buffer sweeps that load psi stage the next tile's psi when shared
+    // memory allows (complex64: measured no gain)
+    SweepArgs b = a;
+    b.stage = 0;
+    if (TWO && FX && !(a.kind == SWEEP_LEAN_OPS && a.load_fmt == 2)) {
+      const size_t st = ((sm + 15) & ~(size_t)15) + ((FX ? sizeof(longlong2) : sizeof(float2)) << CF::B);
+      if (st <= lean_smem_cap<CF, FX, TWO>()) {
+        b.stage = 1;
+        if (a.kind == SWEEP_LEAN_OPS) lean_launch<CF, FX, TWO, true>(b, last, st, s);
+        else lean_launch<CF, FX, TWO, false>(b, last, st, s);
+        return;
+      }
+    }
+    if (a.kind == SWEEP_LEAN_OPS) lean_launch<CF, FX, TWO, true>(b, last, sm, s);
+    else lean_launch<CF, FX, TWO, false>(b, last, sm, s);
     return;
   }
   sweep_kernel<CF, FX, TWO><<<a.grid, CF::NT, sm, s>>>(a);

@@ -80,6 +80,16 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// all but the newest N committed groups of this thread are complete
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 __device__ __forceinline__ uint64_t tile_base(const SweepGeom& g, int64_t tile) {
   const int lowrest_bits = g.j0 - g.c;
@@ -174,6 +184,7 @@ struct Sweeper {
   V v[R];        // register tile of psi (layout cur)
   V w[R];        // register tile of lambda (two-buffer sweeps)
   V* X;          // exchange buffer, 2^B slots (2 x 2^B for two-buffer sweeps: psi, then lambda)
+  V* Ps = nullptr;  // lean two-buffer sweeps: psi of the next tile, 2^B slots (or nullptr)
   void* Cs;      // cost tile, 2^B slots
   const V* Ts;   // shared-memory copy of one layer's phase table (or nullptr); float32 states
   const fx::Factor* Tf;  // the same for fixed-point states, as prepared factors
@@ -1169,9 +1180,15 @@ struct Lean : Sweeper<CF, FX, TWO> {
 
 // One tile of a lean sweep: stage the cost tile (op programs), load or create the state in
 // layout 0, run the mixer or the op program, store.  COHERENT loads read state written
-// earlier in the same launch.
+// earlier in the same launch.  With a staging area (two-buffer sweeps, s.Ps), psi of the
+// block's next tile `next` travels into it by asynchronous copies while this tile computes;
+// `have` says that this tile's psi is there.  Each thread copies and reads back only its own
+// layout-0 slots, so the staging needs no barrier, only waits for the thread's own copy
+// groups; the cost tile's group is committed after the prefetch of this tile's psi and before
+// the prefetch of the next one.
 template <class CF, bool FX, bool TWO, bool OPS, int LAST, bool COHERENT>
-__device__ __forceinline__ void lean_tile(Lean<CF, FX, TWO>& s, const SweepArgs& a, int64_t tile, void* Cs) {
+__device__ __forceinline__ void lean_tile(Lean<CF, FX, TWO>& s, const SweepArgs& a, int64_t tile, void* Cs,
+                                          int64_t next = -1, bool have = false) {
   using V = typename Lean<CF, FX, TWO>::V;
   constexpr int R = CF::R;
   V (&v)[R] = s.v;
@@ -1185,6 +1202,8 @@ __device__ __forceinline__ void lean_tile(Lean<CF, FX, TWO>& s, const SweepArgs&
   const bool init = OPS && a.load_fmt == 2;
   const bool ld_lam = TWO && (!OPS || a.load_lam), st_lam = TWO && (!OPS || a.store_lam);
   const int st_fmt = OPS ? a.store_fmt : 0;
+  const bool stage = TWO && s.Ps != nullptr && !init;
+  const bool staged = stage && have;
   const uint64_t base = tile_base(g, tile);
   s.base = base;
   s.cur = 0;
@@ -1197,17 +1216,39 @@ __device__ __forceinline__ void lean_tile(Lean<CF, FX, TWO>& s, const SweepArgs&
       const uint64_t z = local_to_z(g, base, i);
       cp_async16((char*)Cs + (size_t)phys_cost(i, cf64) * (cf64 ? 8 : 4), (const char*)a.C + z * (cf64 ? 8 : 4));
     }
+    if (stage) cp_async_commit();
+  }
+  if (staged) {  // this tile's psi (the group before the cost tile's) is in
+    if (cost) cp_async_wait<1>();
+    else cp_async_wait<0>();
   }
   const uint64_t z0 = local_to_z(g, base, tb0);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const uint64_t z = z0 + (uint64_t)r * zs;
-    if constexpr (FX) v[r] = init ? make_longlong2(a.init_fx, 0) : ld_state<COHERENT>((const V*)a.psi + z);
-    else v[r] = init ? make_float2(a.init_f32, 0.f) : ld_state<COHERENT>((const V*)a.psi + z);
+    const uint32_t ps = tb0 + ((uint32_t)r << CF::lo(0));
+    if constexpr (FX) v[r] = init ? make_longlong2(a.init_fx, 0) : staged ? s.Ps[ps] : ld_state<COHERENT>((const V*)a.psi + z);
+    else v[r] = init ? make_float2(a.init_f32, 0.f) : staged ? s.Ps[ps] : ld_state<COHERENT>((const V*)a.psi + z);
     if constexpr (TWO) w[r] = ld_lam ? ld_state<COHERENT>((const V*)a.lam + z) : V{};
   }
+  if (stage && next >= 0) {
+    const uint64_t zn = local_to_z(g, tile_base(g, next), tb0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      V* dst = s.Ps + tb0 + ((uint32_t)r << CF::lo(0));
+      const V* src = (const V*)a.psi + zn + (uint64_t)r * zs;
+      if constexpr (sizeof(V) == 16) cp_async16(dst, src);
+      else cp_async8(dst, src);
+    }
+    cp_async_commit();
+  }
   if (cost) {
-    cp_async_wait_all();
+    if (stage) {  // all but the newest group (the prefetch, if any): the cost tile is in
+      if (next >= 0) cp_async_wait<1>();
+      else cp_async_wait<0>();
+    } else {
+      cp_async_wait_all();
+    }
     __syncthreads();
   }
   s.template run<LAST, OPS>();
