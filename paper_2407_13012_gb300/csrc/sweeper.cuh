@@ -1042,15 +1042,30 @@ struct Lean : Sweeper<CF, FX, TWO> {
     if (dpre == nullptr) __syncthreads();
     if constexpr (TWO) {
       if (xacc >= 0) {
-        i128 xs[2] = {0, 0};  // two independent exact sums (shorter carry chains)
+        // sum_r pr_r (t - 2 popcount(group bits of index r)); the index is the thread's
+        // bits OR r << lo(L), so the popcount is the thread's part pt plus popcount(r & gm),
+        // gm = the register bits that are group bits, and the sum is
+        // (t - 2 pt) S - 2 sum_{b in gm} U_b with S = sum_r pr_r, U_b = sum_{r: bit b} pr_r
+        // (exact int128 sums of products below 2^123, shifted once before the weighting)
+        const uint32_t gmask = (1u << t) - 1;
+        const int pt = __popc((ix<L>(0) >> gl) & gmask);
+        const uint32_t gm = (((uint32_t)gmask << gl) >> CF::lo(L)) & (uint32_t)(R - 1);
+        i128 S = 0, U[CF::RB];
+#pragma unroll
+        for (int b = 0; b < CF::RB; ++b) U[b] = 0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          const int pc = __popc((ix<L>(r) >> gl) & ((1u << t) - 1));
           const i128 pr = fx::dot2_exact(this->w[r].x, this->v[r].y, this->w[r].y, this->v[r].x);
-          xs[r & 1] += (pr >> 32) * (t - 2 * pc);
+          S += pr;
+#pragma unroll
+          for (int b = 0; b < CF::RB; ++b)
+            if (r & (1 << b)) U[b] += pr;
         }
-        this->block_add(xacc, 2.0 * i128_to_double(xs[0] + xs[1], 2 * this->a.fx_shift + t - 32 - this->lam_shift),
-                        0.0, false);
+        i128 xs = (S >> 32) * (t - 2 * pt);
+#pragma unroll
+        for (int b = 0; b < CF::RB; ++b)
+          if (gm & (1u << b)) xs -= (U[b] >> 32) * 2;
+        this->block_add(xacc, 2.0 * i128_to_double(xs, 2 * this->a.fx_shift + t - 32 - this->lam_shift), 0.0, false);
       }
     }
     // lean sweeps run only on groups of >= 3 qubits, so the shift form of the multiply
