@@ -51,6 +51,11 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) batch_kernel(const __grid_co
   __shared__ double red[2 * (CF::NT / 32)];
   __shared__ fx::Factor dsm[16];
   __shared__ int cur;
+  // lean sweeps: per-warp accumulators (summed with blk at the end of the graph) and every
+  // mixer diagonal of the sweep staged once
+  constexpr int NW = CF::NT / 32;
+  __shared__ double wacc[LEAN ? kMaxAcc * NW : 1];
+  __shared__ fx::Factor dpre[LEAN && FX ? kLeanMix * 16 : 1];
   const int tid = threadIdx.x;
   const int p = b.p;
   const int nout = 2 * p + 2;
@@ -58,6 +63,8 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) batch_kernel(const __grid_co
     __syncthreads();  // the previous graph is finished with cur, blk and sa
     if (tid == 0) cur = atomicAdd(queue, 1);
     for (int r = tid; r < nout; r += CF::NT) blk[r] = 0.0;
+    if constexpr (LEAN)
+      for (int r = tid; r < nout * NW; r += CF::NT) wacc[r] = 0.0;
     __syncthreads();
     const int gi = cur;
     if (gi >= count) break;
@@ -101,22 +108,58 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) batch_kernel(const __grid_co
       }
       for (int k = tid; k < bs.nops; k += CF::NT) sa.ops[k] = bs.ops[k];
       __syncthreads();
-      if (LEAN && bs.lean_last >= 0 && !bs.two) {  // forward sweep: psi alone
+      const bool lean = LEAN && bs.lean_last >= 0;
+      bool staged = false;
+      if constexpr (LEAN && FX) {
+        if (lean) {  // exp(-i beta (t - 2k)), k = 0..t, of each mixer, as prepared factors
+          const int t = bs.g.t;
+          int m = 0;
+          for (int k = 0; k < bs.nops; ++k) m += (bs.ops[k] & 0xff) == OP_MIX;
+          if (m <= kLeanMix) {
+            m = 0;
+            for (int k = 0; k < bs.nops; ++k) {
+              const uint32_t op = bs.ops[k];
+              if ((op & 0xff) != OP_MIX) continue;
+              if (tid <= t) {
+                const longlong2 e =
+                    __ldg((const longlong2*)sa.d_table + ((long long)((op >> 16) & 0xff) * 14 + t) * 14 + tid);
+                dpre[16 * m + tid] = fx::factor(e.x, (op & F_SIGN) ? -e.y : e.y);
+              }
+              ++m;
+            }
+            staged = true;
+            __syncthreads();
+          }
+        }
+      }
+      if (lean && !bs.two) {  // forward sweep: psi alone
         Lean<CF, FX, false> s1(sa, X, Cs, blk, red);
         s1.Ds = dsm;
         s1.evalid = 1u << CF::B;
+        s1.wacc = wacc;
+        if (staged) s1.dpre = dpre;
         lean_tiles<CF, FX, false>(s1, sa, bs.lean_last, Cs);
       } else {
         S s(sa, X, Cs, blk, red);
         s.Ds = dsm;
         s.evalid = 1u << (bs.g.t + bs.g.c);
         if constexpr (FX) s.lam_shift = G.lam_shift;
-        if (LEAN && bs.lean_last >= 0) lean_tiles<CF, FX, true>(s, sa, bs.lean_last, Cs);
-        else for (int64_t tile = 0; tile < bs.g.tiles; ++tile) sweep_tile<CF, FX, true, true>(s, sa, tile, Cs);
+        if (lean) {
+          s.wacc = wacc;
+          if (staged) s.dpre = dpre;
+          lean_tiles<CF, FX, true>(s, sa, bs.lean_last, Cs);
+        } else {
+          for (int64_t tile = 0; tile < bs.g.tiles; ++tile) sweep_tile<CF, FX, true, true>(s, sa, tile, Cs);
+        }
       }
     }
-    __syncthreads();  // block_add results are in blk
-    for (int r = tid; r < nout; r += CF::NT) b.out[(int64_t)G.out * nout + r] = blk[r];
+    __syncthreads();  // block_add results are in blk and wacc
+    for (int r = tid; r < nout; r += CF::NT) {
+      double v = blk[r];
+      if constexpr (LEAN)
+        for (int w = 0; w < NW; ++w) v += wacc[r * NW + w];
+      b.out[(int64_t)G.out * nout + r] = v;
+    }
   }
 }
 
