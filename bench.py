@@ -649,6 +649,13 @@ def run_ours(a):
     traffic = None
     if tr is not None:
         traffic = tr.get("bytes_per_launch")
+    # the method's least HBM traffic for the step's 3p layers: a forward layer reads and
+    # writes psi once and reads C, (2S + c) 2^n bytes; an adjoint layer does so for psi and
+    # lambda, (4S + c) 2^n (S, c: bytes per amplitude and per cost entry)
+    S_b = 16 if a.dtype == "c128" else 8
+    c_b = 4 if integer else 8
+    min_bytes = float(2 ** a.n) * (2 * a.p * (2 * S_b + c_b) + a.p * (4 * S_b + c_b))
+    min_gbs = min_bytes / (step_ms / 1e3) / 1e9
 
     if rank == 0:
         line = {
@@ -664,7 +671,9 @@ def run_ours(a):
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "layer sweep", "launches": sweep_n,
                          "algorithmic_bytes_per_launch": sweep_bytes / max(1, sweep_n),
-                         "peak_source": f"{peak_kind} hbm_gbs"},
+                         "peak_source": f"{peak_kind} hbm_gbs",
+                         "layer_min_bytes_per_step": min_bytes, "layer_min_gbs": min_gbs,
+                         "layer_min_frac": min_gbs / peak},
             "kernels_ms": {"sweep": kms[0], "cost": kms[1], "sample": kms[2], "other": kms[3]},
             "kernels_launches": {"sweep": kla[0], "cost": kla[1], "sample": kla[2], "other": kla[3]},
             "gpu_launches": launches,

@@ -78,6 +78,10 @@ static void check(const char* name) {
 }
 
 int main() {
+  // the kernels' configurations, as the test harness reads them from the sources
+#if __has_include("exchange_cfgs.inc")
+#include "exchange_cfgs.inc"
+#endif
   check<Cfg<13, 5, 5, 4, 2>>("complex64 single buffer");
   check<Cfg<13, 4, 4, 4, 1>>("complex64 two buffers");
   check<Cfg<13, 5, 5, 4, 1>>("8192-amplitude tiles, 5 register bits, one block");
