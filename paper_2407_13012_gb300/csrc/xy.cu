@@ -24,12 +24,14 @@
 //   rank(z') - rank(z) = binom(a + 1, j + 1) - binom(a, j + 1) = binom(a, j);
 // the closing pair (0, n-1) ranks z' directly.
 #include "internal.h"
+#include "xy_window.cuh"
 
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 namespace qaoa {
 namespace {
@@ -352,6 +354,150 @@ __global__ void __launch_bounds__(kXYThreads)
   if (threadIdx.x == 0) part[blockIdx.x] = 2.0 * t;
 }
 
+// ------------------------------------------------------------------ windowed mixer passes
+//
+// One launch applies every pair gate of a window [lo, lo + w) of the ring mixer (its even
+// pairs, then its odd pairs; xy_window.cuh derives the tile addressing and why the order is
+// the ring's).  A tile is up to m columns of one class: its binom(w, kw) rows x m columns of
+// amplitudes are gathered into shared memory, each gate in turn rotates its pairs of rows in
+// every column, and the tile is written back.  Backwards (TWO: psi and lambda) the gates run
+// in reverse order; before undoing a gate the owner of each pair adds
+// Im(conj(lambda_z) psi_z' + conj(lambda_z') psi_z), the gate's term at the state right after
+// it.  All gates of a window share the layer's beta, so one partial per block suffices.
+static_assert(xyw::kMaxN == QAOA_XY_MAX_N, "window tables sized for QAOA_XY_MAX_N");
+
+template <typename T>
+__device__ __forceinline__ void xy_rotate(T& x, T& y, typename Real<T>::type cb, typename Real<T>::type sb) {
+  T u, v;
+  u.x = cb * x.x + sb * y.y;  // cos(beta) x - i sin(beta) y
+  u.y = cb * x.y - sb * y.x;
+  v.x = cb * y.x + sb * x.y;  // cos(beta) y - i sin(beta) x
+  v.y = cb * y.y - sb * x.x;
+  x = u;
+  y = v;
+}
+
+template <typename T, bool TWO>
+__global__ void __launch_bounds__(kXYThreads)
+    xy_window_kernel(const __grid_constant__ xyw::Window W, T* __restrict__ psi, T* __restrict__ lam,
+                     typename Real<T>::type cb, typename Real<T>::type sb, double* __restrict__ part) {
+  __shared__ unsigned long long B[xyw::kBN][xyw::kBN];
+  __shared__ unsigned long long rowoff[xyw::kMaxRows];
+  __shared__ unsigned long long colbase[xyw::kMaxCols];
+  __shared__ unsigned short rowpat[xyw::kMaxRows];
+  __shared__ unsigned char pr0[xyw::kMaxGates][xyw::kMaxPairs], pr1[xyw::kMaxGates][xyw::kMaxPairs];
+  __shared__ int npr[xyw::kMaxGates];
+  __shared__ double red[kXYThreads / 32];
+  extern __shared__ __align__(16) unsigned char xy_win_smem[];
+  T* tp = (T*)xy_win_smem;     // psi tile
+  T* tl = tp + W.tile_elems;   // lambda tile (TWO)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int c = tid; c < xyw::kBN; c += kXYThreads) xyw::binom_row(B, c);
+  double acc = 0.0;
+  int cur = -1;  // class whose row tables are in shared memory (the same in every thread)
+  for (unsigned long long tile = blockIdx.x; tile < W.tiles; tile += gridDim.x) {
+    const int ci = xyw::find_class(W, tile);
+    const xyw::Class& C = W.cls[ci];
+    const int rows = C.rows;
+    const unsigned long long col0 = (tile - C.first_tile) * (unsigned long long)C.m;
+    const int ncol = (int)(C.ncols - col0 < (unsigned long long)C.m ? C.ncols - col0 : (unsigned long long)C.m);
+    __syncthreads();  // Pascal's triangle is ready; the previous tile is stored
+    if (ci != cur) {  // row patterns, their rank parts, and each gate's moved rows
+      for (int r = tid; r < rows; r += kXYThreads) {
+        const unsigned long long P = xyw::unrank_bits((unsigned long long)r, W.w, C.kw, B);
+        rowpat[r] = (unsigned short)P;
+        rowoff[r] = xyw::rank_part(P, W.lo, C.kL, B);
+      }
+      __syncthreads();
+      for (int g = warp; g < W.ngates; g += kXYThreads / 32) {
+        const int ga = W.ga[g];
+        int cnt = 0;
+        for (int base = 0; base < rows; base += 32) {
+          const int r = base + lane;
+          const unsigned P = r < rows ? rowpat[r] : 0u;
+          const bool mv = r < rows && ((P >> ga) & 3u) == 1u;
+          const unsigned bal = __ballot_sync(0xffffffffu, mv);
+          if (mv) {
+            const int q = cnt + __popc(bal & ((1u << lane) - 1u));
+            pr0[g][q] = (unsigned char)r;
+            pr1[g][q] = (unsigned char)xyw::partner_row(r, P, ga, B);
+          }
+          cnt += __popc(bal);
+        }
+        if (lane == 0) npr[g] = cnt;
+      }
+      cur = ci;
+    }
+    for (int c = tid; c < ncol; c += kXYThreads) colbase[c] = xyw::col_base(W, C, col0 + c, B);
+    __syncthreads();
+    // one column per run of consecutive ranks when rows of a column are adjacent (len = 1),
+    // otherwise one row segment of consecutive ranks per warp pass
+    const bool cm = C.len == 1;
+    const int ne = rows * ncol;
+    for (int e = tid; e < ne; e += kXYThreads) {
+      int r, c;
+      if (cm) {
+        c = e / rows;
+        r = e - c * rows;
+      } else {
+        r = e / ncol;
+        c = e - r * ncol;
+      }
+      const unsigned long long rk = rowoff[r] + colbase[c];
+      tp[e] = psi[rk];
+      if constexpr (TWO) tl[e] = lam[rk];
+    }
+    __syncthreads();
+    for (int gi = 0; gi < W.ngates; ++gi) {
+      const int g = TWO ? W.ngates - 1 - gi : gi;
+      const int np = npr[g];
+      const int items = np * ncol;
+      for (int it = tid; it < items; it += kXYThreads) {
+        int q, c;
+        if (cm) {
+          c = it / np;
+          q = it - c * np;
+        } else {
+          q = it / ncol;
+          c = it - q * ncol;
+        }
+        const int r0 = pr0[g][q], r1 = pr1[g][q];
+        const int s0 = cm ? c * rows + r0 : r0 * ncol + c;
+        const int s1 = cm ? c * rows + r1 : r1 * ncol + c;
+        T x = tp[s0], y = tp[s1];
+        if constexpr (TWO) {
+          T lx = tl[s0], ly = tl[s1];
+          acc += (double)lx.x * y.y - (double)lx.y * y.x + (double)ly.x * x.y - (double)ly.y * x.x;
+          xy_rotate(lx, ly, cb, sb);
+          tl[s0] = lx;
+          tl[s1] = ly;
+        }
+        xy_rotate(x, y, cb, sb);
+        tp[s0] = x;
+        tp[s1] = y;
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < ne; e += kXYThreads) {
+      int r, c;
+      if (cm) {
+        c = e / rows;
+        r = e - c * rows;
+      } else {
+        r = e / ncol;
+        c = e - r * ncol;
+      }
+      const unsigned long long rk = rowoff[r] + colbase[c];
+      psi[rk] = tp[e];
+      if constexpr (TWO) lam[rk] = tl[e];
+    }
+  }
+  if constexpr (TWO) {
+    const double t = block_sum(acc, red);
+    if (tid == 0) part[blockIdx.x] = 2.0 * t;
+  }
+}
+
 // out[o] = sum of nparts[o] consecutive partial rows (stride kXYPartStride) from row first[o]
 struct XYReducePlan {
   int nout;
@@ -552,6 +698,63 @@ int expectation_t(const XYShape& s, const T* psi, const qaoa_cost_t* cost, doubl
   return status_of(cudaGetLastError());
 }
 
+// The windows of the ring mixer for (n, k), 0 < k < n, n >= 2: tiles of 32 KB of amplitudes
+// per buffer; the closing pair (0, n - 1) (n >= 3) is a per-gate pass after the windows.
+struct XYMixPlan {
+  int nwin;
+  bool closing;
+  xyw::Window win[xyw::kMaxWindows];
+};
+
+template <typename T>
+XYMixPlan* make_mix_plan(const XYShape& s) {
+  XYMixPlan* mp = new XYMixPlan;
+  int lo[xyw::kMaxWindows + 1], w[xyw::kMaxWindows + 1];
+  mp->nwin = xyw::plan_ring_windows(s.n, lo, w);
+  for (int i = 0; i < mp->nwin; ++i)
+    xyw::plan_window(mp->win[i], s.n, s.k, lo[i], w[i], (int)(32768 / sizeof(T)), s.binom);
+  mp->closing = s.n >= 3;
+  return mp;
+}
+
+template <typename T, bool TWO>
+size_t window_smem(const xyw::Window& W) {
+  return (size_t)W.tile_elems * sizeof(T) * (TWO ? 2 : 1);
+}
+
+// one windowed pass; grid = 0 takes every SM's resident blocks (forward), the gradient passes
+// its partial-row grid
+template <typename T, bool TWO>
+cudaError_t launch_window(const xyw::Window& W, T* psi, T* lam, typename Real<T>::type cb,
+                          typename Real<T>::type sb, double* part, unsigned grid, cudaStream_t st) {
+  static std::mutex mu;
+  static unsigned long long done = 0;
+  static int per_sm = 1;
+  const size_t max_smem = (size_t)xyw::kMaxRows * (32768 / sizeof(T) / xyw::kMaxRows + 1) * sizeof(T) *
+                          (TWO ? 2 : 1);  // bound on window_smem for the 32 KB tiles
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!(done & (1ull << (dev & 63)))) {
+      cudaFuncSetAttribute(xy_window_kernel<T, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xy_window_kernel<T, TWO>, kXYThreads, max_smem);
+      if (per_sm < 1) per_sm = 1;
+      done |= 1ull << (dev & 63);
+    }
+  }
+  if (W.tiles == 0) return cudaSuccess;
+  if (grid == 0) {
+    const unsigned long long g = (unsigned long long)sm_count() * per_sm;
+    grid = (unsigned)(W.tiles < g ? W.tiles : g);
+  }
+  const double bytes = (double)W.elems * sizeof(T) * 2 * (TWO ? 2 : 1);
+  note_launch(0, st, true);
+  xy_window_kernel<T, TWO><<<grid, kXYThreads, window_smem<T, TWO>(W), st>>>(W, psi, lam, cb, sb, part);
+  note_launch(0, st, false, bytes);
+  return cudaGetLastError();
+}
+
 template <typename T>
 int layers_t(const XYShape& s, T* psi, const qaoa_cost_t* cost, const double* gamma, const double* beta, int p,
              int init, double* expect_dev, char* ws, cudaStream_t st) {
@@ -578,8 +781,8 @@ int layers_t(const XYShape& s, T* psi, const qaoa_cost_t* cost, const double* ga
     xy_tables_kernel<T><<<grid_for((unsigned long long)p * span, sms), kXYThreads, 0, st>>>(ta);
     note_launch(3, st, false);
   }
-  int pr[QAOA_XY_MAX_N][2];
-  const int np = (s.k > 0 && s.k < s.n) ? ring_pairs(s.n, pr) : 0;
+  const bool mixes = s.k > 0 && s.k < s.n && s.n >= 2;
+  XYMixPlan* mp = mixes && p > 0 ? make_mix_plan<T>(s) : nullptr;
   const unsigned long long moved = s.n >= 2 && s.k >= 1 && s.k <= s.n - 1 ? 2 * s.binom[s.n - 2][s.k - 1] : 0;
   const unsigned long long nch = (s.D + kXYChunk - 1) / kXYChunk;
   for (int l = 0; l < p; ++l) {
@@ -589,19 +792,33 @@ int layers_t(const XYShape& s, T* psi, const qaoa_cost_t* cost, const double* ga
                                                                   cost->cmin, span, gamma[l]);
     note_launch(0, st, false, (double)s.D * (2 * sb + cost_bytes(cost->dtype)));
     const R cb = (R)std::cos(beta[l]), snb = (R)std::sin(beta[l]);
-    for (int q = 0; q < np; ++q) {
-      note_launch(0, st, true);
-      xy_gate_kernel<T><<<grid_for(nch, sms), kXYThreads, 0, st>>>(s, psi, pr[q][0], pr[q][1], cb, snb);
-      note_launch(0, st, false, (double)moved * 2 * sb);
+    if (mp != nullptr) {  // the ring mixer: windowed passes, then the closing pair
+      for (int i = 0; i < mp->nwin; ++i) {
+        const cudaError_t e = launch_window<T, false>(mp->win[i], psi, nullptr, cb, snb, nullptr, 0, st);
+        if (e != cudaSuccess) {
+          delete mp;
+          return QAOA_ERR_CUDA;
+        }
+      }
+      if (mp->closing) {
+        note_launch(0, st, true);
+        xy_gate_kernel<T><<<grid_for(nch, sms), kXYThreads, 0, st>>>(s, psi, 0, s.n - 1, cb, snb);
+        note_launch(0, st, false, (double)moved * 2 * sb);
+      }
     }
     const int rc = status_of(cudaGetLastError());
-    if (rc) return rc;
+    if (rc) {
+      delete mp;
+      return rc;
+    }
   }
+  delete mp;
   if (expect_dev != nullptr) return expectation_t<T>(s, psi, cost, expect_dev, part, st);
   return status_of(cudaGetLastError());
 }
 
-// partial rows of the gradient: E, norm, dE/dgamma_l (p rows), dE/dbeta_l (p x pairs rows)
+// partial rows of the gradient: E, norm, dE/dgamma_l (p rows), dE/dbeta_l (p x pairs rows, of
+// which a layer uses one per mixer window and one for the closing pair)
 size_t xy_grad_part_bytes(int n, int k, int p) {
   int pr[QAOA_XY_MAX_N][2];
   const int np = (k > 0 && k < n) ? ring_pairs(n, pr) : 0;
@@ -629,13 +846,28 @@ int gradient_t(const XYShape& s, T* psi, T* lam, const qaoa_cost_t* cost, const 
   note_launch(0, st, true);
   xy_lambda_kernel<T><<<gr, kXYThreads, 0, st>>>(psi, lam, cost->C_dev, cost->dtype, s.D, part, part + kXYPartStride);
   note_launch(0, st, false, (double)s.D * (2 * sb + cost_bytes(cost->dtype)));
+  // beta rows of layer l: one per window and one for the closing pair (at most np of them),
+  // every row written by a launch of gg blocks
+  XYMixPlan* mp = np > 0 && p > 0 ? make_mix_plan<T>(s) : nullptr;
+  const int brows = mp != nullptr ? mp->nwin + (mp->closing ? 1 : 0) : 0;
   for (int l = p - 1; l >= 0; --l) {
     const R cb = (R)std::cos(beta[l]), snb = (R)(-std::sin(beta[l]));
-    for (int q = np - 1; q >= 0; --q) {
-      double* dst = part + (size_t)(2 + p + (size_t)l * np + q) * kXYPartStride;
-      note_launch(0, st, true);
-      xy_gate_adjoint_kernel<T><<<gg, kXYThreads, 0, st>>>(s, psi, lam, pr[q][0], pr[q][1], cb, snb, dst);
-      note_launch(0, st, false, (double)moved * 4 * sb);
+    double* rows = part + (size_t)(2 + p + (size_t)l * np) * kXYPartStride;
+    if (mp != nullptr) {
+      if (mp->closing) {  // applied last in the layer, undone first
+        note_launch(0, st, true);
+        xy_gate_adjoint_kernel<T><<<gg, kXYThreads, 0, st>>>(s, psi, lam, 0, s.n - 1, cb, snb,
+                                                              rows + (size_t)mp->nwin * kXYPartStride);
+        note_launch(0, st, false, (double)moved * 4 * sb);
+      }
+      for (int i = mp->nwin - 1; i >= 0; --i) {
+        const cudaError_t e =
+            launch_window<T, true>(mp->win[i], psi, lam, cb, snb, rows + (size_t)i * kXYPartStride, gg, st);
+        if (e != cudaSuccess) {
+          delete mp;
+          return QAOA_ERR_CUDA;
+        }
+      }
     }
     note_launch(0, st, true);
     xy_cost_adjoint_kernel<T><<<gr, kXYThreads, 0, st>>>(psi, lam, cost->C_dev, cost->dtype, s.D,
@@ -643,15 +875,19 @@ int gradient_t(const XYShape& s, T* psi, T* lam, const qaoa_cost_t* cost, const 
                                                          gamma[l], part + (size_t)(2 + l) * kXYPartStride);
     note_launch(0, st, false, (double)s.D * (4 * sb + cost_bytes(cost->dtype)));
     rc = status_of(cudaGetLastError());
-    if (rc) return rc;
+    if (rc) {
+      delete mp;
+      return rc;
+    }
   }
+  delete mp;
   XYReducePlan rp;
   std::memset(&rp, 0, sizeof(rp));
   rp.nout = 2 + 2 * p;
   for (int o = 0; o < 2; ++o) rp.first[o] = o, rp.rows[o] = 1, rp.cols[o] = (int)gr;
   for (int l = 0; l < p; ++l) {
     rp.first[2 + l] = 2 + l, rp.rows[2 + l] = 1, rp.cols[2 + l] = (int)gr;
-    rp.first[2 + p + l] = 2 + p + l * np, rp.rows[2 + p + l] = np, rp.cols[2 + p + l] = (int)gg;
+    rp.first[2 + p + l] = 2 + p + l * np, rp.rows[2 + p + l] = brows, rp.cols[2 + p + l] = (int)gg;
   }
   note_launch(3, st, true);
   xy_grad_reduce_kernel<<<rp.nout, kXYThreads, 0, st>>>(rp, part, out);

@@ -39,6 +39,8 @@ def make(n, k, prob, seed, integer=True, cost_dtype="i32"):
 
 
 CASES = [(1, 0), (1, 1), (2, 1), (3, 1), (3, 2), (6, 3), (7, 3), (9, 4), (10, 2), (12, 6), (13, 5), (14, 7)]
+# three mixer windows ([0, 8), [7, 16), [15, n)) with ragged edge classes
+WIDE = [(17, 8), (18, 5), (18, 13)]
 
 
 @pytest.mark.parametrize("n,k", CASES + [(16, 8), (12, 0), (12, 12), (15, 14)])
@@ -78,7 +80,7 @@ def test_xy_cost_vector_float_weights_any_scale(scale):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-@pytest.mark.parametrize("n,k", CASES)
+@pytest.mark.parametrize("n,k", CASES + WIDE)
 @pytest.mark.parametrize("integer", [True, False])
 def test_xy_layers_match_oracle(n, k, dtype, integer):
     q, g, cv, C, rng = make(n, k, 0.5, seed=1000 + 37 * n + k + (0 if integer else 5), integer=integer)
@@ -103,7 +105,7 @@ def test_xy_layers_match_oracle(n, k, dtype, integer):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
-@pytest.mark.parametrize("n,k", CASES)
+@pytest.mark.parametrize("n,k", CASES + WIDE)
 @pytest.mark.parametrize("integer", [True, False])
 def test_xy_gradient_matches_oracle(n, k, dtype, integer):
     """The subspace adjoint gradient against oracle/xy.py's (one 2 Im <lambda|H_g|psi_g> term
