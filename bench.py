@@ -804,14 +804,18 @@ def run_xy(a):
     line = {"metric": "xy-mixer QAOA layers per second (Hamming-weight subspace)", "value": a.p * 1e3 / ms,
             "unit": "layers/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if a.dtype == "c128" else "f32", "data": "synthetic",
+            "dtype": "int64" if a.dtype == "c128" else "f32", "data": "synthetic",
             "config": {"workload": f"balanced-cut QAOA on F_k: n={n} {'random 3-regular' if fam == 'reg3' else fam}, "
                                    f"k={k} ({D} amplitudes), p={a.p}, ring XY mixer, {a.dtype} subspace state; "
                                    f"step = Dicke start + p layers + <C>", "n": n, "k": k, "p": a.p,
+                       "arithmetic": ("float64 pairs in memory; cost unitary and window gate passes in int64 fixed "
+                                      "point with a per-tile scale (value = integer x 2^-(56 - E), components below "
+                                      "2^E); closing pair and <C> in float64") if a.dtype == "c128" else
+                                     "float32 state and rotations; <C> in float32 chunks summed in float64",
                        "state_dtype": a.dtype, "l2": "state larger than L2, no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak if achieved else None, "traffic": None,
-                         "kernel": "phase + pair-gate passes", "launches": kla[0],
+                         "kernel": "window passes (cost unitary + pair gates) + closing-pair pass", "launches": kla[0],
                          "peak_source": f"{src} hbm_gbs"},
             "gpu_launches": launches, "result": {"E": E, "norm": nrm}, "clocks": clk,
             "gradient": {"workload": f"subspace adjoint gradient, n={n}, k={k}, p={a.p}", "evals_per_s": 1e3 / grad_ms,

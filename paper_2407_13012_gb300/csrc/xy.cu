@@ -23,6 +23,7 @@
 // j + 1 among the set bits (j = set bits below a), so
 //   rank(z') - rank(z) = binom(a + 1, j + 1) - binom(a, j + 1) = binom(a, j);
 // the closing pair (0, n-1) ranks z' directly.
+#include "fixedpoint.cuh"
 #include "internal.h"
 #include "xy_window.cuh"
 
@@ -32,6 +33,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 namespace qaoa {
 namespace {
@@ -360,11 +362,17 @@ __global__ void __launch_bounds__(kXYThreads)
 // pairs, then its odd pairs; xy_window.cuh derives the tile addressing and why the order is
 // the ring's).  A tile is up to m columns of one class: its binom(w, kw) rows x m columns of
 // amplitudes are gathered into shared memory, each gate in turn rotates its pairs of rows in
-// every column, and the tile is written back.  Backwards (TWO: psi and lambda) the gates run
-// in reverse order; before undoing a gate the owner of each pair adds
-// Im(conj(lambda_z) psi_z' + conj(lambda_z') psi_z), the gate's term at the state right after
-// it.  All gates of a window share the layer's beta, so one partial per block suffices.
+// every column (the pairs of one gate are disjoint), and the tile is written back.  Backwards (TWO: psi and lambda) the gates run in reverse order; before
+// undoing a gate the owner of each pair adds Im(conj(lambda_z) psi_z' + conj(lambda_z') psi_z),
+// the gate's term at the state right after it.  All gates of a window share the layer's beta,
+// so one partial per block suffices.  Forward complex128 tiles hold the state as int64 fixed
+// point and rotate with 32-bit limb products (fixedpoint.cuh): GB300's float64 pipe would
+// otherwise bound the pass.  The scale is the tile's own: with every component below 2^E,
+// value = integer x 2^-(56 - E).  The gates keep each column's 2-norm, which is below
+// sqrt(2 rows) 2^E < 2^(E + 4) for rows <= 126, so every value stays below 2^(E + 4), i.e.
+// below 2^60 integer units, as the limb products require (any state norm is accepted).
 static_assert(xyw::kMaxN == QAOA_XY_MAX_N, "window tables sized for QAOA_XY_MAX_N");
+static_assert(xyw::kMaxRows <= 128, "tile scale headroom assumes columns of <= 128 rows");
 
 template <typename T>
 __device__ __forceinline__ void xy_rotate(T& x, T& y, typename Real<T>::type cb, typename Real<T>::type sb) {
@@ -377,10 +385,57 @@ __device__ __forceinline__ void xy_rotate(T& x, T& y, typename Real<T>::type cb,
   y = v;
 }
 
-template <typename T, bool TWO>
+// Q62 of |d| <= 1 (from a 2^-61 rounding, so that d = +-1 stays inside from_double's range)
+__device__ __forceinline__ long long xy_q62(double d) { return fx::from_double(d, 61) * 2; }
+
+// the same rotation in fixed point: cb, sb as Q62 limbs (nsb = -sb), each part rounded once
+__device__ __forceinline__ void xy_rotate_fx(longlong2& x, longlong2& y, fx::Limbs cb, fx::Limbs sb, fx::Limbs nsb) {
+  const fx::Limbs xr = fx::split(x.x), xi = fx::split(x.y), yr = fx::split(y.x), yi = fx::split(y.y);
+  x = make_longlong2(fx::dot2_q62(xr, cb, yi, sb, 0), fx::dot2_q62(xi, cb, yr, nsb, 0));
+  y = make_longlong2(fx::dot2_q62(yr, cb, xi, sb, 0), fx::dot2_q62(yi, cb, xr, nsb, 0));
+}
+
+// The layer's cost unitary fused into the first window's pass (PH): forward, each amplitude
+// is multiplied by exp(-i gamma C) as it is loaded; backward, after the window's gates are
+// undone, the owner adds c Im(conj(lambda) psi) (the gamma term at the state right after the
+// cost unitary) to `cpart` and multiplies both buffers by exp(+i gamma C) before the store.
+template <typename T>
+struct XYPhaseArgs {
+  const void* C;
+  int cost_dtype;
+  const T* tab;  // exp(-i gamma c) for c in [cmin, cmin + span), or nullptr
+  long long cmin, span;
+  double gamma;
+  double* cpart;  // backward: the block partials of the gamma term
+};
+
+template <typename T>
+__device__ __forceinline__ T xy_phase_factor(const XYPhaseArgs<T>& ph, unsigned long long r, double& c) {
+  if (ph.cost_dtype == QAOA_COST_I32) {
+    const long long ci = ((const int*)ph.C)[r];
+    const long long i = ci - ph.cmin;
+    c = (double)ci;
+    return (ph.tab != nullptr && i >= 0 && i < ph.span) ? ph.tab[i] : phase_of(ph.gamma * c, (T*)nullptr);
+  }
+  c = ((const double*)ph.C)[r];
+  return phase_of(ph.gamma * c, (T*)nullptr);
+}
+
+template <typename T>
+__device__ __forceinline__ T xy_cmul(T x, T f) {
+  T y;
+  y.x = x.x * f.x - x.y * f.y;
+  y.y = x.x * f.y + x.y * f.x;
+  return y;
+}
+
+template <typename T, bool TWO, bool PH>
 __global__ void __launch_bounds__(kXYThreads)
     xy_window_kernel(const __grid_constant__ xyw::Window W, T* __restrict__ psi, T* __restrict__ lam,
-                     typename Real<T>::type cb, typename Real<T>::type sb, double* __restrict__ part) {
+                     typename Real<T>::type cb, typename Real<T>::type sb, double* __restrict__ part,
+                     const __grid_constant__ XYPhaseArgs<T> ph) {
+  constexpr bool FXR = std::is_same<T, double2>::value && !TWO;  // fixed-point forward tiles
+  using S = typename std::conditional<FXR, longlong2, T>::type;
   __shared__ unsigned long long B[xyw::kBN][xyw::kBN];
   __shared__ unsigned long long rowoff[xyw::kMaxRows];
   __shared__ unsigned long long colbase[xyw::kMaxCols];
@@ -388,12 +443,19 @@ __global__ void __launch_bounds__(kXYThreads)
   __shared__ unsigned char pr0[xyw::kMaxGates][xyw::kMaxPairs], pr1[xyw::kMaxGates][xyw::kMaxPairs];
   __shared__ int npr[xyw::kMaxGates];
   __shared__ double red[kXYThreads / 32];
+  __shared__ unsigned tile_ex;  // fixed-point tiles: largest biased float64 exponent of the tile
   extern __shared__ __align__(16) unsigned char xy_win_smem[];
-  T* tp = (T*)xy_win_smem;     // psi tile
-  T* tl = tp + W.tile_elems;   // lambda tile (TWO)
+  S* tp = (S*)xy_win_smem;     // psi tile
+  S* tl = tp + W.tile_elems;   // lambda tile (TWO)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int c = tid; c < xyw::kBN; c += kXYThreads) xyw::binom_row(B, c);
-  double acc = 0.0;
+  fx::Limbs qc = {0, 0}, qs = {0, 0}, qns = {0, 0};
+  if constexpr (FXR) {
+    qc = fx::split(xy_q62((double)cb));
+    qs = fx::split(xy_q62((double)sb));
+    qns = fx::split(-xy_q62((double)sb));
+  }
+  double acc = 0.0, cacc = 0.0;
   int cur = -1;  // class whose row tables are in shared memory (the same in every thread)
   for (unsigned long long tile = blockIdx.x; tile < W.tiles; tile += gridDim.x) {
     const int ci = xyw::find_class(W, tile);
@@ -429,72 +491,123 @@ __global__ void __launch_bounds__(kXYThreads)
       cur = ci;
     }
     for (int c = tid; c < ncol; c += kXYThreads) colbase[c] = xyw::col_base(W, C, col0 + c, B);
+    if (FXR && tid == 0) tile_ex = 0;
     __syncthreads();
-    // one column per run of consecutive ranks when rows of a column are adjacent (len = 1),
-    // otherwise one row segment of consecutive ranks per warp pass
+    // element e of the tile: column-major when a column's rows are consecutive ranks (len = 1),
+    // otherwise row-major, so consecutive threads touch consecutive ranks
     const bool cm = C.len == 1;
+    const unsigned inner = cm ? (unsigned)rows : (unsigned)ncol;  // < 2^16
+    const unsigned mg = xyw::div_magic(inner);
     const int ne = rows * ncol;
+    unsigned ex_max = 0;
     for (int e = tid; e < ne; e += kXYThreads) {
-      int r, c;
-      if (cm) {
-        c = e / rows;
-        r = e - c * rows;
-      } else {
-        r = e / ncol;
-        c = e - r * ncol;
-      }
+      const unsigned o = xyw::div_small((unsigned)e, mg), i = (unsigned)e - o * inner;
+      const int r = cm ? (int)i : (int)o, c = cm ? (int)o : (int)i;
       const unsigned long long rk = rowoff[r] + colbase[c];
-      tp[e] = psi[rk];
-      if constexpr (TWO) tl[e] = lam[rk];
+      const T x = psi[rk];
+      if constexpr (FXR) {  // raw bits for now; the exponents give the tile's scale
+        const unsigned long long bx = fx::double_to_bits(x.x), by = fx::double_to_bits(x.y);
+        ex_max = max(ex_max, max((unsigned)(bx >> 52) & 0x7FFu, (unsigned)(by >> 52) & 0x7FFu));
+        tp[e] = make_longlong2((long long)bx, (long long)by);
+      } else {
+        T v = x;
+        if constexpr (PH && !TWO) {
+          double cv;
+          v = xy_cmul(v, xy_phase_factor(ph, rk, cv));
+        }
+        tp[e] = v;
+        if constexpr (TWO) tl[e] = lam[rk];
+      }
+    }
+    int fs = 0;  // fixed-point tiles: value = integer x 2^-fs
+    if constexpr (FXR) {
+      ex_max = __reduce_max_sync(0xffffffffu, ex_max);
+      if (lane == 0) atomicMax(&tile_ex, ex_max);
+      __syncthreads();
+      fs = 56 - ((int)tile_ex - 1022);  // every component is below 2^(tile_ex - 1022)
+      for (int e = tid; e < ne; e += kXYThreads) {  // the slots this thread loaded
+        const longlong2 raw = tp[e];
+        longlong2 X = make_longlong2(fx::from_double(fx::bits_to_double((unsigned long long)raw.x), fs),
+                                     fx::from_double(fx::bits_to_double((unsigned long long)raw.y), fs));
+        if constexpr (PH) {  // exp(-i gamma c) as Q62 limbs; a unit factor keeps the bound
+          const unsigned o = xyw::div_small((unsigned)e, mg), i = (unsigned)e - o * inner;
+          const int r = cm ? (int)i : (int)o, c = cm ? (int)o : (int)i;
+          double cv;
+          const T f = xy_phase_factor(ph, rowoff[r] + colbase[c], cv);
+          const long long fre = xy_q62(f.x), fim = xy_q62(f.y);
+          const fx::Limbs fr = fx::split(fre), fi = fx::split(fim), nfi = fx::split(-fim);
+          const fx::Limbs xr = fx::split(X.x), xi = fx::split(X.y);
+          X = make_longlong2(fx::dot2_q62(xr, fr, xi, nfi, 0), fx::dot2_q62(xr, fi, xi, fr, 0));
+        }
+        tp[e] = X;
+      }
     }
     __syncthreads();
+    // gates one after another, each gate's (pair, column) items spread over the block:
+    // consecutive threads take consecutive columns (row-major tiles) or consecutive pairs of
+    // one column (column-major tiles), so shared-memory accesses stay conflict-free
     for (int gi = 0; gi < W.ngates; ++gi) {
       const int g = TWO ? W.ngates - 1 - gi : gi;
       const int np = npr[g];
       const int items = np * ncol;
+      const unsigned in2 = cm ? (unsigned)np : (unsigned)ncol;
+      const unsigned m2 = xyw::div_magic(in2);
       for (int it = tid; it < items; it += kXYThreads) {
-        int q, c;
-        if (cm) {
-          c = it / np;
-          q = it - c * np;
-        } else {
-          q = it / ncol;
-          c = it - q * ncol;
-        }
+        const unsigned o = xyw::div_small((unsigned)it, m2), i = (unsigned)it - o * in2;
+        const int q = cm ? (int)i : (int)o, c = cm ? (int)o : (int)i;
         const int r0 = pr0[g][q], r1 = pr1[g][q];
         const int s0 = cm ? c * rows + r0 : r0 * ncol + c;
         const int s1 = cm ? c * rows + r1 : r1 * ncol + c;
-        T x = tp[s0], y = tp[s1];
-        if constexpr (TWO) {
-          T lx = tl[s0], ly = tl[s1];
-          acc += (double)lx.x * y.y - (double)lx.y * y.x + (double)ly.x * x.y - (double)ly.y * x.x;
-          xy_rotate(lx, ly, cb, sb);
-          tl[s0] = lx;
-          tl[s1] = ly;
+        S x = tp[s0], y = tp[s1];
+        if constexpr (FXR) {
+          xy_rotate_fx(x, y, qc, qs, qns);
+        } else {
+          if constexpr (TWO) {
+            T lx = tl[s0], ly = tl[s1];
+            acc += (double)lx.x * y.y - (double)lx.y * y.x + (double)ly.x * x.y - (double)ly.y * x.x;
+            xy_rotate(lx, ly, cb, sb);
+            tl[s0] = lx;
+            tl[s1] = ly;
+          }
+          xy_rotate(x, y, cb, sb);
         }
-        xy_rotate(x, y, cb, sb);
         tp[s0] = x;
         tp[s1] = y;
       }
       __syncthreads();
     }
     for (int e = tid; e < ne; e += kXYThreads) {
-      int r, c;
-      if (cm) {
-        c = e / rows;
-        r = e - c * rows;
-      } else {
-        r = e / ncol;
-        c = e - r * ncol;
-      }
+      const unsigned o = xyw::div_small((unsigned)e, mg), i = (unsigned)e - o * inner;
+      const int r = cm ? (int)i : (int)o, c = cm ? (int)o : (int)i;
       const unsigned long long rk = rowoff[r] + colbase[c];
-      psi[rk] = tp[e];
-      if constexpr (TWO) lam[rk] = tl[e];
+      if constexpr (FXR) {
+        const longlong2 X = tp[e];
+        psi[rk] = make_double2(fx::to_double(X.x, fs), fx::to_double(X.y, fs));
+      } else if constexpr (TWO) {
+        T x = tp[e], l = tl[e];
+        if constexpr (PH) {
+          double cv;
+          T f = xy_phase_factor(ph, rk, cv);
+          cacc += cv * ((double)l.x * x.y - (double)l.y * x.x);
+          f.y = -f.y;  // exp(+i gamma c)
+          x = xy_cmul(x, f);
+          l = xy_cmul(l, f);
+        }
+        psi[rk] = x;
+        lam[rk] = l;
+      } else {
+        psi[rk] = tp[e];
+      }
     }
   }
   if constexpr (TWO) {
     const double t = block_sum(acc, red);
     if (tid == 0) part[blockIdx.x] = 2.0 * t;
+    if constexpr (PH) {
+      __syncthreads();
+      const double tc = block_sum(cacc, red);
+      if (tid == 0) ph.cpart[blockIdx.x] = 2.0 * tc;
+    }
   }
 }
 
@@ -528,13 +641,35 @@ __global__ void __launch_bounds__(kXYThreads)
                      double* __restrict__ part) {
   __shared__ double se[kXYThreads], sn[kXYThreads];
   double e = 0.0, nn = 0.0;
-  for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < D;
-       r += (unsigned long long)gridDim.x * blockDim.x) {
-    const T x = psi[r];
-    const double pr = (double)x.x * (double)x.x + (double)x.y * (double)x.y;
-    const double c = cost_dtype == QAOA_COST_I32 ? (double)((const int*)C)[r] : ((const double*)C)[r];
-    e += c * pr;
-    nn += pr;
+  if (std::is_same<T, float2>::value && cost_dtype == QAOA_COST_I32) {
+    // complex64 with integer costs: float32 sums of 32 consecutive terms of a thread, added in
+    // float64 (GB300's float64 rate would otherwise bound this pass)
+    float ef = 0.f, nf = 0.f;
+    int cnt = 0;
+    for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < D;
+         r += (unsigned long long)gridDim.x * blockDim.x) {
+      const T x = psi[r];
+      const float pr = (float)x.x * (float)x.x + (float)x.y * (float)x.y;
+      ef = fmaf((float)((const int*)C)[r], pr, ef);
+      nf += pr;
+      if (++cnt == 32) {
+        e += ef;
+        nn += nf;
+        ef = nf = 0.f;
+        cnt = 0;
+      }
+    }
+    e += ef;
+    nn += nf;
+  } else {
+    for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < D;
+         r += (unsigned long long)gridDim.x * blockDim.x) {
+      const T x = psi[r];
+      const double pr = (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+      const double c = cost_dtype == QAOA_COST_I32 ? (double)((const int*)C)[r] : ((const double*)C)[r];
+      e += c * pr;
+      nn += pr;
+    }
   }
   se[threadIdx.x] = e;
   sn[threadIdx.x] = nn;
@@ -699,7 +834,8 @@ int expectation_t(const XYShape& s, const T* psi, const qaoa_cost_t* cost, doubl
 }
 
 // The windows of the ring mixer for (n, k), 0 < k < n, n >= 2: tiles of 32 KB of amplitudes
-// per buffer; the closing pair (0, n - 1) (n >= 3) is a per-gate pass after the windows.
+// per buffer; the first window visits every amplitude, since the layer's cost unitary rides
+// on its pass; the closing pair (0, n - 1) (n >= 3) is a per-gate pass after the windows.
 struct XYMixPlan {
   int nwin;
   bool closing;
@@ -712,7 +848,7 @@ XYMixPlan* make_mix_plan(const XYShape& s) {
   int lo[xyw::kMaxWindows + 1], w[xyw::kMaxWindows + 1];
   mp->nwin = xyw::plan_ring_windows(s.n, lo, w);
   for (int i = 0; i < mp->nwin; ++i)
-    xyw::plan_window(mp->win[i], s.n, s.k, lo[i], w[i], (int)(32768 / sizeof(T)), s.binom);
+    xyw::plan_window(mp->win[i], s.n, s.k, lo[i], w[i], (int)(32768 / sizeof(T)), s.binom, i == 0);
   mp->closing = s.n >= 3;
   return mp;
 }
@@ -724,33 +860,35 @@ size_t window_smem(const xyw::Window& W) {
 
 // one windowed pass; grid = 0 takes every SM's resident blocks (forward), the gradient passes
 // its partial-row grid
-template <typename T, bool TWO>
+template <typename T, bool TWO, bool PH>
 cudaError_t launch_window(const xyw::Window& W, T* psi, T* lam, typename Real<T>::type cb,
-                          typename Real<T>::type sb, double* part, unsigned grid, cudaStream_t st) {
+                          typename Real<T>::type sb, double* part, const XYPhaseArgs<T>& ph, unsigned grid,
+                          cudaStream_t st) {
   static std::mutex mu;
   static unsigned long long done = 0;
   static int per_sm = 1;
-  const size_t max_smem = (size_t)xyw::kMaxRows * (32768 / sizeof(T) / xyw::kMaxRows + 1) * sizeof(T) *
-                          (TWO ? 2 : 1);  // bound on window_smem for the 32 KB tiles
+  const size_t max_smem = (size_t)32768 * (TWO ? 2 : 1);  // tiles hold <= 32 KB of amplitudes per buffer
   {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(mu);
     if (!(done & (1ull << (dev & 63)))) {
-      cudaFuncSetAttribute(xy_window_kernel<T, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xy_window_kernel<T, TWO>, kXYThreads, max_smem);
+      cudaFuncSetAttribute(xy_window_kernel<T, TWO, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, xy_window_kernel<T, TWO, PH>, kXYThreads, max_smem);
       if (per_sm < 1) per_sm = 1;
       done |= 1ull << (dev & 63);
     }
   }
   if (W.tiles == 0) return cudaSuccess;
+  if (window_smem<T, TWO>(W) > max_smem) return cudaErrorInvalidValue;
   if (grid == 0) {
     const unsigned long long g = (unsigned long long)sm_count() * per_sm;
     grid = (unsigned)(W.tiles < g ? W.tiles : g);
   }
-  const double bytes = (double)W.elems * sizeof(T) * 2 * (TWO ? 2 : 1);
+  const double cb_bytes = PH ? (double)W.elems * cost_bytes(ph.cost_dtype) : 0.0;
+  const double bytes = (double)W.elems * sizeof(T) * 2 * (TWO ? 2 : 1) + cb_bytes;
   note_launch(0, st, true);
-  xy_window_kernel<T, TWO><<<grid, kXYThreads, window_smem<T, TWO>(W), st>>>(W, psi, lam, cb, sb, part);
+  xy_window_kernel<T, TWO, PH><<<grid, kXYThreads, window_smem<T, TWO>(W), st>>>(W, psi, lam, cb, sb, part, ph);
   note_launch(0, st, false, bytes);
   return cudaGetLastError();
 }
@@ -786,15 +924,20 @@ int layers_t(const XYShape& s, T* psi, const qaoa_cost_t* cost, const double* ga
   const unsigned long long moved = s.n >= 2 && s.k >= 1 && s.k <= s.n - 1 ? 2 * s.binom[s.n - 2][s.k - 1] : 0;
   const unsigned long long nch = (s.D + kXYChunk - 1) / kXYChunk;
   for (int l = 0; l < p; ++l) {
-    note_launch(0, st, true);
-    xy_phase_kernel<T><<<grid_for(s.D, sms), kXYThreads, 0, st>>>(psi, cost->C_dev, cost->dtype, s.D,
-                                                                  tab ? tab + (size_t)l * span : nullptr,
-                                                                  cost->cmin, span, gamma[l]);
-    note_launch(0, st, false, (double)s.D * (2 * sb + cost_bytes(cost->dtype)));
+    const XYPhaseArgs<T> ph = {cost->C_dev, cost->dtype, tab ? tab + (size_t)l * span : nullptr, cost->cmin, span,
+                               gamma[l], nullptr};
+    if (mp == nullptr) {  // no mixer (k = 0 or k = n): the cost unitary alone
+      note_launch(0, st, true);
+      xy_phase_kernel<T><<<grid_for(s.D, sms), kXYThreads, 0, st>>>(psi, cost->C_dev, cost->dtype, s.D, ph.tab,
+                                                                    cost->cmin, span, gamma[l]);
+      note_launch(0, st, false, (double)s.D * (2 * sb + cost_bytes(cost->dtype)));
+    }
     const R cb = (R)std::cos(beta[l]), snb = (R)std::sin(beta[l]);
-    if (mp != nullptr) {  // the ring mixer: windowed passes, then the closing pair
+    if (mp != nullptr) {  // the cost unitary on the first window's pass, the ring mixer, the closing pair
       for (int i = 0; i < mp->nwin; ++i) {
-        const cudaError_t e = launch_window<T, false>(mp->win[i], psi, nullptr, cb, snb, nullptr, 0, st);
+        const cudaError_t e =
+            i == 0 ? launch_window<T, false, true>(mp->win[i], psi, nullptr, cb, snb, nullptr, ph, 0, st)
+                   : launch_window<T, false, false>(mp->win[i], psi, nullptr, cb, snb, nullptr, ph, 0, st);
         if (e != cudaSuccess) {
           delete mp;
           return QAOA_ERR_CUDA;
@@ -850,6 +993,7 @@ int gradient_t(const XYShape& s, T* psi, T* lam, const qaoa_cost_t* cost, const 
   // every row written by a launch of gg blocks
   XYMixPlan* mp = np > 0 && p > 0 ? make_mix_plan<T>(s) : nullptr;
   const int brows = mp != nullptr ? mp->nwin + (mp->closing ? 1 : 0) : 0;
+  const bool fused = mp != nullptr;  // gamma terms from the first window's pass (gg blocks)
   for (int l = p - 1; l >= 0; --l) {
     const R cb = (R)std::cos(beta[l]), snb = (R)(-std::sin(beta[l]));
     double* rows = part + (size_t)(2 + p + (size_t)l * np) * kXYPartStride;
@@ -860,20 +1004,25 @@ int gradient_t(const XYShape& s, T* psi, T* lam, const qaoa_cost_t* cost, const 
                                                               rows + (size_t)mp->nwin * kXYPartStride);
         note_launch(0, st, false, (double)moved * 4 * sb);
       }
+      // the first window's pass also takes the gamma term and undoes the cost unitary
+      const XYPhaseArgs<T> ph = {cost->C_dev, cost->dtype, tab ? tab + (size_t)l * span : nullptr, cost->cmin,
+                                 span, gamma[l], part + (size_t)(2 + l) * kXYPartStride};
       for (int i = mp->nwin - 1; i >= 0; --i) {
-        const cudaError_t e =
-            launch_window<T, true>(mp->win[i], psi, lam, cb, snb, rows + (size_t)i * kXYPartStride, gg, st);
+        double* row = rows + (size_t)i * kXYPartStride;
+        const cudaError_t e = i == 0 ? launch_window<T, true, true>(mp->win[i], psi, lam, cb, snb, row, ph, gg, st)
+                                     : launch_window<T, true, false>(mp->win[i], psi, lam, cb, snb, row, ph, gg, st);
         if (e != cudaSuccess) {
           delete mp;
           return QAOA_ERR_CUDA;
         }
       }
+    } else {
+      note_launch(0, st, true);
+      xy_cost_adjoint_kernel<T><<<gr, kXYThreads, 0, st>>>(psi, lam, cost->C_dev, cost->dtype, s.D,
+                                                           tab ? tab + (size_t)l * span : nullptr, cost->cmin, span,
+                                                           gamma[l], part + (size_t)(2 + l) * kXYPartStride);
+      note_launch(0, st, false, (double)s.D * (4 * sb + cost_bytes(cost->dtype)));
     }
-    note_launch(0, st, true);
-    xy_cost_adjoint_kernel<T><<<gr, kXYThreads, 0, st>>>(psi, lam, cost->C_dev, cost->dtype, s.D,
-                                                         tab ? tab + (size_t)l * span : nullptr, cost->cmin, span,
-                                                         gamma[l], part + (size_t)(2 + l) * kXYPartStride);
-    note_launch(0, st, false, (double)s.D * (4 * sb + cost_bytes(cost->dtype)));
     rc = status_of(cudaGetLastError());
     if (rc) {
       delete mp;
@@ -886,7 +1035,7 @@ int gradient_t(const XYShape& s, T* psi, T* lam, const qaoa_cost_t* cost, const 
   rp.nout = 2 + 2 * p;
   for (int o = 0; o < 2; ++o) rp.first[o] = o, rp.rows[o] = 1, rp.cols[o] = (int)gr;
   for (int l = 0; l < p; ++l) {
-    rp.first[2 + l] = 2 + l, rp.rows[2 + l] = 1, rp.cols[2 + l] = (int)gr;
+    rp.first[2 + l] = 2 + l, rp.rows[2 + l] = 1, rp.cols[2 + l] = (int)(fused ? gg : gr);
     rp.first[2 + p + l] = 2 + p + l * np, rp.rows[2 + p + l] = brows, rp.cols[2 + p + l] = (int)gg;
   }
   note_launch(3, st, true);

@@ -16,7 +16,8 @@
 // Columns are ordered H-major (H by its rank among the patterns of nh = n - lo - w bits with
 // popcount h) and rank(L)-minor, so a row of a tile reads runs of consecutive ranks.  A tile
 // is up to m consecutive columns of one class.  Classes with kw = 0 or kw = w have a single
-// row that no gate of the window changes; they are not visited.
+// row that no gate of the window changes; only a pass that also applies the cost unitary
+// (to every amplitude) visits them.
 //
 // The ring mixer applies the pairs (a, a + 1) with a even, then those with a odd, then the
 // closing pair (0, n - 1).  The windows [0, e_0), [e_0 - 1, e_1), [e_1 - 1, e_2), ... (every
@@ -45,7 +46,7 @@ constexpr int kMaxRows = 126;                            // binom(9, 4)
 constexpr int kMaxPairs = 35;                            // binom(7, 3): rows one gate moves
 constexpr int kMaxCols = 512;                            // columns per tile
 constexpr int kMaxGates = kMaxW - 1;                     // pairs inside one window
-constexpr int kMaxClasses = (kMaxN - 1) * (kMaxW - 1);  // h = 0..nh <= n - 2, kw = 1..w-1
+constexpr int kMaxClasses = (kMaxN - 1) * (kMaxW + 1);  // h = 0..nh <= n - 2, kw = 0..w
 constexpr int kMaxWindows = (kMaxN + 6) / 8 + 1;         // [0, 8), then 8 new qubits per window
 
 typedef unsigned long long u64;
@@ -121,6 +122,18 @@ XYW_HD int partner_row(int r, unsigned P, int ga, const u64 (*B)[kBN]) {
   return r + (int)B[ga][popc32(P & ((1u << ga) - 1u))];
 }
 
+// x / d for x, d < 2^16 as a multiply-high by m = floor(2^32 / d) + 1 (d >= 2): exact,
+// because x (m d - 2^32) <= x d < 2^32; m = 0 stands for d = 1
+XYW_HD unsigned div_magic(unsigned d) { return d < 2 ? 0u : (unsigned)((1ull << 32) / d + 1); }
+XYW_HD unsigned div_small(unsigned x, unsigned m) {
+  if (m == 0) return x;
+#ifdef __CUDA_ARCH__
+  return __umulhi(x, m);
+#else
+  return (unsigned)(((u64)x * m) >> 32);
+#endif
+}
+
 XYW_HD int find_class(const Window& W, u64 tile) {
   int a = 0, b = W.ncls - 1;
   while (a < b) {
@@ -159,8 +172,10 @@ inline int plan_ring_windows(int n, int* lo, int* w) {
 }
 
 // Window [lo, lo + w) of the ring mixer on n qubits: its pairs and its tile classes.
-// `target` = amplitudes per tile (per buffer).
-inline void plan_window(Window& W, int n, int k, int lo, int w, int target, const u64 (*B)[kBN]) {
+// `target` = amplitudes per tile (per buffer); `every_state` also visits the single-row
+// classes (kw = 0, kw = w), for a pass that applies the cost unitary to every amplitude.
+inline void plan_window(Window& W, int n, int k, int lo, int w, int target, const u64 (*B)[kBN],
+                        bool every_state = false) {
   W.n = n;
   W.k = k;
   W.lo = lo;
@@ -175,7 +190,7 @@ inline void plan_window(Window& W, int n, int k, int lo, int w, int target, cons
   W.elems = 0;
   W.tile_elems = 0;
   for (int h = 0; h <= W.nh; ++h) {
-    for (int kw = 1; kw <= w - 1; ++kw) {
+    for (int kw = every_state ? 0 : 1; kw <= (every_state ? w : w - 1); ++kw) {
       const int kL = k - h - kw;
       if (kL < 0 || kL > lo) continue;
       Class& C = W.cls[W.ncls++];

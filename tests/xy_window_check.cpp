@@ -1,10 +1,11 @@
 // Host check of the windowed XY-mixer passes (paper_2407_13012_gb300/csrc/xy_window.cuh):
+//  * the multiply-high division of the tile index arithmetic is exact;
 //  * the windows' pairs plus the closing pair are the ring pairs, each exactly once, and
 //    every odd pair comes after the even pairs it shares a qubit with;
 //  * for every (n, k) with n <= 16, every tile element's rank is in range, is visited once,
 //    and is the state whose bits below / inside / above the window are the column's L, the
 //    row's pattern and the column's H; exactly the states whose window popcount lies in
-//    1 .. w - 1 are visited;
+//    1 .. w - 1 are visited (every state, for the pass that carries the cost unitary);
 //  * a pair's partner row is the row of the pattern with that set bit moved up by one;
 //  * for n up to 40 the class tables count the right states and sampled tiles address
 //    states of the right shape; every size stays inside the kernel's fixed arrays.
@@ -105,9 +106,9 @@ static void check_windows(int n) {
 }
 
 // every element of every tile of window [lo, lo + w) for (n, k), against brute force
-static void check_tiles_exhaustive(int n, int k, int lo, int w, int target) {
+static void check_tiles_exhaustive(int n, int k, int lo, int w, int target, bool every) {
   Window W;
-  plan_window(W, n, k, lo, w, target, Bt);
+  plan_window(W, n, k, lo, w, target, Bt, every);
   std::vector<u64> states;
   for (u64 z = 0; z < (1ull << n); ++z)
     if (popc(z) == k) states.push_back(z);
@@ -165,13 +166,13 @@ static void check_tiles_exhaustive(int n, int k, int lo, int w, int target) {
         CHECK(r2 > r && r2 < C.rows, "partner range");
         if (r2 < C.rows) CHECK(pat[r2] == (pat[r] ^ (3u << ga)), "partner pattern");
       }
-      CHECK(np >= 1 && np <= kMaxPairs, "pairs per gate %d", np);
+      CHECK((C.rows == 1 ? np == 0 : np >= 1) && np <= kMaxPairs, "pairs per gate %d", np);
     }
   }
   CHECK(elems == W.elems, "elems count");
   for (u64 rk = 0; rk < D; ++rk) {
     const int kw = popc((states[rk] >> lo) & ((1ull << w) - 1));
-    const int want = (kw >= 1 && kw <= w - 1) ? 1 : 0;
+    const int want = (every || (kw >= 1 && kw <= w - 1)) ? 1 : 0;
     CHECK(seen[rk] == want, "n=%d k=%d lo=%d w=%d: rank %llu seen %d want %d", n, k, lo, w, rk, seen[rk], want);
   }
 }
@@ -183,10 +184,12 @@ static void check_tables_large(int n, int k, int target) {
   const u64 D = binom(n, k);
   for (int i = 0; i < nw; ++i) {
     Window W;
-    plan_window(W, n, k, lo[i], w[i], target, Bt);
+    plan_window(W, n, k, lo[i], w[i], target, Bt, i == 0);  // the first window carries the cost unitary
     CHECK(W.ncls <= kMaxClasses, "classes");
+    CHECK(W.tile_elems <= target, "tile larger than the target");
     u64 want = 0;
-    for (int kw = 1; kw <= w[i] - 1; ++kw) want += binom(w[i], kw) * binom(n - w[i], k - kw);
+    for (int kw = (i == 0 ? 0 : 1); kw <= w[i] - (i == 0 ? 0 : 1); ++kw) want += binom(w[i], kw) * binom(n - w[i], k - kw);
+    if (i == 0) CHECK(want == D, "every state");
     CHECK(W.elems == want, "n=%d k=%d window %d: elems %llu want %llu", n, k, i, W.elems, want);
     if (W.tiles == 0) continue;
     const u64 samples[4] = {0, W.tiles / 3, (W.tiles * 2) / 3, W.tiles - 1};
@@ -217,17 +220,21 @@ int main() {
   for (int c = 0; c < kBN; ++c) binom_row(Bt, c);
   for (int c = 0; c < kBN; ++c)
     for (int i = 0; i < kBN; ++i) CHECK(Bt[c][i] == binom(c, i), "binomial table %d %d", c, i);
+  for (unsigned d = 1; d < (1u << 16); d += (d < 600 ? 1 : 97))
+    for (unsigned x = 0; x < (1u << 16); x += (x < 5000 ? 1 : 31))
+      CHECK(div_small(x, div_magic(d)) == x / d, "division %u / %u", x, d);
   for (int n = 2; n <= kMaxN; ++n) check_windows(n);
   for (int n = 2; n <= 16; ++n) {
     int lo[kMaxWindows + 1], w[kMaxWindows + 1];
     const int nw = plan_ring_windows(n, lo, w);
     for (int k = 1; k <= n - 1; ++k)
       for (int i = 0; i < nw; ++i)
-        for (int target : {2048, 40})  // the kernels' tile size and a small one (many ragged tiles)
-          check_tiles_exhaustive(n, k, lo[i], w[i], target);
+        for (int target : {2048, 4096, 40})  // the kernels' tile sizes and a small one (ragged tiles)
+          for (bool every : {false, true}) check_tiles_exhaustive(n, k, lo[i], w[i], target, every);
   }
   for (int n : {20, 24, 28, 31, 32, 36, 40})
-    for (int k = 1; k <= n - 1; ++k) check_tables_large(n, k, 2048);
+    for (int k = 1; k <= n - 1; ++k)
+      for (int target : {2048, 4096}) check_tables_large(n, k, target);
   if (fails) {
     std::printf("%d failures\n", fails);
     return 1;
