@@ -1,15 +1,21 @@
-// Batched adjoint gradients: thousands of small graphs (n ~ 8..20) in one persistent launch.
+// Batched adjoint gradients: thousands of small graphs (n ~ 8..20).
 //
 // The per-graph computation is the plain method (cost vector, Eq. 1's p layers, <C>, and
 // the adjoint gradient of Sec. IV-D); only the scheduling differs from the one-graph path.
-// One CTA owns one graph at a time: it runs the graph's whole sweep plan over the graph's
-// own state buffers, tile after tile, with CTA barriers between sweeps, and writes the
-// graph's outputs from its block accumulators, so no launch boundary or cross-CTA reduction
-// separates the sweeps.  complex128 sweeps on full 2^12 tiles use the lean tile code
-// (compile-time layout sequences; forward sweeps on psi alone), the rest the generic
-// program (for complex64 the lean form spilled and measured slower).  Graphs come off a work counter largest first, which balances the
-// CTAs (longest-processing-time order).  Small graphs (n <= 10) run on 2^10-amplitude tiles,
-// larger ones on 2^12; the host may pick per qubit count from measured times.
+// One prep launch builds every graph's cost vector and tables.  Then the graphs run in one
+// of two ways, by size (the host decides, capi.cu):
+//  * grouped sweeps (the larger graphs, whose one-graph plan is all lean sweeps): the graphs
+//    of one size run the one-graph gradient plan together, each sweep one launch of the
+//    one-graph lean kernel over all of them, each block on its own graph's tiles, tables and
+//    angles (GroupSlot), then one reduction per size;
+//  * the persistent kernel below (the rest): one CTA owns one graph at a time and runs the
+//    graph's whole sweep plan over the graph's own buffers, tile after tile, with CTA
+//    barriers between sweeps, writing the graph's outputs from its block accumulators.
+//    complex128 sweeps on full 2^12 tiles use the lean tile code, the rest the generic
+//    program (for complex64 the lean form spilled and measured slower).  Graphs come off a
+//    work counter largest first (longest-processing-time order).  Small graphs (n <= 10)
+//    run on 2^10-amplitude tiles, larger ones on 2^12; the host may pick per qubit count
+//    from measured times.
 #include "batch_kernel.cuh"
 
 namespace qaoa {
@@ -17,16 +23,21 @@ namespace {
 
 constexpr int kPrepThreads = 256;
 constexpr int kMaxBatchEdges = 512;
+static_assert(QAOA_BATCH_MAX_EDGES <= kMaxBatchEdges, "edge staging holds every edge of a graph");
+static_assert(QAOA_BATCH_MAX_N < 32, "cost-vector indices in 32 bits");
 
 // One launch prepares every graph: blocks [0, cost_blocks) build the cost vectors (2^12
-// entries per block, C(z) = sum over edges of w [z_u != z_v], Sec. III-B's MaxCut cost,
-// int32 for integer weights, else float64 summed in edge order);
-// the next ngraphs blocks build each graph's per-layer terms and tables; the last block
-// (fixed point) builds the shared turn tables.
+// entries per block, C(z) = sum over edges of w [z_u != z_v], Sec. III-B's MaxCut cost, int32
+// for integer weights; float weights are quantised once to a common fixed point,
+// 2^-(62 - e) with sum |w| < 2^e, summed exactly in int64 and rounded once to float64, as the
+// one-graph cost kernel does); the next ngraphs blocks build each graph's per-layer terms and
+// tables; the last block (fixed point) builds the shared turn tables.
 __global__ void __launch_bounds__(kPrepThreads) batch_prep_kernel(const __grid_constant__ BatchArgs b,
                                                                    int64_t cost_blocks) {
   __shared__ int2 e_s[kMaxBatchEdges];
-  __shared__ double w_s[kMaxBatchEdges];
+  __shared__ int wi_s[kMaxBatchEdges];        // integer weights
+  __shared__ long long wq_s[kMaxBatchEdges];  // float weights in fixed point
+  __shared__ int shift_s;
   const int64_t blk = blockIdx.x;
   const int tid = threadIdx.x;
   const int p = b.p;
@@ -39,23 +50,39 @@ __global__ void __launch_bounds__(kPrepThreads) batch_prep_kernel(const __grid_c
       else hi = mid - 1;
     }
     const BatchGraph G = b.graphs[lo];
-    for (int k = tid; k < G.m; k += kPrepThreads) {
-      e_s[k] = make_int2(b.edges[2 * (G.edge + k)], b.edges[2 * (G.edge + k) + 1]);
-      w_s[k] = b.ew[G.edge + k];
+    if (tid == 0) {
+      int sh = 0;
+      if (b.cost_f64) {  // sum |w| in edge order, as the host does for the one-graph kernel
+        double sa = 0.0;
+        for (int k = 0; k < G.m; ++k) sa += fabs(b.ew[G.edge + k]);
+        int e2 = 0;
+        frexp(sa > 0.0 ? sa : 1.0, &e2);
+        sh = 62 - e2;
+      }
+      shift_s = sh;
     }
     __syncthreads();
-    const uint64_t z0 = (uint64_t)(blk - b.blk_off[lo]) << kBatchCostBits;
-    const uint64_t zend = 1ull << G.n;
-    for (uint64_t z = z0 + tid; z < z0 + (1ull << kBatchCostBits) && z < zend; z += kPrepThreads) {
-      if (b.cost_f64) {  // float64 sum in edge order
-        double c = 0.0;
+    for (int k = tid; k < G.m; k += kPrepThreads) {
+      e_s[k] = make_int2(b.edges[2 * (G.edge + k)], b.edges[2 * (G.edge + k) + 1]);
+      const double w = b.ew[G.edge + k];
+      if (b.cost_f64) wq_s[k] = llrint(ldexp(w, shift_s));
+      else wi_s[k] = (int)w;
+    }
+    __syncthreads();
+    // n <= QAOA_BATCH_MAX_N < 32: 32-bit indices
+    const uint32_t z0 = (uint32_t)(blk - b.blk_off[lo]) << kBatchCostBits;
+    const uint32_t zend = min(z0 + (1u << kBatchCostBits), 1u << G.n);
+    if (b.cost_f64) {
+      for (uint32_t z = z0 + tid; z < zend; z += kPrepThreads) {
+        long long c = 0;
         for (int k = 0; k < G.m; ++k)
-          if (((z >> e_s[k].x) ^ (z >> e_s[k].y)) & 1ull) c += w_s[k];
-        ((double*)b.C)[G.cost + (int64_t)z] = c;
-      } else {
+          if (((z >> e_s[k].x) ^ (z >> e_s[k].y)) & 1u) c += wq_s[k];
+        ((double*)b.C)[G.cost + (int64_t)z] = ldexp((double)c, -shift_s);
+      }
+    } else {
+      for (uint32_t z = z0 + tid; z < zend; z += kPrepThreads) {
         int c = 0;
-        for (int k = 0; k < G.m; ++k)
-          if (((z >> e_s[k].x) ^ (z >> e_s[k].y)) & 1ull) c += (int)w_s[k];
+        for (int k = 0; k < G.m; ++k) c += (int)(((z >> e_s[k].x) ^ (z >> e_s[k].y)) & 1u) * wi_s[k];
         ((int*)b.C)[G.cost + (int64_t)z] = c;
       }
     }

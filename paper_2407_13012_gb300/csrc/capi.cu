@@ -932,9 +932,10 @@ struct BatchLayout {
   std::vector<int64_t> blk_off;
   std::vector<double> angles;      // processing order
   int n_large = 0;                 // graphs [0, n_large) use 2^12 tiles, the rest 2^10
+  int n_grouped = 0;               // graphs [0, n_grouped) run as grouped one-graph sweeps
   size_t off_graphs = 0, off_plans = 0, off_blk = 0, off_edges = 0, off_ew = 0, off_angles = 0, head_bytes = 0;
   size_t off_queue = 0, off_trig = 0, off_psi = 0, off_lam = 0, off_C = 0, off_phase = 0, off_dtab = 0,
-         off_turn = 0, total = 0;
+         off_turn = 0, off_gslot = 0, off_grow = 0, off_gpart = 0, total = 0;
 };
 
 int default_tile(int n) { return n <= 10 ? 0 : 1; }
@@ -1003,6 +1004,50 @@ int batch_plan(int n, int B, int RB, bool fx, bool cost_f64, int p, BatchPlan& P
     }
   }
   return QAOA_OK;
+}
+
+// Grouped batched gradients: graphs of one size n run the one-graph gradient plan together,
+// each sweep one launch of the lean kernel over all of them (GroupSlot: per-graph offsets,
+// tables, angles; kGroupTiles tiles or more per block).  A plan qualifies when every sweep
+// runs the lean code; smaller graphs stay in the persistent batch kernel.
+constexpr int kGroupMinN = 15;   // below, the plan has groups of < 3 qubits (generic sweeps)
+constexpr int kGroupTiles = 8;   // tiles per block and graph, at least (up to kGroupMaxBpg blocks)
+constexpr int kGroupMaxBpg = 16;
+
+struct GroupPlan {
+  int B = 0;
+  std::vector<Group> gs;
+  std::vector<Sweep> sw;
+  std::vector<int> ncontrib;
+  int nout = 0;
+  int bpg = 1;
+};
+
+static bool group_plan(int n, int dtype, int p, bool cost_f64, GroupPlan& G) {
+  if (n < kGroupMinN) return false;
+  G.B = sweep_tile_bits(dtype, true);
+  G.gs = plan_groups(n, G.B);
+  G.sw.clear();
+  G.nout = 2 * p + 2;
+  G.ncontrib.assign(G.nout, 0);
+  plan_gradient((int)G.gs.size(), p, G.sw, [&](Sweep& s, int out0, int outs) {
+    const uint32_t acc = (uint32_t)s.red_slot.size();
+    for (int i = 0; i < outs; ++i) {
+      s.red_slot.push_back((out0 + i) * kMaxContrib + G.ncontrib[out0 + i]);
+      G.ncontrib[out0 + i]++;
+    }
+    return acc;
+  });
+  for (int o = 0; o < G.nout; ++o)
+    if (G.ncontrib[o] > kMaxContrib) return false;
+  int64_t tiles = 1;
+  for (const Sweep& s : G.sw) {
+    if ((int)s.ops.size() > kMaxOps || (int)s.red_slot.size() > kMaxAcc) return false;
+    if (lean_kind(s, G.gs[s.group], G.B, dtype, cost_f64) == SWEEP_GENERIC) return false;
+    tiles = std::max(tiles, tiles_of(G.gs[s.group], n));
+  }
+  G.bpg = (int)std::max<int64_t>(1, std::min<int64_t>(kGroupMaxBpg, tiles / kGroupTiles));
+  return true;
 }
 
 int batch_layout(int dtype, int p, int ngraphs, const qaoa_graph_t* gs, const double* angles, const int32_t* tiles,
@@ -1082,6 +1127,20 @@ int batch_layout(int dtype, int p, int ngraphs, const qaoa_graph_t* gs, const do
       for (int j = 0; j < 2 * p; ++j) L.angles[(size_t)k * 2 * p + j] = angles[(size_t)i * 2 * p + j];
     if (tile[i] == 1) L.n_large = k + 1;
   }
+  // leading large-tile graphs whose size has an all-lean grouped plan
+  size_t gpart = 0;
+  {
+    int k = 0;
+    while (k < L.n_large) {
+      int e = k;
+      while (e < L.n_large && L.graphs[e].n == L.graphs[k].n) ++e;
+      GroupPlan G;
+      if (!group_plan(L.graphs[k].n, dtype, p, L.cost_f64, G)) break;
+      gpart = std::max(gpart, (size_t)G.nout * kMaxContrib * (size_t)(e - k) * G.bpg * sizeof(double));
+      k = e;
+    }
+    L.n_grouped = k;
+  }
   if (L.edges.empty()) {
     L.edges.assign(2, 0);
     L.ew.assign(1, 0.0);
@@ -1107,8 +1166,93 @@ int batch_layout(int dtype, int p, int ngraphs, const qaoa_graph_t* gs, const do
   L.off_phase = take(vs * std::max<int64_t>(tab, 1));
   L.off_dtab = take(fx ? (size_t)16 * p * 196 * std::max(ngraphs, 1) : 0);
   L.off_turn = take(fx ? (size_t)16 * 3072 : 0);
+  L.off_gslot = take(sizeof(GroupSlot) * std::max(L.n_grouped, 1));
+  L.off_grow = take(sizeof(int) * std::max(L.n_grouped, 1));
+  L.off_gpart = take(std::max<size_t>(gpart, 8));
   L.total = o;
   return QAOA_OK;
+}
+
+// the grouped sweeps of graphs [k0, k1) (one size; GroupSlots and output rows already on the
+// device at slot and row)
+static int run_group(int dtype, int p, const BatchLayout& L, const BatchArgs& b, int k0, int k1,
+                     const GroupSlot* slot, const int* row, double* partials, cudaStream_t st) {
+  const int n = L.graphs[k0].n, ng = k1 - k0;
+  GroupPlan G;
+  if (!group_plan(n, dtype, p, L.cost_f64, G)) return QAOA_ERR_UNSUPPORTED;
+  const bool fx = dtype == QAOA_C128;
+  int tmax = 1;
+  for (const Group& g : G.gs) tmax = std::max(tmax, g.t);
+  const int S = fx_shift_for(tmax);
+  const double amp0 = std::pow(2.0, -0.5 * n);
+  const int grid = ng * G.bpg;
+  const size_t vs = fx ? 16 : 8;
+  int max_span = 0;
+  for (int k = k0; k < k1; ++k) max_span = std::max(max_span, L.graphs[k].span);
+  for (const Sweep& s : G.sw) {
+    SweepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.psi = b.psi;
+    a.lam = s.two ? b.lam : nullptr;
+    a.C = b.C;
+    a.cost_dtype = L.cost_f64 ? QAOA_COST_F64 : QAOA_COST_I32;
+    const Group& g = G.gs[s.group];
+    a.g = {n, g.j0, g.t, g.c, tiles_of(g, n)};
+    a.tile_bits = G.B;
+    a.load_fmt = s.init ? 2 : 0;
+    a.store_fmt = s.store_psi ? 0 : -1;
+    a.load_lam = s.load_lam;
+    a.store_lam = s.store_lam;
+    a.fx_shift = S;
+    a.init_fx = (long long)std::llrint(std::ldexp(amp0, S));
+    a.init_f32 = (float)amp0;
+    a.nops = (int)s.ops.size();
+    bool reads_c = false;
+    for (size_t k = 0; k < s.ops.size(); ++k) {
+      a.ops[k] = s.ops[k];
+      const uint32_t kind = s.ops[k] & 0xff;
+      reads_c |= (kind == OP_PHASE || kind == OP_LAMBDA || kind == OP_RED_EXPECT || kind == OP_RED_CTERM);
+    }
+    a.needs_cost = reads_c;
+    a.np = p;
+    a.dev_trig = b.trig;  // per graph: GroupSlot.trig
+    a.phase_table = max_span > 0 ? b.phase : nullptr;
+    a.span = max_span;  // shared-memory sizing; each graph's own span is in its slot
+    a.smem_table_layer = -1;
+    if (max_span > 0 && max_span <= kSmemTable) {
+      for (uint32_t op : s.ops)
+        if ((op & 0xff) == OP_PHASE) {
+          a.smem_table_layer = (int)((op >> 16) & 0xff);
+          break;
+        }
+    }
+    a.d_table = b.dtab;
+    a.turn_table = b.turn;
+    a.nred = (int)s.red_slot.size();
+    for (int r = 0; r < a.nred; ++r) a.red_slot[r] = s.red_slot[r];
+    a.partials = partials;
+    a.grid = grid;
+    a.gslot = slot;
+    a.gbpg = G.bpg;
+    const double cb = L.cost_f64 ? 8.0 : 4.0;
+    const double per = (double)vs * ((s.init ? 0 : 1) + (s.store_psi ? 1 : 0) + (s.two && s.load_lam ? 1 : 0) +
+                                     (s.two && s.store_lam ? 1 : 0)) +
+                       (reads_c ? cb : 0.0);
+    a.algo_bytes = per * (double)(1ull << n) * ng;
+    a.kind = lean_kind(s, g, G.B, dtype, L.cost_f64);
+    if (a.kind == SWEEP_GENERIC) return QAOA_ERR_UNSUPPORTED;
+    const int rc = cuda_status(launch_sweep(dtype, s.two, a, st));
+    if (rc) return rc;
+  }
+  ReducePlan r;
+  std::memset(&r, 0, sizeof(r));
+  r.nout = G.nout;
+  r.grid = grid;
+  for (int o = 0; o < G.nout; ++o) {
+    r.ncontrib[o] = G.ncontrib[o];
+    r.scale[o] = 1.0;
+  }
+  return cuda_status(launch_group_reduce(r, ng, G.bpg, row, partials, b.out, st));
 }
 
 int batch_run(int dtype, int p, const BatchLayout& L, double* out_dev, void* ws_dev, size_t ws_bytes, void* stream) {
@@ -1150,8 +1294,40 @@ int batch_run(int dtype, int p, const BatchLayout& L, double* out_dev, void* ws_
   b.out = out_dev;
   int rc = cuda_status(launch_batch_prep(b, L.blk_off[ng], s));
   if (rc) return rc;
+  if (L.n_grouped > 0) {  // per-graph slots of the grouped sweeps (device addresses in this workspace)
+    const bool fx = dtype == QAOA_C128;
+    const size_t vs = fx ? 16 : 8;
+    std::vector<GroupSlot> slots(L.n_grouped);
+    std::vector<int> rows(L.n_grouped);
+    for (int k = 0; k < L.n_grouped; ++k) {
+      const BatchGraph& G = L.graphs[k];
+      GroupSlot& g = slots[k];
+      g.zoff = G.state;
+      g.phase_table = G.span > 0 ? (const void*)((char*)b.phase + G.table * vs) : nullptr;
+      g.cmin = G.cmin;
+      g.span = G.span;
+      g.d_table = fx ? (const void*)((char*)b.dtab + (size_t)k * p * 196 * sizeof(longlong2)) : nullptr;
+      g.trig = b.trig + (size_t)k * 3 * p;
+      g.lam_shift = G.lam_shift;
+      rows[k] = G.out;
+    }
+    if (cudaMemcpyAsync(ws + L.off_gslot, slots.data(), sizeof(GroupSlot) * slots.size(), cudaMemcpyHostToDevice,
+                        s) != cudaSuccess ||
+        cudaMemcpyAsync(ws + L.off_grow, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+      return QAOA_ERR_CUDA;
+    int k = 0;
+    while (k < L.n_grouped) {
+      int e = k;
+      while (e < L.n_grouped && L.graphs[e].n == L.graphs[k].n) ++e;
+      rc = run_group(dtype, p, L, b, k, e, (const GroupSlot*)(ws + L.off_gslot) + k, (const int*)(ws + L.off_grow) + k,
+                     (double*)(ws + L.off_gpart), s);
+      if (rc) return rc;
+      k = e;
+    }
+  }
   int* queue = (int*)(ws + L.off_queue);
-  rc = cuda_status(launch_batch(b, 1, 0, L.n_large, queue, s));
+  rc = cuda_status(launch_batch(b, 1, L.n_grouped, L.n_large - L.n_grouped, queue, s));
   if (rc) return rc;
   return cuda_status(launch_batch(b, 0, L.n_large, ng - L.n_large, queue + 1, s));
 }

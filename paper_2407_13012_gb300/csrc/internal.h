@@ -56,6 +56,18 @@ struct SweepGeom {
 
 enum SweepKind : int { SWEEP_GENERIC = 0, SWEEP_LEAN_MIX = 1, SWEEP_LEAN_OPS = 2 };
 
+// One graph of a grouped sweep (batched gradients): the lean kernel runs the same sweep for
+// many graphs of one size, blocks [g * gbpg, (g + 1) * gbpg) on graph g, whose state, lambda
+// and cost vector start zoff elements into the arenas and whose tables and angles are its own.
+struct GroupSlot {
+  int64_t zoff;
+  const void* phase_table;  // p * span entries, or nullptr
+  int64_t cmin, span;
+  const void* d_table;      // fixed point: p * 14 * 14 mixer-diagonal entries
+  const double* trig;       // [g2pi p | cos p | sin p]
+  int lam_shift;            // fixed point: 2^lam_shift >= max |C|
+};
+
 struct SweepArgs {
   int kind;  // SweepKind: generic op program or one of the lean shapes
   void* psi;
@@ -99,6 +111,9 @@ struct SweepArgs {
   double* partials;
   int grid;
   double algo_bytes;  // HBM bytes this sweep must move (for timing reports)
+  // grouped sweeps (lean kernels only): per-graph data, blocks per graph; nullptr = one graph
+  const GroupSlot* gslot;
+  int gbpg;
 };
 
 // A reduction plan: out[o] = scale[o] * sum over contributions k < ncontrib[o] and
@@ -125,6 +140,10 @@ struct TableArgs {
 // launchers (return a CUDA error code)
 cudaError_t launch_sweep(int dtype, bool two, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_reduce(const ReducePlan& r, const double* partials, double* out, cudaStream_t s);
+// out[out_row[g] * nout + o] = sum over contributions k < ncontrib[o] and the blocks j < bpg of
+// graph g of partials[(o * kMaxContrib + k) * grid + g * bpg + j], for graphs g < ngraphs
+cudaError_t launch_group_reduce(const ReducePlan& r, int ngraphs, int bpg, const int* out_row,
+                                const double* partials, double* out, cudaStream_t s);
 cudaError_t launch_tables(const TableArgs& t, cudaStream_t s);
 cudaError_t launch_cost_bound(const void* C, int f64, int n, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_norm(const void* psi, int dtype, int n, double* partials, int* nblocks, cudaStream_t s);

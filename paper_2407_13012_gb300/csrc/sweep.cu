@@ -7,22 +7,23 @@ namespace qaoa {
 namespace {
 
 
-// One layer's phase table in shared memory: float32 factors as they are, fixed-point factors
-// prepared for the limb multiply (fx::Factor, 24 bytes per entry).  Callers synchronise.
+// One layer's phase table (the sweeper's graph's) in shared memory: float32 factors as they
+// are, fixed-point factors prepared for the limb multiply (fx::Factor, 24 bytes per entry).
+// Callers synchronise.
 template <bool FX, class S>
 __device__ __forceinline__ void stage_table(S& s, const SweepArgs& a, void* dst, int nt) {
   using V = typename S::V;
-  const V* src = (const V*)a.phase_table + (long long)a.smem_table_layer * a.span;
+  const V* src = (const V*)s.ptab + (long long)a.smem_table_layer * s.pspan;
   if constexpr (FX) {
     fx::Factor* tf = (fx::Factor*)dst;
-    for (int k = threadIdx.x; k < a.span; k += nt) {
+    for (int k = threadIdx.x; k < s.pspan; k += nt) {
       const longlong2 e = __ldg((const longlong2*)src + k);
       tf[k] = fx::factor(e.x, e.y);
     }
     s.Tf = tf;
   } else {
     V* ts = (V*)dst;
-    for (int k = threadIdx.x; k < a.span; k += nt) ts[k] = __ldg(src + k);
+    for (int k = threadIdx.x; k < s.pspan; k += nt) ts[k] = __ldg(src + k);
     s.Ts = ts;
   }
   s.ts_layer = a.smem_table_layer;
@@ -45,6 +46,19 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
   for (int r = threadIdx.x; r < kLeanAcc * NW; r += CF::NT) wacc[r] = 0.0;
   S s(a, X, Cs, nullptr, nullptr);
   s.wacc = wacc;
+  // grouped sweeps: this block's graph and its share of the graph's tiles
+  int64_t t0 = blockIdx.x, tstep = gridDim.x;
+  if (a.gslot != nullptr) {
+    const GroupSlot& gsl = a.gslot[blockIdx.x / a.gbpg];
+    s.zoff = gsl.zoff;
+    s.ptab = gsl.phase_table;
+    s.pcmin = gsl.cmin;
+    s.pspan = gsl.span;
+    s.trig = gsl.trig;
+    s.dtab = gsl.d_table;
+    t0 = blockIdx.x % a.gbpg;
+    tstep = a.gbpg;
+  }
   if constexpr (FX) {  // every mixer's diagonal exp(-i beta (t - 2k)), k = 0..t, as prepared factors
     const int t = a.g.t;
     int m = 0;
@@ -52,7 +66,7 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
       const uint32_t op = a.ops[k];
       if ((op & 0xff) != OP_MIX) continue;
       if (threadIdx.x <= (uint32_t)t) {
-        const longlong2 e = __ldg((const longlong2*)a.d_table + ((long long)((op >> 16) & 0xff) * 14 + t) * 14 + threadIdx.x);
+        const longlong2 e = __ldg((const longlong2*)s.dtab + ((long long)((op >> 16) & 0xff) * 14 + t) * 14 + threadIdx.x);
         dpre[16 * m + threadIdx.x] = fx::factor(e.x, (op & F_SIGN) ? -e.y : e.y);
       }
       ++m;
@@ -69,7 +83,9 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
   }
   s.evalid = 1u << CF::B;
   if constexpr (FX && TWO) {
-    if (a.cmax_dev != nullptr) {
+    if (a.gslot != nullptr) {
+      s.lam_shift = a.gslot[blockIdx.x / a.gbpg].lam_shift;
+    } else if (a.cmax_dev != nullptr) {
       const unsigned long long b = *a.cmax_dev;
       const int ex = (int)((b >> 52) & 0x7FF);
       const int k = ex == 0 ? 0 : ex - 1023 + ((b & ((1ull << 52) - 1)) != 0 ? 1 : 0);
@@ -78,8 +94,8 @@ __global__ void __launch_bounds__(CF::NT, CF::MINB) lean_kernel(const __grid_con
   }
   __syncthreads();
   bool have = false;  // this tile's psi is in the staging area
-  for (int64_t tile = blockIdx.x; tile < a.g.tiles; tile += gridDim.x) {
-    const int64_t next = tile + gridDim.x < a.g.tiles ? tile + gridDim.x : -1;
+  for (int64_t tile = t0; tile < a.g.tiles; tile += tstep) {
+    const int64_t next = tile + tstep < a.g.tiles ? tile + tstep : -1;
     lean_tile<CF, FX, TWO, OPS, LAST, false>(s, a, tile, Cs, next, have);
     have = s.Ps != nullptr && next >= 0;
   }
@@ -149,6 +165,24 @@ __global__ void reduce_kernel(const __grid_constant__ ReducePlan r, const double
     __syncthreads();
   }
   if (threadIdx.x == 0) out[o] = sh[0] * r.scale[o];
+}
+
+// grouped sweeps: one warp per (graph, output), summing the graph's contributions and blocks
+// in a fixed order
+__global__ void group_reduce_kernel(const __grid_constant__ ReducePlan r, int ngraphs, int bpg,
+                                    const int* __restrict__ out_row, const double* __restrict__ partials,
+                                    double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (item >= (int64_t)ngraphs * r.nout) return;
+  const int g = (int)(item / r.nout), o = (int)(item % r.nout);
+  double v = 0.0;
+  for (int i = lane; i < r.ncontrib[o] * bpg; i += 32) {
+    const int k = i / bpg, j = i - k * bpg;
+    v += partials[((int64_t)o * kMaxContrib + k) * r.grid + (int64_t)g * bpg + j];
+  }
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  if (lane == 0) out[(int64_t)out_row[g] * r.nout + o] = v * r.scale[o];
 }
 
 // integer-cost phase tables exp(-i gamma_l c), c = cmin + k; then (fixed point) the
@@ -471,6 +505,16 @@ cudaError_t launch_expect(int dtype, const void* psi, const void* C, int cost_dt
 cudaError_t launch_reduce(const ReducePlan& r, const double* partials, double* out, cudaStream_t s) {
   note_launch(3, s, true);
   reduce_kernel<<<r.nout, 256, 0, s>>>(r, partials, out);
+  note_launch(3, s, false);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_reduce(const ReducePlan& r, int ngraphs, int bpg, const int* out_row,
+                                const double* partials, double* out, cudaStream_t s) {
+  const int64_t items = (int64_t)ngraphs * r.nout;
+  if (items == 0) return cudaSuccess;
+  note_launch(3, s, true);
+  group_reduce_kernel<<<(unsigned)((items + 7) / 8), 256, 0, s>>>(r, ngraphs, bpg, out_row, partials, out);
   note_launch(3, s, false);
   return cudaGetLastError();
 }

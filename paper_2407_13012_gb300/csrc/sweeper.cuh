@@ -160,14 +160,14 @@ __device__ __forceinline__ longlong2 turn_phase(unsigned long long t, const long
 
 // per-layer angle terms: kernel parameters, or device memory ([g2pi p | cos p | sin p],
 // written by angle_prep_kernel) when the angles live on the device
-__device__ __forceinline__ double arg_g2pi(const SweepArgs& a, int l) {
-  return a.dev_trig ? a.dev_trig[l] : a.g2pi[l];
+__device__ __forceinline__ double arg_g2pi(const SweepArgs& a, const double* trig, int l) {
+  return trig ? trig[l] : a.g2pi[l];
 }
-__device__ __forceinline__ double arg_cosb(const SweepArgs& a, int l) {
-  return a.dev_trig ? a.dev_trig[a.np + l] : a.cosb[l];
+__device__ __forceinline__ double arg_cosb(const SweepArgs& a, const double* trig, int l) {
+  return trig ? trig[a.np + l] : a.cosb[l];
 }
-__device__ __forceinline__ double arg_sinb(const SweepArgs& a, int l) {
-  return a.dev_trig ? a.dev_trig[2 * a.np + l] : a.sinb[l];
+__device__ __forceinline__ double arg_sinb(const SweepArgs& a, const double* trig, int l) {
+  return trig ? trig[2 * a.np + l] : a.sinb[l];
 }
 
 __device__ __forceinline__ double cost_f(const void* Cs, bool f64, uint32_t i) {
@@ -199,11 +199,18 @@ struct Sweeper {
   uint32_t evalid;
   uint64_t base;
   const uint32_t tid;
+  // the graph's data: a's, or one graph's of a grouped sweep (lean kernels)
+  int64_t zoff;          // element offset of psi, lambda and C
+  const void* ptab;      // phase tables
+  int64_t pcmin, pspan;  // their integer cost range
+  const double* trig;    // per-layer angle terms in device memory, or nullptr (kernel parameters)
+  const void* dtab;      // fixed point: mixer diagonals
 
   __device__ Sweeper(const SweepArgs& a_, V* X_, void* Cs_, double* blk_, double* red_)
       : a(a_), X(X_), Cs(Cs_), Ts(nullptr), Tf(nullptr), Ds(nullptr), ts_layer(-1), blk(blk_), red(red_), cur(0),
         lam_shift(0),
-        in_shift(0), evalid(0), base(0), tid(threadIdx.x) {}
+        in_shift(0), evalid(0), base(0), tid(threadIdx.x), zoff(0), ptab(a_.phase_table), pcmin(a_.cmin),
+        pspan(a_.span), trig(a_.dev_trig), dtab(a_.d_table) {}
 
   __device__ __forceinline__ uint32_t idx(int r) const { return CF::idx(cur, tid, r); }
 
@@ -341,8 +348,8 @@ struct Sweeper {
   // phase factor of cost c computed directly (out of line: only costs outside the table and
   // float costs take it)
   __device__ __forceinline__ V phase_direct(int layer, double c) const {
-    if constexpr (FX) return phase_fx_direct(arg_g2pi(a, layer) * c, (const longlong2*)a.turn_table);
-    else return phase_f32_direct(arg_g2pi(a, layer) * c);
+    if constexpr (FX) return phase_fx_direct(arg_g2pi(a, trig, layer) * c, (const longlong2*)a.turn_table);
+    else return phase_f32_direct(arg_g2pi(a, trig, layer) * c);
   }
   // psi (or lambda) *= exp(-i s gamma_l C): table lookups first, the rest out of line
   template <bool INV>
@@ -354,8 +361,8 @@ struct Sweeper {
       for (int r = 0; r < R; ++r) {
         // table index in 32-bit arithmetic (the host keeps table bounds inside int32, so an
         // entry outside [cmin, cmax] can never wrap into the table)
-        const uint32_t k = (uint32_t)cost_i(Cs, idx(r)) - (uint32_t)a.cmin;
-        if (k < (uint32_t)a.span) {
+        const uint32_t k = (uint32_t)cost_i(Cs, idx(r)) - (uint32_t)pcmin;
+        if (k < (uint32_t)pspan) {
           if constexpr (FX) {
             const fx::C64 o = fx::cmul_factor<false, INV>(u[r].x, u[r].y, Tf[k], 0);
             u[r] = make_longlong2(o.x, o.y);
@@ -364,14 +371,14 @@ struct Sweeper {
           miss |= 1u << r;
         }
       }
-    } else if (!f64 && a.phase_table != nullptr) {
-      const V* tab = (layer == ts_layer && Ts != nullptr) ? Ts : (const V*)a.phase_table + (long long)layer * a.span;
+    } else if (!f64 && ptab != nullptr) {
+      const V* tab = (layer == ts_layer && Ts != nullptr) ? Ts : (const V*)ptab + (long long)layer * pspan;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         // table index in 32-bit arithmetic (the host keeps table bounds inside int32, so an
         // entry outside [cmin, cmax] can never wrap into the table)
-        const uint32_t k = (uint32_t)cost_i(Cs, idx(r)) - (uint32_t)a.cmin;
-        if (k < (uint32_t)a.span) {
+        const uint32_t k = (uint32_t)cost_i(Cs, idx(r)) - (uint32_t)pcmin;
+        if (k < (uint32_t)pspan) {
           V e = tab[k];
           if constexpr (INV) e.y = -e.y;
           u[r] = vmul(u[r], e);
@@ -403,8 +410,8 @@ struct Sweeper {
       for (int r = 0; r < R; ++r) {
         // table index in 32-bit arithmetic (the host keeps table bounds inside int32, so an
         // entry outside [cmin, cmax] can never wrap into the table)
-        const uint32_t k = (uint32_t)cost_i(Cs, idx(r)) - (uint32_t)a.cmin;
-        if (k < (uint32_t)a.span) {
+        const uint32_t k = (uint32_t)cost_i(Cs, idx(r)) - (uint32_t)pcmin;
+        if (k < (uint32_t)pspan) {
           if constexpr (FX) {
             const fx::Factor& f = Tf[k];
             const fx::C64 o = fx::cmul_factor<false, INV>(v[r].x, v[r].y, f, 0);
@@ -416,14 +423,14 @@ struct Sweeper {
           miss |= 1u << r;
         }
       }
-    } else if (!f64 && a.phase_table != nullptr) {
-      const V* tab = (layer == ts_layer && Ts != nullptr) ? Ts : (const V*)a.phase_table + (long long)layer * a.span;
+    } else if (!f64 && ptab != nullptr) {
+      const V* tab = (layer == ts_layer && Ts != nullptr) ? Ts : (const V*)ptab + (long long)layer * pspan;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         // table index in 32-bit arithmetic (the host keeps table bounds inside int32, so an
         // entry outside [cmin, cmax] can never wrap into the table)
-        const uint32_t k = (uint32_t)cost_i(Cs, idx(r)) - (uint32_t)a.cmin;
-        if (k < (uint32_t)a.span) {
+        const uint32_t k = (uint32_t)cost_i(Cs, idx(r)) - (uint32_t)pcmin;
+        if (k < (uint32_t)pspan) {
           V e = tab[k];
           if constexpr (INV) e.y = -e.y;
           v[r] = vmul(v[r], e);
@@ -517,7 +524,7 @@ struct Sweeper {
   }
 
   __device__ __forceinline__ void mix_f32(int layer, bool inverse, bool on_psi, bool on_lam, int xacc) {
-    const double cbd = arg_cosb(a, layer), sbd = inverse ? -arg_sinb(a, layer) : arg_sinb(a, layer);
+    const double cbd = arg_cosb(a, trig, layer), sbd = inverse ? -arg_sinb(a, trig, layer) : arg_sinb(a, trig, layer);
     const bool tanf = fabs(cbd) >= fabs(sbd);
     const float tu = tanf ? (float)(sbd / cbd) : (float)(cbd / sbd);
     const float m = tanf ? (float)cbd : (float)sbd;
@@ -630,7 +637,7 @@ struct Sweeper {
   // (sign applied); the caller synchronises before and after
   __device__ __forceinline__ void load_diagonal(int layer, bool inverse, int t) {
     if (tid <= (uint32_t)t) {
-      const longlong2 e = __ldg((const longlong2*)a.d_table + ((long long)layer * 14 + t) * 14 + tid);
+      const longlong2 e = __ldg((const longlong2*)dtab + ((long long)layer * 14 + t) * 14 + tid);
       Ds[tid] = fx::factor(e.x, inverse ? -e.y : e.y);
     }
   }
@@ -1130,8 +1137,8 @@ struct Lean : Sweeper<CF, FX, TWO> {
   template <int L>
   __device__ __forceinline__ void f32_mixer(int layer, bool inverse, int xacc) {
     if constexpr (!FX) {
-      const double cbd = arg_cosb(this->a, layer);
-      const double sbd = inverse ? -arg_sinb(this->a, layer) : arg_sinb(this->a, layer);
+      const double cbd = arg_cosb(this->a, this->trig, layer);
+      const double sbd = inverse ? -arg_sinb(this->a, this->trig, layer) : arg_sinb(this->a, this->trig, layer);
       const bool tanf = fabs(cbd) >= fabs(sbd);
       const float tu = tanf ? (float)(sbd / cbd) : (float)(cbd / sbd);
       const float m = tanf ? (float)cbd : (float)sbd;
@@ -1229,7 +1236,7 @@ __device__ __forceinline__ void lean_tile(Lean<CF, FX, TWO>& s, const SweepArgs&
     for (uint32_t ch = tid; ch < nch; ch += CF::NT) {
       const uint32_t i = ch * per;
       const uint64_t z = local_to_z(g, base, i);
-      cp_async16((char*)Cs + (size_t)phys_cost(i, cf64) * (cf64 ? 8 : 4), (const char*)a.C + z * (cf64 ? 8 : 4));
+      cp_async16((char*)Cs + (size_t)phys_cost(i, cf64) * (cf64 ? 8 : 4), (const char*)a.C + (s.zoff + z) * (cf64 ? 8 : 4));
     }
     if (stage) cp_async_commit();
   }
@@ -1242,16 +1249,16 @@ __device__ __forceinline__ void lean_tile(Lean<CF, FX, TWO>& s, const SweepArgs&
   for (int r = 0; r < R; ++r) {
     const uint64_t z = z0 + (uint64_t)r * zs;
     const uint32_t ps = tb0 + ((uint32_t)r << CF::lo(0));
-    if constexpr (FX) v[r] = init ? make_longlong2(a.init_fx, 0) : staged ? s.Ps[ps] : ld_state<COHERENT>((const V*)a.psi + z);
-    else v[r] = init ? make_float2(a.init_f32, 0.f) : staged ? s.Ps[ps] : ld_state<COHERENT>((const V*)a.psi + z);
-    if constexpr (TWO) w[r] = ld_lam ? ld_state<COHERENT>((const V*)a.lam + z) : V{};
+    if constexpr (FX) v[r] = init ? make_longlong2(a.init_fx, 0) : staged ? s.Ps[ps] : ld_state<COHERENT>((const V*)a.psi + s.zoff + z);
+    else v[r] = init ? make_float2(a.init_f32, 0.f) : staged ? s.Ps[ps] : ld_state<COHERENT>((const V*)a.psi + s.zoff + z);
+    if constexpr (TWO) w[r] = ld_lam ? ld_state<COHERENT>((const V*)a.lam + s.zoff + z) : V{};
   }
   if (stage && next >= 0) {
     const uint64_t zn = local_to_z(g, tile_base(g, next), tb0);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       V* dst = s.Ps + tb0 + ((uint32_t)r << CF::lo(0));
-      const V* src = (const V*)a.psi + zn + (uint64_t)r * zs;
+      const V* src = (const V*)a.psi + s.zoff + zn + (uint64_t)r * zs;
       if constexpr (sizeof(V) == 16) cp_async16(dst, src);
       else cp_async8(dst, src);
     }
@@ -1270,7 +1277,7 @@ __device__ __forceinline__ void lean_tile(Lean<CF, FX, TWO>& s, const SweepArgs&
   const uint64_t z1 = local_to_z(g, base, tb0);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    const uint64_t z = z1 + (uint64_t)r * zs;
+    const uint64_t z = s.zoff + z1 + (uint64_t)r * zs;
     if constexpr (FX) {
       if (st_fmt == 0) ((V*)a.psi)[z] = v[r];
       else if (st_fmt == 1)

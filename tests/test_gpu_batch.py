@@ -61,6 +61,21 @@ def test_batch_large_graphs_vs_oracle(dtype):
     check_rows(run(insts, dtype, np.zeros(q.MAX_N + 1)), insts, dtype, p)
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_batch_grouped_buckets_vs_oracle(dtype):
+    """Several graphs per size at n = 16..19 (the sizes whose sweeps run grouped, one launch
+    for all graphs of a size, each graph with its own weights, cost range and angles), mixed
+    with small graphs for the persistent kernel; every row against the oracle."""
+    p = 3
+    insts = []
+    for n_lo, count, seed in ((16, 24, 31), (18, 12, 32)):
+        insts += [x for x in synth.batch_instances(count, seed, n_lo=n_lo, n_hi=n_lo + 1, p=p)]
+    insts += synth.batch_instances(6, 33, n_lo=5, n_hi=12, p=p)
+    sizes = [x[0] for x in insts]
+    assert min(sizes.count(n) for n in (16, 17, 18, 19)) >= 2
+    check_rows(run(insts, dtype), insts, dtype, p)
+
+
 def test_batch_degenerate_graphs_and_depths():
     """n = 1 and edgeless graphs (C = 0: E = 0, zero gradient), and p = 1 and 6."""
     for p in (1, 6):
