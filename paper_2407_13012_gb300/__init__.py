@@ -144,9 +144,16 @@ class Graph:
         return len(self.edges)
 
     def as_struct(self) -> GraphT:
-        uv = self.edges.ctypes.data_as(ct.POINTER(ct.c_int32))
-        w = self.weights.ctypes.data_as(ct.POINTER(ct.c_double)) if self.weights is not None else None
-        return GraphT(self.n, self.m, uv, w, WEIGHT_INT if self.integer else WEIGHT_F64)
+        """The C descriptor.  It points into this graph's edge and weight arrays, so it is kept
+        (with references to those arrays) until one of the fields is replaced."""
+        key = (self.edges, self.weights, self.n, self.integer)
+        c = self.__dict__.get("_struct")
+        if c is None or any(a is not b for a, b in zip(c[0][:2], key[:2])) or c[0][2:] != key[2:]:
+            uv = self.edges.ctypes.data_as(ct.POINTER(ct.c_int32))
+            w = self.weights.ctypes.data_as(ct.POINTER(ct.c_double)) if self.weights is not None else None
+            c = (key, GraphT(self.n, self.m, uv, w, WEIGHT_INT if self.integer else WEIGHT_F64))
+            self.__dict__["_struct"] = c
+        return c[1]
 
     def check(self) -> tuple[int, int]:
         """Host-side validation; returns integer bounds (cmin, cmax) on C(z)."""

@@ -508,13 +508,16 @@ int qaoa_graph_check(const qaoa_graph_t* g, int64_t* cmin, int64_t* cmax) {
   if (g->m > 0 && g->uv == nullptr) return QAOA_ERR_INVALID_ARG;
   if (g->weight_kind != QAOA_WEIGHT_INT && g->weight_kind != QAOA_WEIGHT_F64) return QAOA_ERR_INVALID_ARG;
   if (g->m > (int64_t)g->n * (g->n - 1) / 2) return QAOA_ERR_INVALID_ARG;
-  std::set<std::pair<int, int>> seen;
+  static_assert(QAOA_MAX_N <= 32, "adjacency rows are 32-bit masks");
+  uint32_t adj[QAOA_MAX_N] = {};  // edges seen so far, one bit per neighbour
   double sum_abs = 0.0;
   int64_t neg = 0, pos = 0;
   for (int64_t e = 0; e < g->m; ++e) {
     const int u = g->uv[2 * e], v = g->uv[2 * e + 1];
     if (u < 0 || v < 0 || u >= g->n || v >= g->n || u == v) return QAOA_ERR_INVALID_ARG;
-    if (!seen.insert({std::min(u, v), std::max(u, v)}).second) return QAOA_ERR_INVALID_ARG;
+    if (adj[u] & (1u << v)) return QAOA_ERR_INVALID_ARG;  // a repeated edge (either orientation)
+    adj[u] |= 1u << v;
+    adj[v] |= 1u << u;
     const double w = g->w ? g->w[e] : 1.0;
     if (!std::isfinite(w)) return QAOA_ERR_INVALID_ARG;
     sum_abs += std::fabs(w);
