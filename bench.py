@@ -808,9 +808,10 @@ def run_xy(a):
             "config": {"workload": f"balanced-cut QAOA on F_k: n={n} {'random 3-regular' if fam == 'reg3' else fam}, "
                                    f"k={k} ({D} amplitudes), p={a.p}, ring XY mixer, {a.dtype} subspace state; "
                                    f"step = Dicke start + p layers + <C>", "n": n, "k": k, "p": a.p,
-                       "arithmetic": ("float64 pairs in memory; cost unitary and window gate passes in int64 fixed "
-                                      "point with a per-tile scale (value = integer x 2^-(56 - E), components below "
-                                      "2^E); closing pair and <C> in float64") if a.dtype == "c128" else
+                       "arithmetic": ("float64 pairs in memory; cost unitary and window gate passes (forward and "
+                                      "adjoint) in int64 fixed point with a per-tile scale (value = integer x "
+                                      "2^-(56 - E), components below 2^E); closing pair and <C> in float64")
+                                     if a.dtype == "c128" else
                                      "float32 state and rotations; <C> in float32 chunks summed in float64",
                        "state_dtype": a.dtype, "l2": "state larger than L2, no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -450,8 +450,9 @@ int qaoa_batch_autotune(int dtype, int p, int n_lo, int n_hi, int graphs_per_n, 
  *    mod 2 pi).  complex128 states are float64 in memory; the forward layers
  *    gather tiles of up to 9 consecutive qubits into int64 fixed point with a
  *    scale of their own (value = integer x 2^-(56 - E), every component of the
- *    tile below 2^E, any state norm) and round each rotated part once; the
- *    closing pair, the adjoint pass and the reductions run in float64.
+ *    tile below 2^E, any state norm) and round each rotated part once, the
+ *    adjoint pass likewise for psi and lambda (gradient terms as exact 128-bit
+ *    products); the closing pair and the final reductions run in float64.
  * Limits: 1 <= n <= QAOA_XY_MAX_N, 0 <= k <= n, m <= QAOA_XY_MAX_EDGES; the
  * caller sizes every buffer with qaoa_xy_dim().  Graphs are validated as in
  * qaoa_graph_check() except for these limits.

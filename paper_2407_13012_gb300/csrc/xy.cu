@@ -365,12 +365,13 @@ __global__ void __launch_bounds__(kXYThreads)
 // every column (the pairs of one gate are disjoint), and the tile is written back.  Backwards (TWO: psi and lambda) the gates run in reverse order; before
 // undoing a gate the owner of each pair adds Im(conj(lambda_z) psi_z' + conj(lambda_z') psi_z),
 // the gate's term at the state right after it.  All gates of a window share the layer's beta,
-// so one partial per block suffices.  Forward complex128 tiles hold the state as int64 fixed
+// so one partial per block suffices.  complex128 tiles hold psi (and lambda) as int64 fixed
 // point and rotate with 32-bit limb products (fixedpoint.cuh): GB300's float64 pipe would
-// otherwise bound the pass.  The scale is the tile's own: with every component below 2^E,
-// value = integer x 2^-(56 - E).  The gates keep each column's 2-norm, which is below
-// sqrt(2 rows) 2^E < 2^(E + 4) for rows <= 126, so every value stays below 2^(E + 4), i.e.
-// below 2^60 integer units, as the limb products require (any state norm is accepted).
+// otherwise bound the pass.  Each buffer's scale is the tile's own: with every component
+// below 2^E, value = integer x 2^-(56 - E).  The gates keep each column's 2-norm, which is
+// below sqrt(2 rows) 2^E < 2^(E + 4) for rows <= 126, so every value stays below 2^(E + 4),
+// i.e. below 2^60 integer units, as the limb products require (any norm is accepted); the
+// gradient terms are exact 128-bit products, converted to float64 once per tile.
 static_assert(xyw::kMaxN == QAOA_XY_MAX_N, "window tables sized for QAOA_XY_MAX_N");
 static_assert(xyw::kMaxRows <= 128, "tile scale headroom assumes columns of <= 128 rows");
 
@@ -429,12 +430,30 @@ __device__ __forceinline__ T xy_cmul(T x, T f) {
   return y;
 }
 
+// float64 components of a fixed-point tile slot (raw bits while the tile's scale is open)
+__device__ __forceinline__ longlong2 xy_fx_load(const longlong2 raw, int fs) {
+  return make_longlong2(fx::from_double(fx::bits_to_double((unsigned long long)raw.x), fs),
+                        fx::from_double(fx::bits_to_double((unsigned long long)raw.y), fs));
+}
+__device__ __forceinline__ unsigned xy_exp_bits(double2 v) {
+  const unsigned long long bx = fx::double_to_bits(v.x), by = fx::double_to_bits(v.y);
+  return max((unsigned)(bx >> 52) & 0x7FFu, (unsigned)(by >> 52) & 0x7FFu);
+}
+// x * f (conj(f) when CONJ) for a fixed-point x and a unit float64 factor f, as Q62 limbs
+template <bool CONJ>
+__device__ __forceinline__ longlong2 xy_fx_phase(longlong2 x, double2 f) {
+  const long long fre = xy_q62(f.x), fim = xy_q62(CONJ ? -f.y : f.y);
+  const fx::Limbs fr = fx::split(fre), fi = fx::split(fim), nfi = fx::split(-fim);
+  const fx::Limbs xr = fx::split(x.x), xi = fx::split(x.y);
+  return make_longlong2(fx::dot2_q62(xr, fr, xi, nfi, 0), fx::dot2_q62(xr, fi, xi, fr, 0));
+}
+
 template <typename T, bool TWO, bool PH>
 __global__ void __launch_bounds__(kXYThreads)
     xy_window_kernel(const __grid_constant__ xyw::Window W, T* __restrict__ psi, T* __restrict__ lam,
                      typename Real<T>::type cb, typename Real<T>::type sb, double* __restrict__ part,
                      const __grid_constant__ XYPhaseArgs<T> ph) {
-  constexpr bool FXR = std::is_same<T, double2>::value && !TWO;  // fixed-point forward tiles
+  constexpr bool FXR = std::is_same<T, double2>::value;  // complex128: fixed-point tiles
   using S = typename std::conditional<FXR, longlong2, T>::type;
   __shared__ unsigned long long B[xyw::kBN][xyw::kBN];
   __shared__ unsigned long long rowoff[xyw::kMaxRows];
@@ -443,7 +462,7 @@ __global__ void __launch_bounds__(kXYThreads)
   __shared__ unsigned char pr0[xyw::kMaxGates][xyw::kMaxPairs], pr1[xyw::kMaxGates][xyw::kMaxPairs];
   __shared__ int npr[xyw::kMaxGates];
   __shared__ double red[kXYThreads / 32];
-  __shared__ unsigned tile_ex;  // fixed-point tiles: largest biased float64 exponent of the tile
+  __shared__ unsigned tile_ex[2];  // fixed-point tiles: largest biased float64 exponent of psi, lambda
   extern __shared__ __align__(16) unsigned char xy_win_smem[];
   S* tp = (S*)xy_win_smem;     // psi tile
   S* tl = tp + W.tile_elems;   // lambda tile (TWO)
@@ -491,7 +510,7 @@ __global__ void __launch_bounds__(kXYThreads)
       cur = ci;
     }
     for (int c = tid; c < ncol; c += kXYThreads) colbase[c] = xyw::col_base(W, C, col0 + c, B);
-    if (FXR && tid == 0) tile_ex = 0;
+    if (FXR && tid == 0) tile_ex[0] = tile_ex[1] = 0;
     __syncthreads();
     // element e of the tile: column-major when a column's rows are consecutive ranks (len = 1),
     // otherwise row-major, so consecutive threads touch consecutive ranks
@@ -499,16 +518,20 @@ __global__ void __launch_bounds__(kXYThreads)
     const unsigned inner = cm ? (unsigned)rows : (unsigned)ncol;  // < 2^16
     const unsigned mg = xyw::div_magic(inner);
     const int ne = rows * ncol;
-    unsigned ex_max = 0;
+    unsigned exp_psi = 0, exp_lam = 0;
     for (int e = tid; e < ne; e += kXYThreads) {
       const unsigned o = xyw::div_small((unsigned)e, mg), i = (unsigned)e - o * inner;
       const int r = cm ? (int)i : (int)o, c = cm ? (int)o : (int)i;
       const unsigned long long rk = rowoff[r] + colbase[c];
       const T x = psi[rk];
-      if constexpr (FXR) {  // raw bits for now; the exponents give the tile's scale
-        const unsigned long long bx = fx::double_to_bits(x.x), by = fx::double_to_bits(x.y);
-        ex_max = max(ex_max, max((unsigned)(bx >> 52) & 0x7FFu, (unsigned)(by >> 52) & 0x7FFu));
-        tp[e] = make_longlong2((long long)bx, (long long)by);
+      if constexpr (FXR) {  // raw bits for now; the exponents give the tile's scales
+        exp_psi = max(exp_psi, xy_exp_bits(x));
+        tp[e] = make_longlong2((long long)fx::double_to_bits(x.x), (long long)fx::double_to_bits(x.y));
+        if constexpr (TWO) {
+          const T l = lam[rk];
+          exp_lam = max(exp_lam, xy_exp_bits(l));
+          tl[e] = make_longlong2((long long)fx::double_to_bits(l.x), (long long)fx::double_to_bits(l.y));
+        }
       } else {
         T v = x;
         if constexpr (PH && !TWO) {
@@ -519,33 +542,34 @@ __global__ void __launch_bounds__(kXYThreads)
         if constexpr (TWO) tl[e] = lam[rk];
       }
     }
-    int fs = 0;  // fixed-point tiles: value = integer x 2^-fs
+    int fs = 0, fl = 0;  // fixed-point tiles: psi value = integer x 2^-fs, lambda 2^-fl
     if constexpr (FXR) {
-      ex_max = __reduce_max_sync(0xffffffffu, ex_max);
-      if (lane == 0) atomicMax(&tile_ex, ex_max);
+      exp_psi = __reduce_max_sync(0xffffffffu, exp_psi);
+      if (lane == 0) atomicMax(&tile_ex[0], exp_psi);
+      if constexpr (TWO) {
+        exp_lam = __reduce_max_sync(0xffffffffu, exp_lam);
+        if (lane == 0) atomicMax(&tile_ex[1], exp_lam);
+      }
       __syncthreads();
-      fs = 56 - ((int)tile_ex - 1022);  // every component is below 2^(tile_ex - 1022)
+      fs = 56 - ((int)tile_ex[0] - 1022);  // every component is below 2^(tile_ex - 1022)
+      fl = 56 - ((int)tile_ex[1] - 1022);
       for (int e = tid; e < ne; e += kXYThreads) {  // the slots this thread loaded
-        const longlong2 raw = tp[e];
-        longlong2 X = make_longlong2(fx::from_double(fx::bits_to_double((unsigned long long)raw.x), fs),
-                                     fx::from_double(fx::bits_to_double((unsigned long long)raw.y), fs));
-        if constexpr (PH) {  // exp(-i gamma c) as Q62 limbs; a unit factor keeps the bound
+        longlong2 X = xy_fx_load(tp[e], fs);
+        if constexpr (PH && !TWO) {  // the layer's cost unitary; a unit factor keeps the bound
           const unsigned o = xyw::div_small((unsigned)e, mg), i = (unsigned)e - o * inner;
           const int r = cm ? (int)i : (int)o, c = cm ? (int)o : (int)i;
           double cv;
-          const T f = xy_phase_factor(ph, rowoff[r] + colbase[c], cv);
-          const long long fre = xy_q62(f.x), fim = xy_q62(f.y);
-          const fx::Limbs fr = fx::split(fre), fi = fx::split(fim), nfi = fx::split(-fim);
-          const fx::Limbs xr = fx::split(X.x), xi = fx::split(X.y);
-          X = make_longlong2(fx::dot2_q62(xr, fr, xi, nfi, 0), fx::dot2_q62(xr, fi, xi, fr, 0));
+          X = xy_fx_phase<false>(X, xy_phase_factor(ph, rowoff[r] + colbase[c], cv));
         }
         tp[e] = X;
+        if constexpr (TWO) tl[e] = xy_fx_load(tl[e], fl);
       }
     }
     __syncthreads();
     // gates one after another, each gate's (pair, column) items spread over the block:
     // consecutive threads take consecutive columns (row-major tiles) or consecutive pairs of
     // one column (column-major tiles), so shared-memory accesses stay conflict-free
+    fx::i128 tacc = 0;  // fixed point: this thread's gate terms of the tile, x 2^-(fs + fl - 4)
     for (int gi = 0; gi < W.ngates; ++gi) {
       const int g = TWO ? W.ngates - 1 - gi : gi;
       const int np = npr[g];
@@ -559,29 +583,46 @@ __global__ void __launch_bounds__(kXYThreads)
         const int s0 = cm ? c * rows + r0 : r0 * ncol + c;
         const int s1 = cm ? c * rows + r1 : r1 * ncol + c;
         S x = tp[s0], y = tp[s1];
-        if constexpr (FXR) {
-          xy_rotate_fx(x, y, qc, qs, qns);
-        } else {
-          if constexpr (TWO) {
-            T lx = tl[s0], ly = tl[s1];
+        if constexpr (TWO) {
+          S lx = tl[s0], ly = tl[s1];
+          if constexpr (FXR) {  // exact products (each below 2^121), summed with 4 bits to spare
+            tacc += (fx::dot2_exact(lx.x, y.y, lx.y, y.x) + fx::dot2_exact(ly.x, x.y, ly.y, x.x)) >> 4;
+            xy_rotate_fx(lx, ly, qc, qs, qns);
+          } else {
             acc += (double)lx.x * y.y - (double)lx.y * y.x + (double)ly.x * x.y - (double)ly.y * x.x;
             xy_rotate(lx, ly, cb, sb);
-            tl[s0] = lx;
-            tl[s1] = ly;
           }
-          xy_rotate(x, y, cb, sb);
+          tl[s0] = lx;
+          tl[s1] = ly;
         }
+        if constexpr (FXR) xy_rotate_fx(x, y, qc, qs, qns);
+        else xy_rotate(x, y, cb, sb);
         tp[s0] = x;
         tp[s1] = y;
       }
       __syncthreads();
     }
+    if constexpr (FXR && TWO) acc += fx::i128_to_double(tacc, fs + fl - 4);
+    fx::i128 cacc_i = 0;  // fixed point, integer costs: sum of c (conj(lambda) psi products >> 32)
     for (int e = tid; e < ne; e += kXYThreads) {
       const unsigned o = xyw::div_small((unsigned)e, mg), i = (unsigned)e - o * inner;
       const int r = cm ? (int)i : (int)o, c = cm ? (int)o : (int)i;
       const unsigned long long rk = rowoff[r] + colbase[c];
       if constexpr (FXR) {
-        const longlong2 X = tp[e];
+        longlong2 X = tp[e];
+        if constexpr (TWO) {
+          longlong2 L = tl[e];
+          if constexpr (PH) {  // the gamma term at the state right after the cost unitary, then undo it
+            double cv;
+            const T f = xy_phase_factor(ph, rk, cv);
+            const fx::i128 pr = fx::dot2_exact(L.x, X.y, L.y, X.x);  // Im(conj(lambda) psi)
+            if (ph.cost_dtype == QAOA_COST_I32) cacc_i += (pr >> 32) * (long long)cv;
+            else cacc += cv * fx::i128_to_double(pr, fs + fl);
+            X = xy_fx_phase<true>(X, f);
+            L = xy_fx_phase<true>(L, f);
+          }
+          lam[rk] = make_double2(fx::to_double(L.x, fl), fx::to_double(L.y, fl));
+        }
         psi[rk] = make_double2(fx::to_double(X.x, fs), fx::to_double(X.y, fs));
       } else if constexpr (TWO) {
         T x = tp[e], l = tl[e];
@@ -599,6 +640,7 @@ __global__ void __launch_bounds__(kXYThreads)
         psi[rk] = tp[e];
       }
     }
+    if constexpr (FXR && TWO && PH) cacc += fx::i128_to_double(cacc_i, fs + fl - 32);
   }
   if constexpr (TWO) {
     const double t = block_sum(acc, red);
