@@ -13,7 +13,7 @@ shard); timing is the max over ranks.  ``--impl reference`` times the FP64 CPU
 oracle on a bounded sample of the same workload on the host cores.
 
 Outside the timed step the line also carries: ``gradient`` (gradient evaluations per
-second), ``batched`` (4096 small graphs in one persistent launch against one at a time),
+second), ``batched`` (4096 small graphs in one batched call against one at a time),
 ``time_to_ratio`` (time for 256 graphs to reach an approximation ratio: batched or plain
 optimiser, from the linear ramp or the learned proposer) and ``cpu_baseline`` (the oracle
 on one core and on all host cores).  ``--workload batched|xy|ttr`` prints one of those
@@ -340,7 +340,7 @@ BATCH_WORKLOAD = ("{g} graphs, n ~ U{{8..20}}, half random 3-regular / half G(n,
 
 
 def measure_batched(q, dev, dtype: str, count: int, reps: int = 3, autotune: bool = True):
-    """The batched workload: one persistent launch over all graphs against the plain path
+    """The batched workload: one batched call over all graphs against the plain path
     (cost vector + gradient per graph, one graph at a time), both timed with CUDA events."""
     import torch
     import synth
@@ -384,7 +384,7 @@ def measure_batched(q, dev, dtype: str, count: int, reps: int = 3, autotune: boo
             "graph_grads_per_s": count / (batched_ms / 1e3), "batched_ms": batched_ms, "plain_ms": plain_ms,
             "speedup": plain_ms / batched_ms, "max_abs_diff_vs_plain": agree,
             "tiles": {int(n): int(tiles[n]) for n in range(8, 21)} if tiles is not None else "library default",
-            "launches": "1 prep + 1 persistent per tile size",
+            "launches": "1 prep + grouped sweeps per size (n >= 16 c128, n >= 18 c64) + 1 persistent per tile size",
             "timing": "CUDA events, median of %d batched runs; plain: one run over all graphs" % reps}
 
 

@@ -387,11 +387,14 @@ int qaoa_timing_read(double* ms, int64_t* launches, double* bytes, int64_t* drop
  * what qaoa_gradient computes from |+>: [E, <psi|psi>, dE/dgamma_1..p,
  * dE/dbeta_1..p] (Eq. 1, Sec. IV-D).  Integer weights give int32 costs and
  * phase tables; if any graph has float weights, every graph gets float64 costs
- * (weights summed in edge order) and directly computed phases.
- * All graphs run in one persistent launch per tile size: each CTA takes the
- * next graph (largest n first) and runs its whole plan, so there is one launch
- * for the batch instead of ~2p(k-1)+3 per graph.  The paper evaluates graphs
- * one at a time; batching is this library's addition.
+ * (the weights in one common fixed point, summed exactly and rounded once, as
+ * qaoa_cost_vector does) and directly computed phases.
+ * Graphs on 2^12 tiles whose size has an all-lean one-graph plan (n >= 16
+ * complex128, n >= 18 complex64) run grouped: each sweep of that plan is one
+ * launch for all graphs of the size.  The rest run in one persistent launch per
+ * tile size: each CTA takes the next graph (largest n first) and runs its whole
+ * plan.  The paper evaluates graphs one at a time; batching is this library's
+ * addition.
  *  graphs      ngraphs host descriptors (n <= QAOA_BATCH_MAX_N,
  *              m <= QAOA_BATCH_MAX_EDGES); checked as by qaoa_graph_check.
  *  angles      host, ngraphs x 2p doubles: row i = [gamma_1..p | beta_1..p]

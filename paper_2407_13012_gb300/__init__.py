@@ -500,7 +500,7 @@ def _tiles_arg(tiles):
 
 
 def batch_gradient(graphs, angles, dtype: str = "c128", tiles=None, device="cuda"):
-    """Batched S7 for many small graphs in one persistent launch.
+    """Batched S7 for many small graphs (grouped sweeps per size, one persistent launch for the rest).
 
     graphs: sequence of Graph; angles: (ngraphs, 2p) host array, row i = [gamma | beta] of
     graph i.  Returns a (ngraphs, 2p + 2) float64 device tensor, row i = [E, norm,
