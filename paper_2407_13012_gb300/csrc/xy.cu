@@ -389,11 +389,12 @@ __device__ __forceinline__ void xy_rotate(T& x, T& y, typename Real<T>::type cb,
 // Q62 of |d| <= 1 (from a 2^-61 rounding, so that d = +-1 stays inside from_double's range)
 __device__ __forceinline__ long long xy_q62(double d) { return fx::from_double(d, 61) * 2; }
 
-// the same rotation in fixed point: cb, sb as Q62 limbs (nsb = -sb), each part rounded once
+// the same rotation in fixed point: cb, sb as Q62 limbs (nsb = -sb); each part from six limb
+// products (the two low x low ones dropped: within three units of exact rounding)
 __device__ __forceinline__ void xy_rotate_fx(longlong2& x, longlong2& y, fx::Limbs cb, fx::Limbs sb, fx::Limbs nsb) {
   const fx::Limbs xr = fx::split(x.x), xi = fx::split(x.y), yr = fx::split(y.x), yi = fx::split(y.y);
-  x = make_longlong2(fx::dot2_q62(xr, cb, yi, sb, 0), fx::dot2_q62(xi, cb, yr, nsb, 0));
-  y = make_longlong2(fx::dot2_q62(yr, cb, xi, sb, 0), fx::dot2_q62(yi, cb, xr, nsb, 0));
+  x = make_longlong2(fx::dot2_q62_hi(xr, cb, yi, sb, 0), fx::dot2_q62_hi(xi, cb, yr, nsb, 0));
+  y = make_longlong2(fx::dot2_q62_hi(yr, cb, xi, sb, 0), fx::dot2_q62_hi(yi, cb, xr, nsb, 0));
 }
 
 // The layer's cost unitary fused into the first window's pass (PH): forward, each amplitude
@@ -445,7 +446,7 @@ __device__ __forceinline__ longlong2 xy_fx_phase(longlong2 x, double2 f) {
   const long long fre = xy_q62(f.x), fim = xy_q62(CONJ ? -f.y : f.y);
   const fx::Limbs fr = fx::split(fre), fi = fx::split(fim), nfi = fx::split(-fim);
   const fx::Limbs xr = fx::split(x.x), xi = fx::split(x.y);
-  return make_longlong2(fx::dot2_q62(xr, fr, xi, nfi, 0), fx::dot2_q62(xr, fi, xi, fr, 0));
+  return make_longlong2(fx::dot2_q62_hi(xr, fr, xi, nfi, 0), fx::dot2_q62_hi(xr, fi, xi, fr, 0));
 }
 
 template <typename T, bool TWO, bool PH>
