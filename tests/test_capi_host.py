@@ -55,6 +55,8 @@ def test_graph_check_accepts_and_bounds():
     (4, [[0, 4]], None, True),             # vertex out of range
     (4, [[0, -1]], None, True),            # negative vertex
     (4, [[0, 1], [1, 0]], None, True),     # repeated edge, other orientation
+    (4, [[2, 3], [0, 1], [2, 3]], None, True),  # repeated edge, same orientation
+    (32, [[31, 0], [5, 31], [0, 31]], None, True),  # repeated edge on the highest vertex
     (4, [[0, 1]], [1.5], True),            # non-integral weight under INT
     (4, [[0, 1]], [float("nan")], False),  # non-finite weight
     (4, [[0, 1]], [float("inf")], False),
@@ -65,6 +67,27 @@ def test_graph_check_accepts_and_bounds():
 def test_graph_check_rejects(n, edges, weights, integer):
     rc, _, _ = check(n, edges, weights, integer)
     assert rc == q.QAOA_ERR_INVALID_ARG
+
+
+def test_graph_check_accepts_the_highest_vertices():
+    rc, lo, hi = check(32, [[31, 0], [30, 31], [0, 1], [1, 30]], [1.0, 2.0, 3.0, 4.0])
+    assert rc == 0 and lo == 0 and hi == 10
+
+
+def test_graph_descriptor_follows_replaced_arrays():
+    """The binding builds a graph's C descriptor once; replacing the edges or the weights gives
+    a new one that points at the new arrays."""
+    g = q.Graph(4, np.array([[0, 1], [1, 2]]), np.array([1.0, 2.0]))
+    d1 = g.as_struct()
+    assert g.as_struct() is d1 and d1.m == 2
+    g.edges = np.ascontiguousarray(np.array([[0, 1], [1, 2], [2, 3]], dtype=np.int32))
+    d2 = g.as_struct()
+    assert d2 is not d1 and d2.m == 3 and d2.uv[4] == 2 and d2.uv[5] == 3
+    g.weights = np.array([1.0, 2.0, 5.0])
+    d3 = g.as_struct()
+    assert d3 is not d2 and d3.w[2] == 5.0
+    lo_hi = g.check()
+    assert lo_hi == (0, 8)
 
 
 def test_workspace_sizes():
